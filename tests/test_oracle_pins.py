@@ -1,0 +1,432 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a
+first-principles derivation (WENO5), closed forms and invariants
+(freestream, conservation, symmetry, element balance, backward Euler for a
+linear source), convergence orders, the exact Riemann solution of the Sod
+problem (Sec. 5.1(1)), thermodynamic equilibrium (for Eq. 4.9) and an
+independent stiff integration of a constant-volume reactor (Sec. 5.1(2)).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import ref_exact
+from paper_2504_13750_gb300 import inputs
+
+H2AIR = inputs.load_mechanism("h2air_synth")
+GAS = inputs.load_mechanism("ideal_gamma14")
+R_GAS = 287.0
+
+
+def _cons(mech, st):
+    return orc.prim_to_cons(mech, st["T"], st["p"], st["u"], st["v"], st["Y"])
+
+
+# ----------------------------------------------------------------------------
+# WENO5
+# ----------------------------------------------------------------------------
+def _weno_from_definition():
+    """Candidate values, linear weights and smoothness indicators derived from
+    their definitions (Jiang & Shu 1996): quadratics matching cell averages on
+    each 3-cell substencil, the quartic on all 5 cells, and
+    beta_k = sum_{l=1,2} int_cell (d^l p_k / dx^l)^2 dx (dx = 1)."""
+    sp = pytest.importorskip("sympy")
+    x = sp.Symbol("x")
+    f = sp.symbols("f0:5")  # cell averages on cells -2..2 (centre cell 0)
+    cells = [-2, -1, 0, 1, 2]
+
+    def fit(idx, deg):
+        c = sp.symbols(f"c0:{deg + 1}")
+        P = sum(c[m] * x**m for m in range(deg + 1))
+        eqs = [sp.integrate(P, (x, cells[j] - sp.Rational(1, 2), cells[j] + sp.Rational(1, 2))) - f[j] for j in idx]
+        sol = sp.solve(eqs, c)
+        return sp.expand(P.subs(sol))
+
+    half = sp.Rational(1, 2)
+    q, beta = [], []
+    for k in range(3):
+        P = fit([k, k + 1, k + 2], 2)
+        q.append(sp.expand(P.subs(x, half)))
+        beta.append(sp.expand(sum(sp.integrate(sp.diff(P, x, l) ** 2, (x, -half, half)) for l in (1, 2))))
+    P5 = fit([0, 1, 2, 3, 4], 4).subs(x, half)
+    d = sp.symbols("d0:3")
+    resid = sp.expand(sum(d[k] * q[k] for k in range(3)) - P5)
+    dsol = sp.solve([resid.coeff(fj) for fj in f], d)
+    dv = [dsol[d[k]] for k in range(3)]
+    return (sp.lambdify(f, q), sp.lambdify(f, beta), [float(v) for v in dv])
+
+
+def test_weno5_matches_first_principles():
+    qf, bf, d = _weno_from_definition()
+    assert np.allclose(d, [0.1, 0.6, 0.3], rtol=0, atol=1e-15)
+    rng = np.random.default_rng(0)
+    eps = 1e-6
+    for trial in range(200):
+        scale = 10.0 ** rng.uniform(-3, 6)
+        fv = rng.normal(size=5) * scale
+        if trial % 4 == 0:
+            fv[3:] += 20 * scale  # a jump inside the stencil
+        q = np.array(qf(*fv))
+        b = np.array(bf(*fv))
+        a = np.array(d) / (eps + b) ** 2
+        ref = np.sum(a * q) / np.sum(a)
+        got = orc.weno5(fv, eps)
+        assert abs(got - ref) <= 1e-12 * (np.max(np.abs(fv)) + 1e-300), (fv, got, ref)
+
+
+def test_weno5_special_cases():
+    # polynomial data of degree <= 1: all smoothness indicators agree, the
+    # weights are the linear ones and the face value is exact
+    for c0, c1 in [(3.0, 0.0), (-2.0, 0.5), (1e5, -37.0)]:
+        cells = np.arange(-2, 3)
+        got = orc.weno5(c0 + c1 * cells, 1e-6)
+        assert abs(got - (c0 + c1 * 0.5)) <= 1e-12 * abs(c0)
+    # odd symmetry, bitwise
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        fv = rng.normal(size=5) * 1e3
+        assert orc.weno5(-fv, 1e-6) == -orc.weno5(fv, 1e-6)
+    # essentially non-oscillatory: a jump between f3 and f4 leaves stencil 0/1
+    # smooth; the face value stays within the smooth data range
+    fv = np.array([1.0, 1.0, 1.0, 1.0, 100.0])
+    assert abs(orc.weno5(fv, 1e-6) - 1.0) < 1e-6
+
+
+# ----------------------------------------------------------------------------
+# Semi-discretisation + RK3
+# ----------------------------------------------------------------------------
+def _advection(N, dt_of, tend=0.002, u0=100.0):
+    """Contact-wave advection: rho = 1 + 0.2 sin(2 pi x), u, p constant,
+    periodic in x. The exact solution is a translation."""
+    dx = 1.0 / N
+    x = (np.arange(N) + 0.5) * dx
+    rho = 1 + 0.2 * np.sin(2 * np.pi * x)
+    p = 1e5 * np.ones(N)
+    T = p / (rho * R_GAS)
+    g = inputs.grid_dict(N, 1, dx, dx, [inputs.BC_PERIODIC] * 2 + [inputs.BC_ZEROGRAD] * 2)
+    U = orc.prim_to_cons(GAS, T[None], p[None], u0 * np.ones((1, N)), np.zeros((1, N)), np.ones((1, 1, N)))
+    dt = dt_of(dx)
+    n = int(np.ceil(tend / dt))
+    U, Tt, st, t, _ = orc.step(GAS, g, U, T[None].copy(), n, dt=tend / n, chem=False)
+    assert st == 0
+    return U[0, 0], 1 + 0.2 * np.sin(2 * np.pi * (x - u0 * tend))
+
+
+def test_space_order_five():
+    errs = []
+    for N in (20, 40, 80):
+        rho, ex = _advection(N, lambda dx: 0.5 * dx ** (5 / 3) / 450.0)
+        errs.append(np.mean(np.abs(rho - ex)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 4.7), orders
+
+
+def test_time_order_three():
+    # fixed grid; the error against a 16x finer dt isolates the RK3 error
+    N = 40
+    ref, _ = _advection(N, lambda dx: 0.05 * dx / 450.0)
+    errs = []
+    for cfl in (1.2, 0.6, 0.3):
+        rho, _ = _advection(N, lambda dx: cfl * dx / 450.0)
+        errs.append(np.max(np.abs(rho - ref)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - 3.0) < 0.3), orders
+
+
+def test_freestream_exact():
+    st = inputs.tube(H2AIR, 24, 8, ign_frac=0.0)
+    U = _cons(H2AIR, st)
+    L, Fx, Gy, al = orc.rhs(H2AIR, st["grid"], U, st["T"])
+    assert np.all(L == 0.0)
+
+
+def test_sod_exact_riemann():
+    gold = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "sod_star_state.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                gold[k] = float(v)
+    ps, us = ref_exact.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    assert abs(ps - gold["p_star"]) < 1e-5 and abs(us - gold["u_star"]) < 1e-5
+    errs = {}
+    for N in (400, 800):
+        st = inputs.sod(GAS, N)
+        U, T = _cons(GAS, st), st["T"].copy()
+        t, tend = 0.0, 0.01
+        while t < tend - 1e-15:
+            dt = min(orc.cfl_dt(GAS, st["grid"], U, T, 0.2), tend - t)
+            U, T, s, tt, _ = orc.step(GAS, st["grid"], U, T, 1, dt=dt, chem=False)
+            assert s == 0
+            t += tt
+        ex = ref_exact.riemann_exact((1.0, 0.0, 1e5), (0.125, 0.0, 1e4), st["x"], tend)
+        rho = U[0, 0]
+        u = U[1, 0] / rho
+        p, _ = orc.primitives(GAS, U, T)
+        errs[N] = [np.mean(np.abs(a - b)) / np.mean(np.abs(b)) for a, b in
+                   ((rho, ex[0]), (p[0], ex[2]))] + [np.mean(np.abs(u - ex[1])) / us / np.sqrt(1e5)]
+    # bounds frozen from the first run at 400 cells (L1(rho) = 3.1e-3)
+    assert errs[400][0] < 3.5e-3 and errs[400][1] < 3.5e-3 and errs[400][2] < 1e-2, errs
+    # first-order convergence across discontinuities
+    assert all(errs[400][i] / errs[800][i] > 1.6 for i in range(3)), errs
+
+
+# ----------------------------------------------------------------------------
+# Thermodynamics and Newton recovery
+# ----------------------------------------------------------------------------
+def test_thermo_consistency():
+    # Eq. 4.4 and 4.5 must integrate Eq. 4.3: dh/dT = cp, ds/dT = cp/T
+    for k in range(H2AIR["ns"]):
+        for T in (300.0, 900.0, 2000.0, 3500.0):
+            h = 1e-5 * T
+            cp, _, _ = orc.thermo(H2AIR, k, T)
+            _, hp, sp_ = orc.thermo(H2AIR, k, T + h)
+            _, hm, sm = orc.thermo(H2AIR, k, T - h)
+            assert abs((hp - hm) / (2 * h) - cp) < 1e-8 * cp
+            assert abs((sp_ - sm) / (2 * h) - cp / T) < 1e-8 * cp / T
+    # anchors of the synthetic table: h(298.15) = formation enthalpy of H2O
+    k = H2AIR["species"].index("H2O")
+    _, h, _ = orc.thermo(H2AIR, k, 298.15)
+    assert abs(h * 8.314472 - (-241.8e3)) < 1e-6 * 241.8e3
+
+
+def test_newton_recovers_temperature():
+    rng = np.random.default_rng(3)
+    n = 200
+    T = rng.uniform(250.0, 3500.0, n)
+    p = rng.uniform(0.3, 80.0, n) * inputs.ATM
+    Y = rng.dirichlet(np.ones(H2AIR["ns"]), n).T
+    u, v = rng.normal(0, 500, n), rng.normal(0, 500, n)
+    U = orc.prim_to_cons(H2AIR, T, p, u, v, Y)
+    grid = inputs.grid_dict(n, 1, 1.0, 1.0, [1] * 4)
+    for warm in (np.full(n, 1000.0), T * 1.3, T * 0.8):
+        Tr, st = orc.newton(H2AIR, grid, U, warm)
+        assert st == 0
+        assert np.max(np.abs(Tr - T) / T) < 1e-12
+    # calorically perfect gas: closed form T = e / cv
+    Ug = orc.prim_to_cons(GAS, T, p, u, v, np.ones((1, n)))
+    e = Ug[3] / Ug[0] - 0.5 * (Ug[1] ** 2 + Ug[2] ** 2) / Ug[0] ** 2
+    Tr, st = orc.newton(GAS, grid, Ug, np.full(n, 500.0))
+    assert np.max(np.abs(Tr - e / (2.5 * R_GAS)) / Tr) < 1e-12
+    pg, cg = orc.primitives(GAS, Ug, Tr)
+    assert np.max(np.abs(cg - np.sqrt(1.4 * R_GAS * Tr)) / cg) < 1e-12
+    assert np.max(np.abs(pg - p) / p) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Kinetics and point-implicit chemistry
+# ----------------------------------------------------------------------------
+def _elements_matrix(mech):
+    el = mech["elements"]
+    names = sorted({e for s in mech["species"] for e in el[s]})
+    return np.array([[el[s].get(e, 0) for s in mech["species"]] for e in names], dtype=float)
+
+
+def test_rates_conserve_mass_and_elements():
+    E = _elements_matrix(H2AIR)
+    M = H2AIR["M"]
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        T = rng.uniform(500.0, 3500.0)
+        X = 10.0 ** rng.uniform(-6, 2, H2AIR["ns"])
+        w = orc.production_rates(H2AIR, T, X)
+        scale = np.max(np.abs(w)) + 1e-300
+        assert abs(np.sum(w)) <= 1e-12 * scale * H2AIR["ns"]
+        assert np.all(np.abs(E @ (w / M)) <= 1e-12 * np.max(np.abs(w / M)) * H2AIR["ns"])
+        assert w[-1] == 0.0  # N2 inert
+
+
+def test_jacobian_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    st = inputs.ignition_cell(H2AIR, T0=2200.0, p0=10 * inputs.ATM)
+    for trial in range(10):
+        Y = rng.dirichlet(np.ones(H2AIR["ns"])) * 0.5 + 0.5 * st["Y"][:, 0, 0]
+        U = orc.prim_to_cons(H2AIR, np.array([1500.0 + 200 * trial]), np.array([10 * inputs.ATM]),
+                             np.zeros(1), np.zeros(1), Y[:, None])[:, 0]
+        T = 1500.0 + 200 * trial
+        S, J = orc.source_jacobian(H2AIR, U, T)
+        nsp = H2AIR["ns"] - 1
+        for l in range(nsp):
+            h = 1e-6 * U[4 + l] + 1e-12
+            up, um = U.copy(), U.copy()
+            up[4 + l] += h
+            um[4 + l] -= h
+            Sp, _ = orc.source_jacobian(H2AIR, up, T)
+            Sm, _ = orc.source_jacobian(H2AIR, um, T)
+            fd = (Sp - Sm) / (2 * h)
+            assert np.max(np.abs(fd - J[:, l])) <= 1e-6 * (np.max(np.abs(J)) + 1e-300), (trial, l)
+
+
+def _linear_mech(kf, dh_R=1500.0, ds_R=0.7):
+    """A <=> B with an inert carrier N; same heat capacity, offsets in the
+    enthalpy and entropy constants so that K_c = exp(ds_R - dh_R / T)."""
+    base = [3.5, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0]
+    nasa = np.array([base, base, base])
+    nasa[1, 5] = dh_R
+    nasa[1, 6] = ds_R
+    return {"name": "linear", "species": ["A", "B", "N"], "ns": 3, "nr": 1,
+            "M": np.array([0.03, 0.03, 0.028]), "nasa": nasa,
+            "A": np.array([kf]), "b": np.zeros(1), "Ea": np.zeros(1),
+            "nuf": np.array([[1, 0, 0]], dtype=np.int32), "nub": np.array([[0, 1, 0]], dtype=np.int32),
+            "tb": np.zeros(1, dtype=np.int32), "eff": np.ones((1, 3)), "elements": {}}
+
+
+def test_point_implicit_is_backward_euler_for_linear_source():
+    kf, T, dt = 3.0e4, 1200.0, 2e-5
+    m = _linear_mech(kf)
+    Kc = np.exp(0.7 - 1500.0 / T)
+    kb = kf / Kc
+    MA, MB = 0.03, 0.03
+    rhoA, rhoB, rhoN = 0.4, 0.1, 0.7
+    u = np.array([rhoA + rhoB + rhoN, 0.0, 0.0, 1e5, rhoA, rhoB])
+    # exact linear system in (rhoA, rhoB): d/dt = A (rhoA, rhoB)
+    A = np.array([[-kf, kb], [kf, -kb]])  # equal molar masses
+    expect = np.linalg.solve(np.eye(2) - dt * A, np.array([rhoA, rhoB]))
+    got, st = orc.point_implicit(m, u[:, None], np.array([T]), dt)
+    assert st == 0
+    assert np.allclose(got[4:6, 0], expect, rtol=1e-13, atol=0)
+    assert abs(got[4, 0] + got[5, 0] - (rhoA + rhoB)) < 1e-15
+    _ = MA, MB
+
+
+def test_point_implicit_reaches_gibbs_equilibrium():
+    # repeated point-implicit updates at frozen T converge to S = 0; that
+    # composition must minimise the Helmholtz energy (pins Eq. 4.9)
+    T = 2600.0
+    st = inputs.ignition_cell(H2AIR, T0=T, p0=5 * inputs.ATM)
+    U = _cons(H2AIR, st)[:, 0, 0]
+    for dt in [1e-9] * 200 + [1e-7] * 200 + [1e-5] * 400:
+        U, s = orc.point_implicit(H2AIR, U[:, None], np.array([T]), dt)
+        U = U[:, 0]
+        assert s == 0
+    M = H2AIR["M"]
+    c = np.append(U[4:] / M[:-1], (U[0] - U[4:].sum()) / M[-1])
+    ceq, res = ref_exact.gibbs_equilibrium(H2AIR, T, c, H2AIR["elements"])
+    major = ceq > 1e-3 * ceq.max()
+    assert np.max(np.abs(c[major] - ceq[major]) / ceq[major]) < 1e-4, (c, ceq)
+
+
+def _crossing(t, T, level):
+    """Time at which T first reaches ``level`` (linear interpolation)."""
+    i = int(np.argmax(T >= level))
+    assert i > 0
+    return t[i - 1] + (level - T[i - 1]) * (t[i] - t[i - 1]) / (T[i] - T[i - 1])
+
+
+def test_ignition_delay_matches_independent_stiff_integration():
+    T0, p0 = 1500.0, 20 * inputs.ATM
+    st = inputs.ignition_cell(H2AIR, T0=T0, p0=p0)
+    U0 = _cons(H2AIR, st)
+    rho = U0[0, 0, 0]
+    Y0 = st["Y"][:, 0, 0]
+    t_end = 2.0e-4
+    t_eval = np.linspace(0, t_end, 20001)
+    R = ref_exact.ConstantVolumeReactor(H2AIR)
+    tr, Tr, _ = R.ignition(rho, Y0, T0, t_end, t_eval)
+    tau_ref = _crossing(tr, Tr, T0 + 400.0)
+
+    def oracle_run(dt):
+        U, T = U0.copy(), st["T"].copy()
+        ts, Ts = [0.0], [T0]
+        chunk = max(1, int(round(1e-8 / dt)))
+        for _ in range(int(round(t_end / dt)) // chunk):
+            U, T, s, tt, _ = orc.step(H2AIR, st["grid"], U, T, chunk, dt=dt, chem=True)
+            assert s == 0
+            ts.append(ts[-1] + tt)
+            Ts.append(T[0, 0])
+        ts, Ts = np.array(ts), np.array(Ts)
+        return _crossing(ts, Ts, T0 + 400.0), Ts[-1]
+
+    tau5, Tend5 = oracle_run(5e-9)  # the paper's adopted dt (Sec. 5.1(2))
+    tau10, _ = oracle_run(1e-8)
+    assert abs(tau5 - tau_ref) / tau_ref < 0.01, (tau5, tau_ref)
+    assert abs(Tend5 - Tr[-1]) / Tr[-1] < 1e-3
+    # first order in dt: halving dt roughly halves the delay error
+    e5, e10 = abs(tau5 - tau_ref), abs(tau10 - tau_ref)
+    assert 1.6 < e10 / e5 < 2.5, (e5, e10, tau_ref)
+
+
+# ----------------------------------------------------------------------------
+# Whole-step invariants on the detonation tube
+# ----------------------------------------------------------------------------
+def test_tube_conserves_mass_elements_energy():
+    st = inputs.tube(H2AIR, 64, 16)
+    U = _cons(H2AIR, st)
+    T = st["T"].copy()
+    U1, T1, s, t, dts = orc.step(H2AIR, st["grid"], U, T, 60, cfl=0.5, chem=True)
+    assert s == 0
+    iOH = H2AIR["species"].index("OH")
+    assert U1[4 + iOH].max() > 1e-6  # chemistry is active in the igniter
+    M = H2AIR["M"]
+    E = _elements_matrix(H2AIR)
+
+    def totals(U):
+        rhoY = np.concatenate([U[4:], (U[0] - U[4:].sum(axis=0))[None]], axis=0)
+        moles = rhoY.reshape(H2AIR["ns"], -1).sum(axis=1) / M
+        return np.concatenate([[U[0].sum(), U[3].sum()], E @ moles])
+
+    a, b = totals(U), totals(U1)
+    assert np.max(np.abs(b - a) / np.abs(a)) < 1e-12, (a, b)
+
+
+def test_symmetry_and_transpose_bitwise():
+    st = inputs.tube(H2AIR, 32, 12)
+    # make the state symmetric about the mid-height with a y-dependent T
+    y = np.arange(12)
+    st["T"] = st["T"] * (1.0 + 0.02 * np.cos(2 * np.pi * (y[:, None] + 0.5) / 12))
+    st["T"][6:] = st["T"][5::-1]  # exact mirror image, bit for bit
+    U = _cons(H2AIR, st)
+    # flux operator only: on this coarse grid the CFL step is far beyond the
+    # point-implicit chemistry's stable range (negative species appear)
+    U1, T1, s, _, _ = orc.step(H2AIR, st["grid"], U, st["T"].copy(), 25, cfl=0.5, chem=False)
+    assert s == 0
+    for k in range(U.shape[0]):
+        mirrored = U1[k, ::-1, :]
+        if k == 2:
+            assert np.array_equal(U1[k], -mirrored)
+        else:
+            assert np.array_equal(U1[k], mirrored)
+    # transposition (dx = dy): swap axes and the two momenta
+    Ut = np.transpose(U, (0, 2, 1)).copy()
+    Ut[[1, 2]] = Ut[[2, 1]]
+    gt = dict(st["grid"], nx=st["grid"]["ny"], ny=st["grid"]["nx"])
+    Ut1, Tt1, s, _, _ = orc.step(H2AIR, gt, Ut, st["T"].T.copy(), 25, cfl=0.5, chem=False)
+    back = np.transpose(Ut1, (0, 2, 1))
+    back[[1, 2]] = back[[2, 1]]
+    assert np.array_equal(back, U1)
+    assert np.array_equal(Tt1.T, T1)
+
+
+def test_tangent_model_matches_finite_differences():
+    st = inputs.tube(H2AIR, 12, 6)
+    rng = np.random.default_rng(7)
+    # per-cell T spread so that the global max of Eq. 4.11 has a unique argmax
+    st["T"] = st["T"] + rng.normal(0.0, 5.0, st["T"].shape)
+    U = _cons(H2AIR, st)
+    T = st["T"].copy()
+    dt = 0.5 * orc.cfl_dt(H2AIR, st["grid"], U, T, 0.5)
+    dT0 = rng.normal(0, 1.0, T.shape)
+    # a temperature direction at fixed p and Y, by linearising prim_to_cons
+    h = 1e-3
+    Up = orc.prim_to_cons(H2AIR, st["T"] + h * dT0, st["p"], st["u"], st["v"], st["Y"])
+    Um = orc.prim_to_cons(H2AIR, st["T"] - h * dT0, st["p"], st["u"], st["v"], st["Y"])
+    dU0 = (Up - Um) / (2 * h)
+    _, _, dU, _, s = orc.step_tangent(H2AIR, st["grid"], U, T, dU0, dT0, 4, dt)
+    assert s == 0
+    hs = 1e-4
+    Ua, _, _, _, _ = orc.step(H2AIR, st["grid"], U + hs * dU0, T + hs * dT0, 4, dt=dt)
+    Ub, _, _, _, _ = orc.step(H2AIR, st["grid"], U - hs * dU0, T - hs * dT0, 4, dt=dt)
+    fd = (Ua - Ub) / (2 * hs)
+    for k in range(U.shape[0]):
+        scale = np.max(np.abs(dU[k])) + 1e-300
+        assert np.max(np.abs(fd[k] - dU[k])) <= 1e-5 * scale + 1e-12 * np.max(np.abs(U[k])), k
+
+
+def test_opcount_is_positive_and_fixed():
+    g = inputs.grid_dict(8, 4, 1.0, 1.0, [0] * 4)
+    ops = orc.opcount(H2AIR, g, 0)
+    # a WENO5 reconstruction in its plain textbook form
+    assert ops["add"] > 15 and ops["mul"] > 15 and ops["div"] >= 4 and ops["exp"] == 0
