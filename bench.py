@@ -1,0 +1,312 @@
+"""Benchmark: FP64 cell-steps/s of the reacting-flow step on a 4096 x 512
+H2-air detonation tube (2.1 M cells, 9 species / 19 reactions, slip walls,
+CFL 0.5, seeded 1 % density perturbation), one JSON line on stdout.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one advance_one_step (CFL dt, 3 LF-split WENO5 RK stages with
+Newton T recovery, point-implicit chemistry) over the whole grid. Each rank
+runs its own replica of the tube (the solve is independent per GPU: weak
+scaling, no data-path collective); `value` is the sum over ranks of
+cells x steps / the max over ranks of the device-timed region.
+
+`--impl reference` times the CPU FP64 oracle (the plain restatement of the
+method used by the tests) on the host cores on a slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 4096, 512
+CFL = 0.5
+WORKLOAD = "h2air_detonation_tube_4096x512_9sp19r_cfl0.5"
+METRIC = "FP64 cell-steps/s per GB300"
+UNIT = "cell-steps/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def tube_state():
+    from paper_2504_13750_gb300 import inputs
+
+    mech = inputs.load_mechanism("h2air_synth")
+    st = inputs.tube(mech, NX, NY, perturb_seed=0)
+    return mech, st
+
+
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def weno_flops():
+    """Algorithmic flops of one textbook WENO5 reconstruction, as counted by
+    the oracle's operation-counting scalar (stored by oracle/count_ops.py)."""
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_opcounts.json")) as f:
+        return json.load(f)["weno5"]["flops"]
+
+
+# ----------------------------------------------------------------------------
+def cpu_baseline_oracle(mech, st, steps=2):
+    """The oracle as it stands on the host cores: `steps` full steps of the
+    4096 x 512 tube. Returns (cell-steps/s, cores, sample text)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as orc
+
+    orc.build()
+    cores = orc.set_threads(0)
+    U = orc.prim_to_cons(mech, st["T"], st["p"], st["u"], st["v"], st["Y"])
+    t0 = time.perf_counter()
+    orc.step(mech, st["grid"], U, st["T"], steps, cfl=CFL)
+    dt = time.perf_counter() - t0
+    return NX * NY * steps / dt, cores, f"{steps} full steps of the {NX}x{NY} tube ({dt:.1f} s)"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as orc
+    from paper_2504_13750_gb300 import inputs
+
+    orc.build()
+    mech = inputs.load_mechanism("h2air_synth")
+    # each step: one oracle step on a 4096 x 32 slab of the same tube (the
+    # bottom rows, slip walls), so the whole run stays within minutes
+    rows = 32
+    st = inputs.tube(mech, NX, rows, perturb_seed=0)
+    cores = orc.set_threads(0)
+    U = orc.prim_to_cons(mech, st["T"], st["p"], st["u"], st["v"], st["Y"])
+    T = st["T"].copy()
+    for _ in range(args.warmup):
+        U, T, _, _, _ = orc.step(mech, st["grid"], U, T, 1, cfl=CFL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, T, _, _, _ = orc.step(mech, st["grid"], U, T, 1, cfl=CFL)
+    el = time.perf_counter() - t0
+    value = NX * rows * args.steps / el
+    sample = f"one oracle step of a {NX}x{rows} slab of the tube per step ({args.steps} timed, {args.warmup} warm-up)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "sample_rows": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2504_13750_gb300 import build, janc
+
+    build.build()
+    mech, st = tube_state()
+    # CPU baseline first (rank 0, N = 1 only), before the GPU is busy
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_baseline_oracle(mech, st)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    stream = torch.cuda.Stream()
+    g = janc.Grid(mech, NX, NY, st["grid"]["dx"], st["grid"]["dy"], st["grid"]["bc"], chemistry=True,
+                  stream=stream)
+    g.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    g.step(args.warmup, cfl=CFL)
+    torch.cuda.synchronize()
+
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index) as clk:
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        janc.janc_profile(g.handle, True)
+        ev0.record(stream)
+        g.step(args.steps, cfl=CFL)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+    janc.janc_profile(g.handle, False)
+    ms = ev0.elapsed_time(ev1)
+    prof = janc.janc_profile_read(g.handle)
+    stt = g.status()
+    if stt["status"] != 0:
+        raise RuntimeError(f"device status {stt['status']:#x} after the timed region")
+    if pg:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = NX * NY
+    value = world * cells * args.steps / (ms * 1e-3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    nv = g.nv
+    Uh = torch.empty((nv, NY, NX), dtype=torch.float64, pin_memory=True).numpy()
+    Th = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True).numpy()
+    janc.janc_get_state(g.handle, Uh, Th)
+    e2e_steps = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        janc.janc_set_state(g.handle, Uh, Th)
+        janc.janc_step(g.handle, 1, cfl=CFL)
+        janc.janc_get_state(g.handle, Uh, Th)
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(Uh.nbytes + Th.nbytes), "d2h_bytes_per_step": int(Uh.nbytes + Th.nbytes),
+           "steps": e2e_steps}
+
+    # ---- roofline of the dominant kernel (face fluxes: FP64-pipe bound) ----
+    ff_ms, ff_n = prof["face_flux"]
+    faces = (NX + 1) * NY + NX * (NY + 1)
+    flops_launch = nv * faces * (2 * weno_flops() + 1)
+    achieved = flops_launch / (ff_ms / ff_n * 1e-3) / 1e12
+    peaks = measured_peaks()
+    fp64_nominal = 1.25  # TFLOP/s, GB300 FP64 (recipe's nominal figure)
+    dfma = janc.janc_fp64_peak(stream.cuda_stream, 4000)
+    fp64_measured = 2.0 * dfma / 1e12
+    total_prof = sum(v[0] for v in prof.values())
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_nominal, "unit": "TFLOP/s",
+            "frac": achieved / fp64_nominal, "traffic": None, "kernel": "k_face_flux",
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz)",
+            "peak_measured_dfma_tflops": fp64_measured, "frac_of_measured_dfma": achieved / fp64_measured,
+            "flops_per_launch": flops_launch, "avg_launch_ms": ff_ms / ff_n}
+    # HBM view of the same kernel (the benchmark spec asks for it beside the FP64 view)
+    bytes_launch = 8 * (nv + 2) * cells + 8 * nv * faces  # state + u/v/p planes read, face fluxes written
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    roof_hbm = {"achieved_gbs": bytes_launch / (ff_ms / ff_n * 1e-3) / 1e9, "peak_gbs": hbm,
+                "frac": bytes_launch / (ff_ms / ff_n * 1e-3) / 1e9 / hbm, "bytes_per_launch": bytes_launch}
+    kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / total_prof if total_prof else None}
+               for k, v in prof.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "cells": cells, "species": 9, "reactions": 19,
+                   "cfl": CFL, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: each state buffer is 16 planes x 2.1 M cells = 268 MB"},
+        "e2e": e2e,
+        "roofline": roof,
+        "roofline_hbm": roof_hbm,
+        "kernels": kernels,
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "t_sim_s": stt["t"],
+    }
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * janc.h - C ABI of the GB300 (sm_103a) reacting-flow step.
+ *
+ * The library advances the 2D reactive Euler equations (arXiv 2504.13750,
+ * Sec. 4.1, Eq. 4.1) on a uniform Cartesian grid with the scheme of Sec. 4.2:
+ * global Lax-Friedrichs flux splitting (Eq. 4.11) with WENO5 reconstruction
+ * and 3 ghost layers, 3rd-order TVD Runge-Kutta for the flux terms, Newton
+ * recovery of T from the energy, and the first-order point-implicit chemistry
+ * update (Eq. 4.12-4.13) with Arrhenius and equilibrium rates (Eq. 4.6-4.9).
+ * One call of janc_step runs advance_one_step of Sec. 4.3 n times.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: 0 on success, a negative JANC_E_* code on failure. Nothing
+ *    throws across the ABI; janc_last_error() gives a text for the calling
+ *    thread's most recent failure.
+ *  - Arithmetic is IEEE FP64 throughout.
+ *  - State layout: structure of arrays, U[nv][ny][nx] with x fastest,
+ *    nv = ns + 3 planes in the order rho, rho u, rho v, E, rho Y_1 ..
+ *    rho Y_{ns-1} (SI units: kg/m^3, kg/(m^2 s), J/m^3); T[ny][nx] in K.
+ *    The ns-th species is not carried (Y_ns = 1 - sum of the others).
+ *  - Pointer arguments marked "host or device" are read or written according
+ *    to the `where` argument (JANC_HOST / JANC_DEVICE). Host copies are
+ *    synchronous with respect to the caller; device pointers are used in
+ *    order on the grid's stream. All buffers passed in stay owned by the
+ *    caller and may be released once the call returns (host) or once the
+ *    stream has passed the call (device).
+ *  - Work is enqueued on the CUDA stream given at creation (NULL = legacy
+ *    default stream). janc_step is asynchronous; device-side failures are
+ *    recorded in a status word that janc_status / janc_get_state report.
+ *  - A grid handle must not be used from two host threads at once.
+ */
+#ifndef JANC_H_
+#define JANC_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define JANC_OK 0
+#define JANC_E_INVALID (-1)     /* bad argument (null pointer, size, mode) */
+#define JANC_E_UNSUPPORTED (-2) /* valid but not built (e.g. species count) */
+#define JANC_E_CUDA (-3)        /* a CUDA runtime call failed */
+#define JANC_E_NOMEM (-4)       /* device allocation failed or workspace too small */
+#define JANC_E_DEVICE (-5)      /* the device status word reports a failure */
+
+/* Boundary kinds (user boundary hooks of Sec. 4.3 reduced to three forms). */
+#define JANC_BC_WALL 0      /* slip wall: mirror ghosts, wall-normal momentum negated */
+#define JANC_BC_ZEROGRAD 1  /* non-reflecting: zero-gradient copy of the edge cell */
+#define JANC_BC_PERIODIC 2  /* periodic wrap (both sides of an axis must agree) */
+
+#define JANC_HOST 0
+#define JANC_DEVICE 1
+
+/* Device status bits (OR-ed by the kernels, read by janc_status). */
+#define JANC_ST_NONFINITE 1      /* a NaN or Inf appeared in the state */
+#define JANC_ST_NONPOSITIVE 2    /* rho, T or p <= 0 */
+#define JANC_ST_NEWTON_FAIL 4    /* T recovery did not converge in newton_maxit */
+#define JANC_ST_SINGULAR 8       /* zero pivot in the point-implicit solve */
+
+typedef struct janc_grid_s* janc_grid_t;
+
+/* Grid description.
+ * nx, ny >= 1 cells; dx, dy > 0 m; bc = {left, right, bottom, top};
+ * chemistry = 1 runs advance_source_term (Eq. 4.12-4.13) after the flux RK3,
+ * 0 runs the explicit variant of advance_one_step (Sec. 4.3);
+ * weno_eps = epsilon of the WENO5-JS weights (1e-6 if <= 0);
+ * newton_tol / newton_maxit = stop when |dT| <= tol * T (1e-12 / 50 if <= 0). */
+typedef struct {
+  int nx, ny;
+  double dx, dy;
+  int bc[4];
+  int chemistry;
+  double weno_eps;
+  double newton_tol;
+  int newton_maxit;
+} janc_grid_desc;
+
+/* Mechanism and thermodynamic data (Eq. 4.3-4.9), all SI, copied at creation.
+ * ns species (the last one is not carried in U), nr reactions.
+ * M[ns] kg/mol; nasa[ns*7] NASA-7 coefficients a_0..a_6 (single range);
+ * A[nr], b[nr], Ea[nr]: k_f = A T^b exp(-Ea / (Ru T)), Ea in J/mol;
+ * nuf[nr*ns], nub[nr*ns]: reactant / product stoichiometric coefficients;
+ * tb[nr] = 1 when reaction i carries the third-body factor sum_j eff[i*ns+j] X_j
+ * (1 otherwise). Supported: ns in {1, 3, 9}, nr <= 32, at most 3 distinct
+ * species on each side of a reaction, coefficients 0..3. */
+typedef struct {
+  int ns, nr;
+  const double* M;
+  const double* nasa;
+  const double* A;
+  const double* b;
+  const double* Ea;
+  const int* nuf;
+  const int* nub;
+  const int* tb;
+  const double* eff;
+} janc_mechanism;
+
+typedef struct {
+  int status;          /* OR of JANC_ST_* since creation or the last reset */
+  int steps_done;      /* steps completed since creation */
+  double t;            /* simulated time since creation, s */
+  double dt_last;      /* dt of the most recent step, s */
+  double alpha[2];     /* LF speeds (Eq. 4.11) of the current state, m/s */
+} janc_status_info;
+
+/* Bytes of device workspace janc_create_grid needs for this grid. */
+int janc_workspace_bytes(const janc_grid_desc* d, const janc_mechanism* m, size_t* bytes);
+
+/* Create a grid. `workspace` is a device allocation of at least
+ * janc_workspace_bytes(d, m) bytes, 256-byte aligned, owned by the caller and
+ * kept alive until janc_destroy_grid; pass NULL to let the library allocate
+ * (and free) its own. `cuda_stream` is a cudaStream_t (NULL = default). The
+ * state is undefined until janc_set_state or janc_set_state_primitive. */
+int janc_create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* workspace, size_t workspace_bytes,
+                     void* cuda_stream, janc_grid_t* out);
+
+/* Load the conserved state U[nv][ny][nx] (host or device). With T0 non-NULL
+ * it is the warm start of the Newton T recovery (end of Sec. 4.2); with NULL
+ * the recovery starts from 1000 K. Resets the status word. */
+int janc_set_state(janc_grid_t g, const double* U, const double* T0, int where);
+
+/* Load the state from primitive fields T, p, u, v [ny][nx] and mass
+ * fractions Y[ns][ny][nx] of all ns species (host or device), through the
+ * equation of state of Eq. 4.2. Resets the status word. */
+int janc_set_state_primitive(janc_grid_t g, const double* T, const double* p, const double* u, const double* v,
+                             const double* Y, int where);
+
+/* Advance n_steps steps of advance_one_step (Sec. 4.3). Exactly one of
+ * dt > 0 (fixed step) or cfl > 0 must be given; with cfl each step uses
+ * dt = cfl * min(dx, dy) / max(alpha_x, alpha_y) of its starting state,
+ * computed on the device. t_out / dt_last_out (host, may be NULL) receive the
+ * simulated time of the call and the last dt; giving either synchronises the
+ * stream. */
+int janc_step(janc_grid_t g, int n_steps, double dt, double cfl, double* t_out, double* dt_last_out);
+
+/* Copy out U[nv][ny][nx] and T[ny][nx] (either may be NULL), host or device.
+ * Host copies synchronise the stream. Returns JANC_E_DEVICE (after copying)
+ * when the status word is non-zero. */
+int janc_get_state(janc_grid_t g, double* U, double* T, int where);
+
+/* Right-hand side of the current state, for checking: the split WENO5 face
+ * fluxes Fx[nv][ny][nx+1] (x-face i-1/2 at index i) and Gy[nv][ny+1][nx]
+ * (y-face j-1/2 at index j) of Eq. 4.10-4.11, L = -(dF/dx + dG/dy)
+ * [nv][ny][nx], and alpha[2] (any may be NULL), host or device. */
+int janc_rhs(janc_grid_t g, double* Fx, double* Gy, double* L, double* alpha, int where);
+
+/* Per-kernel timing. While enabled, janc_step brackets every kernel launch
+ * with CUDA events on the grid's stream. janc_profile_read synchronises,
+ * returns per kernel class (0 = face fluxes, 1 = RK stage update, 2 =
+ * chemistry) the summed device time in ms and the launch count, and clears
+ * the counters. Arrays have 3 entries. */
+int janc_profile(janc_grid_t g, int enable);
+int janc_profile_read(janc_grid_t g, double* ms, long long* launches);
+
+/* Read the status word and counters (synchronises the stream). */
+int janc_status(janc_grid_t g, janc_status_info* s);
+
+/* Text of the calling thread's most recent error ("" if none). */
+const char* janc_last_error(void);
+
+/* Release the grid (waits for its stream). */
+void janc_destroy_grid(janc_grid_t g);
+
+/* FP64 pipe throughput probe: runs n_iter dependent-chain DFMA loops on
+ * every SM and reports the DFMA lane operations per second it sustained
+ * (a measured FP64 peak for roofline fractions). Synchronous. */
+int janc_fp64_peak(void* cuda_stream, int n_iter, double* dfma_per_s);
+
+/* Accuracy check of the library's FP64 reciprocal (MUFU seed refined by two
+ * Newton-Raphson steps) against IEEE division on the device, over the n host
+ * values x (positive normal doubles): max_ulp receives the largest distance
+ * in units in the last place. Synchronous; allocates scratch. */
+int janc_selfcheck_rcp(const double* x, int n, long long* max_ulp);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JANC_H_ */

@@ -1,0 +1,518 @@
+// C ABI of the reacting-flow step (see include/janc.h for the contract).
+//
+// Device memory of one grid (one workspace, 256-byte aligned pieces):
+//   3 state buffers of nv + 4 planes [ny][nx] each (conserved, T, u, v, p):
+//     S0 = U^n (and U^{n+1} after the step), S1 = stage 1 / scratch,
+//     S2 = stage 2;
+//   Fx[nv][ny][nx+1], Gy[nv][ny+1][nx] face fluxes;
+//   alpha slots: 2 x u64 per state of a chunk of steps (bit patterns of the
+//     non-negative LF speeds, reduced with atomicMax);
+//   clock2 (t, dt_last), status word, mechanism table.
+// The step sequence per time step (advance_one_step, Sec. 4.3) is
+//   flux(S0) -> update1 -> S1, flux(S1) -> update2 -> S2,
+//   flux(S2) -> update3 -> S0 (in place), [chem on S0 in place],
+// with dt computed on the device from the alpha slot of the step's start.
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/janc.h"
+#include "janc_device.cuh"
+#include "janc_internal.h"
+
+using namespace janc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+int fail_cuda(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return JANC_E_CUDA;
+}
+
+constexpr int CHUNK = 256;  // steps per alpha-slot chunk
+constexpr int SLOTS_PER_STEP = 4;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t state, fx, gy, alpha, clock, status, mech, total;
+};
+
+Layout layout_of(int nx, int ny, int nv) {
+  Layout L;
+  const size_t n = (size_t)nx * ny;
+  L.state = align256(sizeof(double) * (size_t)(nv + 4) * n);
+  L.fx = align256(sizeof(double) * (size_t)nv * ny * (nx + 1));
+  L.gy = align256(sizeof(double) * (size_t)nv * (ny + 1) * nx);
+  L.alpha = align256(sizeof(unsigned long long) * 2 * (SLOTS_PER_STEP * CHUNK + 1));
+  L.clock = align256(sizeof(double) * 2);
+  L.status = align256(sizeof(int));
+  L.mech = align256(sizeof(MechDev));
+  L.total = 3 * L.state + L.fx + L.gy + L.alpha + L.clock + L.status + L.mech;
+  return L;
+}
+
+int check_desc(const janc_grid_desc* d, const janc_mechanism* m) {
+  if (!d || !m) return fail(JANC_E_INVALID, "null descriptor");
+  if (d->nx < 1 || d->ny < 1) return fail(JANC_E_INVALID, "nx, ny must be >= 1");
+  if (!(d->dx > 0.0) || !(d->dy > 0.0)) return fail(JANC_E_INVALID, "dx, dy must be > 0");
+  for (int s = 0; s < 4; ++s)
+    if (d->bc[s] < 0 || d->bc[s] > 2) return fail(JANC_E_INVALID, "unknown boundary kind");
+  if ((d->bc[0] == JANC_BC_PERIODIC) != (d->bc[1] == JANC_BC_PERIODIC) ||
+      (d->bc[2] == JANC_BC_PERIODIC) != (d->bc[3] == JANC_BC_PERIODIC))
+    return fail(JANC_E_INVALID, "periodic boundaries must be set on both sides of an axis");
+  if ((d->bc[0] != JANC_BC_ZEROGRAD || d->bc[1] != JANC_BC_ZEROGRAD) && d->nx < 3)
+    return fail(JANC_E_INVALID, "wall or periodic boundaries in x need nx >= 3");
+  if ((d->bc[2] != JANC_BC_ZEROGRAD || d->bc[3] != JANC_BC_ZEROGRAD) && d->ny < 3)
+    return fail(JANC_E_INVALID, "wall or periodic boundaries in y need ny >= 3");
+  if (!(m->ns == 1 || m->ns == 3 || m->ns == 9)) return fail(JANC_E_UNSUPPORTED, "species count must be 1, 3 or 9");
+  if (m->nr < 0 || m->nr > MAX_NR) return fail(JANC_E_UNSUPPORTED, "at most 32 reactions");
+  if (!m->M || !m->nasa) return fail(JANC_E_INVALID, "null molar masses or NASA-7 table");
+  if (m->nr > 0 && (!m->A || !m->b || !m->Ea || !m->nuf || !m->nub || !m->tb || !m->eff))
+    return fail(JANC_E_INVALID, "null reaction table");
+  if (d->chemistry && (m->nr == 0 || m->ns < 3)) return fail(JANC_E_INVALID, "chemistry needs reactions and ns >= 3");
+  return JANC_OK;
+}
+
+int build_mech(const janc_mechanism* m, MechDev* h) {
+  std::memset(h, 0, sizeof(MechDev));
+  const int ns = m->ns;
+  h->ns = ns;
+  h->nr = m->nr;
+  for (int k = 0; k < ns; ++k) {
+    if (!(m->M[k] > 0.0)) return fail(JANC_E_INVALID, "molar masses must be > 0");
+    h->M[k] = m->M[k];
+    h->invM[k] = 1.0 / m->M[k];
+    const double* a = m->nasa + 7 * k;
+    for (int q = 0; q < 5; ++q) h->hc[k][q] = a[q] / (q + 1);
+    h->hc[k][5] = a[5];
+    h->gc[k][0] = a[0];
+    h->gc[k][1] = a[1] / 2.0;
+    h->gc[k][2] = a[2] / 6.0;
+    h->gc[k][3] = a[3] / 12.0;
+    h->gc[k][4] = a[4] / 20.0;
+    h->gc[k][5] = -a[5];
+    h->gc[k][6] = a[6] - a[0];
+    h->mratio[k] = m->M[k] / m->M[ns - 1];
+  }
+  for (int i = 0; i < m->nr; ++i) {
+    if (!(m->A[i] > 0.0)) return fail(JANC_E_INVALID, "Arrhenius A must be > 0");
+    h->lnA[i] = std::log(m->A[i]);
+    h->b[i] = m->b[i];
+    h->EaR[i] = m->Ea[i] / RU;
+    int nre = 0, npr = 0, dn = 0;
+    for (int j = 0; j < ns; ++j) {
+      const int f = m->nuf[i * ns + j], bb = m->nub[i * ns + j];
+      if (f < 0 || f > 3 || bb < 0 || bb > 3) return fail(JANC_E_UNSUPPORTED, "stoichiometric coefficients 0..3");
+      if (f) {
+        if (nre == MAX_SIDE) return fail(JANC_E_UNSUPPORTED, "more than 3 reactant species");
+        h->rsp[i][nre] = j;
+        h->rnu[i][nre++] = f;
+      }
+      if (bb) {
+        if (npr == MAX_SIDE) return fail(JANC_E_UNSUPPORTED, "more than 3 product species");
+        h->psp[i][npr] = j;
+        h->pnu[i][npr++] = bb;
+      }
+      dn += bb - f;
+    }
+    h->nre[i] = nre;
+    h->npr[i] = npr;
+    h->dnu[i] = dn;
+    h->tb[i] = m->tb[i] ? 1 : 0;
+    for (int j = 0; j < ns; ++j) {
+      const double e = m->tb[i] ? m->eff[i * ns + j] : 0.0;
+      h->effm1[i][j] = e - 1.0;
+    }
+    for (int l = 0; l < ns - 1; ++l) {
+      const double el = m->tb[i] ? m->eff[i * ns + l] : 0.0;
+      const double eN = m->tb[i] ? m->eff[i * ns + ns - 1] : 0.0;
+      h->ceff[i][l] = el - h->mratio[l] * eN;
+    }
+  }
+  return JANC_OK;
+}
+
+}  // namespace
+
+struct janc_grid_s {
+  janc_grid_desc d;
+  int ns, nv;
+  long long n;
+  GridDev gd;
+  Layout L;
+  char* ws;
+  bool owns_ws;
+  cudaStream_t stream;
+  double* S[3];
+  double* Fx;
+  double* Gy;
+  unsigned long long* alpha;
+  double* clock2;
+  int* status;
+  MechDev* mech;
+  int steps_done;
+  // per-kernel event timing (janc_profile)
+  bool prof_on = false;
+  struct Mark { cudaEvent_t a, b; int cls; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+cudaEvent_t take_event(janc_grid_s* g) {
+  if (!g->pool.empty()) {
+    cudaEvent_t e = g->pool.back();
+    g->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launches `f` (a callable returning cudaError_t) and, while profiling is on,
+// brackets it with events on the grid's stream.
+template <class F>
+cudaError_t timed(janc_grid_s* g, int cls, F&& f) {
+  if (!g->prof_on) return f();
+  janc_grid_s::Mark m{take_event(g), take_event(g), cls};
+  cudaEventRecord(m.a, g->stream);
+  cudaError_t e = f();
+  cudaEventRecord(m.b, g->stream);
+  g->marks.push_back(m);
+  return e;
+}
+
+}  // namespace
+
+static StateView sv(const janc_grid_s* g, int k) { return StateView{g->S[k]}; }
+
+extern "C" {
+
+const char* janc_last_error(void) { return g_err.c_str(); }
+
+int janc_workspace_bytes(const janc_grid_desc* d, const janc_mechanism* m, size_t* bytes) {
+  int rc = check_desc(d, m);
+  if (rc) return rc;
+  if (!bytes) return fail(JANC_E_INVALID, "null output");
+  *bytes = layout_of(d->nx, d->ny, m->ns + 3).total;
+  return JANC_OK;
+}
+
+int janc_create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* workspace, size_t workspace_bytes,
+                     void* cuda_stream, janc_grid_t* out) {
+  int rc = check_desc(d, m);
+  if (rc) return rc;
+  if (!out) return fail(JANC_E_INVALID, "null output handle");
+  MechDev hm;
+  rc = build_mech(m, &hm);
+  if (rc) return rc;
+  janc_grid_s* g = new janc_grid_s();
+  g->d = *d;
+  if (!(g->d.weno_eps > 0.0)) g->d.weno_eps = 1e-6;
+  if (!(g->d.newton_tol > 0.0)) g->d.newton_tol = 1e-12;
+  if (g->d.newton_maxit <= 0) g->d.newton_maxit = 50;
+  g->ns = m->ns;
+  g->nv = m->ns + 3;
+  g->n = (long long)d->nx * d->ny;
+  g->L = layout_of(d->nx, d->ny, g->nv);
+  g->stream = (cudaStream_t)cuda_stream;
+  GridDev& gd = g->gd;
+  gd.nx = d->nx;
+  gd.ny = d->ny;
+  gd.n = g->n;
+  gd.dx = d->dx;
+  gd.dy = d->dy;
+  gd.rdx = 1.0 / d->dx;
+  gd.rdy = 1.0 / d->dy;
+  for (int s = 0; s < 4; ++s) gd.bc[s] = d->bc[s];
+  gd.eps4 = 4.0 * g->d.weno_eps;
+  gd.newton_tol = g->d.newton_tol;
+  gd.newton_maxit = g->d.newton_maxit;
+  if (workspace) {
+    if (workspace_bytes < g->L.total || ((uintptr_t)workspace & 255u)) {
+      delete g;
+      return fail(JANC_E_NOMEM, "workspace too small or not 256-byte aligned");
+    }
+    g->ws = (char*)workspace;
+    g->owns_ws = false;
+  } else {
+    cudaError_t e = cudaMalloc(&g->ws, g->L.total);
+    if (e != cudaSuccess) {
+      delete g;
+      return fail(JANC_E_NOMEM, "cudaMalloc of the grid workspace failed");
+    }
+    g->owns_ws = true;
+  }
+  char* p = g->ws;
+  for (int k = 0; k < 3; ++k) { g->S[k] = (double*)p; p += g->L.state; }
+  g->Fx = (double*)p; p += g->L.fx;
+  g->Gy = (double*)p; p += g->L.gy;
+  g->alpha = (unsigned long long*)p; p += g->L.alpha;
+  g->clock2 = (double*)p; p += g->L.clock;
+  g->status = (int*)p; p += g->L.status;
+  g->mech = (MechDev*)p; p += g->L.mech;
+  cudaError_t e = cudaMemcpyAsync(g->mech, &hm, sizeof(MechDev), cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->clock2, 0, 2 * sizeof(double), g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->status, 0, sizeof(int), g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->alpha, 0, g->L.alpha, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) {
+    if (g->owns_ws) cudaFree(g->ws);
+    delete g;
+    return fail_cuda(e, "janc_create_grid");
+  }
+  g->steps_done = 0;
+  *out = g;
+  return JANC_OK;
+}
+
+void janc_destroy_grid(janc_grid_t g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  for (auto& m : g->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+  for (auto e : g->pool) cudaEventDestroy(e);
+  if (g->owns_ws) cudaFree(g->ws);
+  delete g;
+}
+
+static int copy_in(janc_grid_t g, double* dst, const double* src, size_t count, int where) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(double),
+                                  where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream);
+  if (e == cudaSuccess && where == JANC_HOST) e = cudaStreamSynchronize(g->stream);
+  return e == cudaSuccess ? JANC_OK : fail_cuda(e, "copy in");
+}
+
+static int copy_out(janc_grid_t g, double* dst, const double* src, size_t count, int where) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(double),
+                                  where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream);
+  if (e == cudaSuccess && where == JANC_HOST) e = cudaStreamSynchronize(g->stream);
+  return e == cudaSuccess ? JANC_OK : fail_cuda(e, "copy out");
+}
+
+int janc_set_state(janc_grid_t g, const double* U, const double* T0, int where) {
+  if (!g || !U) return fail(JANC_E_INVALID, "null argument");
+  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
+  int rc = copy_in(g, g->S[0], U, (size_t)g->nv * g->n, where);
+  if (rc) return rc;
+  const double* t0 = nullptr;
+  if (T0) {
+    // stage the warm start in S1's T plane
+    double* tp = g->S[1] + (size_t)g->nv * g->n;
+    rc = copy_in(g, tp, T0, (size_t)g->n, where);
+    if (rc) return rc;
+    t0 = tp;
+  }
+  cudaError_t e = cudaMemsetAsync(g->status, 0, sizeof(int), g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->alpha, 0, 2 * sizeof(unsigned long long), g->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "janc_set_state");
+  e = launch_set_conserved(g->ns, sv(g, 0), t0, g->gd, g->mech, g->alpha, g->status, g->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "set_conserved launch");
+  return JANC_OK;
+}
+
+int janc_set_state_primitive(janc_grid_t g, const double* T, const double* p, const double* u, const double* v,
+                             const double* Y, int where) {
+  if (!g || !T || !p || !u || !v || !Y) return fail(JANC_E_INVALID, "null argument");
+  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
+  const size_t n = (size_t)g->n;
+  const double *dT = T, *dp = p, *du = u, *dv = v, *dY = Y;
+  if (where == JANC_HOST) {
+    // stage through S1 (4 + ns planes fit in nv + 4 = ns + 7 planes)
+    double* base = g->S[1];
+    int rc = copy_in(g, base, T, n, where);
+    if (!rc) rc = copy_in(g, base + n, p, n, where);
+    if (!rc) rc = copy_in(g, base + 2 * n, u, n, where);
+    if (!rc) rc = copy_in(g, base + 3 * n, v, n, where);
+    if (!rc) rc = copy_in(g, base + 4 * n, Y, (size_t)g->ns * n, where);
+    if (rc) return rc;
+    dT = base; dp = base + n; du = base + 2 * n; dv = base + 3 * n; dY = base + 4 * n;
+  }
+  cudaError_t e = cudaMemsetAsync(g->status, 0, sizeof(int), g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->alpha, 0, 2 * sizeof(unsigned long long), g->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "janc_set_state_primitive");
+  e = launch_set_primitive(g->ns, sv(g, 0), dT, dp, du, dv, dY, g->gd, g->mech, g->alpha, g->status, g->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "set_primitive launch");
+  if (where == JANC_HOST) {
+    e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "set_primitive");
+  }
+  return JANC_OK;
+}
+
+int janc_step(janc_grid_t g, int n_steps, double dt, double cfl, double* t_out, double* dt_last_out) {
+  if (!g) return fail(JANC_E_INVALID, "null grid");
+  if (n_steps < 0) return fail(JANC_E_INVALID, "n_steps < 0");
+  if ((dt > 0.0) == (cfl > 0.0)) return fail(JANC_E_INVALID, "give exactly one of dt > 0 or cfl > 0");
+  StepCtl ctl;
+  ctl.dt_fixed = dt > 0.0 ? dt : 0.0;
+  ctl.cfl = cfl > 0.0 ? cfl : 0.0;
+  ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
+  double t_before = 0.0;
+  if (t_out) {
+    cudaError_t e = cudaMemcpyAsync(&t_before, g->clock2, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "janc_step clock read");
+  }
+  const StateView S0 = sv(g, 0), S1 = sv(g, 1), S2 = sv(g, 2);
+  const bool chem = g->d.chemistry != 0;
+  int done = 0;
+  while (done < n_steps) {
+    const int nc = (n_steps - done) < CHUNK ? (n_steps - done) : CHUNK;
+    cudaError_t e = cudaMemsetAsync(g->alpha + 2, 0, sizeof(unsigned long long) * 2 * SLOTS_PER_STEP * nc, g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "alpha reset");
+    for (int s = 0; s < nc; ++s) {
+      unsigned long long* a0 = g->alpha + 2 * (SLOTS_PER_STEP * s);
+      unsigned long long* a1 = a0 + 2;
+      unsigned long long* a2 = a0 + 4;
+      unsigned long long* a3 = a0 + 6;
+      unsigned long long* a4 = a0 + 8;  // next step's start
+      e = timed(g, 0, [&] { return launch_face_flux(g->nv, S0, a0, g->Fx, g->Gy, g->gd, g->stream); });
+      if (e == cudaSuccess)
+        e = timed(g, 1, [&] {
+          return launch_rk_update(g->ns, 1, S0, S0, S1, g->Fx, g->Gy, g->gd, g->mech, ctl, a0, a1, g->status,
+                                  g->clock2, g->stream);
+        });
+      if (e == cudaSuccess)
+        e = timed(g, 0, [&] { return launch_face_flux(g->nv, S1, a1, g->Fx, g->Gy, g->gd, g->stream); });
+      if (e == cudaSuccess)
+        e = timed(g, 1, [&] {
+          return launch_rk_update(g->ns, 2, S1, S0, S2, g->Fx, g->Gy, g->gd, g->mech, ctl, a0, a2, g->status,
+                                  nullptr, g->stream);
+        });
+      if (e == cudaSuccess)
+        e = timed(g, 0, [&] { return launch_face_flux(g->nv, S2, a2, g->Fx, g->Gy, g->gd, g->stream); });
+      if (e == cudaSuccess)
+        e = timed(g, 1, [&] {
+          return launch_rk_update(g->ns, 3, S2, S0, S0, g->Fx, g->Gy, g->gd, g->mech, ctl, a0, chem ? a3 : a4,
+                                  g->status, nullptr, g->stream);
+        });
+      if (e == cudaSuccess && chem)
+        e = timed(g, 2, [&] { return launch_chem(g->ns, S0, g->gd, g->mech, ctl, a0, a4, g->status, g->stream); });
+      if (e != cudaSuccess) return fail_cuda(e, "step launch");
+    }
+    // the last state's alpha becomes slot 0
+    e = cudaMemcpyAsync(g->alpha, g->alpha + 2 * (SLOTS_PER_STEP * nc), 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "alpha carry");
+    done += nc;
+  }
+  g->steps_done += n_steps;
+  if (t_out || dt_last_out) {
+    double c2[2];
+    cudaError_t e = cudaMemcpyAsync(c2, g->clock2, sizeof(c2), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "janc_step clock read");
+    if (t_out) *t_out = c2[0] - t_before;
+    if (dt_last_out) *dt_last_out = c2[1];
+  }
+  return JANC_OK;
+}
+
+int janc_get_state(janc_grid_t g, double* U, double* T, int where) {
+  if (!g) return fail(JANC_E_INVALID, "null grid");
+  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
+  int rc = JANC_OK;
+  if (U) rc = copy_out(g, U, g->S[0], (size_t)g->nv * g->n, where);
+  if (!rc && T) rc = copy_out(g, T, g->S[0] + (size_t)g->nv * g->n, (size_t)g->n, where);
+  if (rc) return rc;
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "status read");
+  if (st) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "device status word 0x%x", st);
+    return fail(JANC_E_DEVICE, buf);
+  }
+  return JANC_OK;
+}
+
+int janc_rhs(janc_grid_t g, double* Fx, double* Gy, double* L, double* alpha, int where) {
+  if (!g) return fail(JANC_E_INVALID, "null grid");
+  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
+  cudaError_t e = launch_face_flux(g->nv, sv(g, 0), g->alpha, g->Fx, g->Gy, g->gd, g->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "rhs flux launch");
+  const int nv = g->nv, nx = g->gd.nx, ny = g->gd.ny;
+  int rc = JANC_OK;
+  if (Fx) rc = copy_out(g, Fx, g->Fx, (size_t)nv * ny * (nx + 1), where);
+  if (!rc && Gy) rc = copy_out(g, Gy, g->Gy, (size_t)nv * (ny + 1) * nx, where);
+  if (!rc && L) {
+    double* tmp = g->S[1];  // nv planes of scratch
+    e = launch_rhs_L(nv, g->Fx, g->Gy, tmp, g->gd, g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "rhs L launch");
+    rc = copy_out(g, L, tmp, (size_t)nv * g->n, where);
+  }
+  if (!rc && alpha) {
+    unsigned long long a[2];
+    e = cudaMemcpyAsync(a, g->alpha, sizeof(a), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "alpha read");
+    double ad[2];
+    std::memcpy(ad, a, sizeof(ad));
+    if (where == JANC_HOST) {
+      alpha[0] = ad[0];
+      alpha[1] = ad[1];
+    } else {
+      e = cudaMemcpyAsync(alpha, ad, sizeof(ad), cudaMemcpyHostToDevice, g->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+      if (e != cudaSuccess) return fail_cuda(e, "alpha write");
+    }
+  }
+  return rc;
+}
+
+int janc_profile(janc_grid_t g, int enable) {
+  if (!g) return fail(JANC_E_INVALID, "null grid");
+  g->prof_on = enable != 0;
+  return JANC_OK;
+}
+
+int janc_profile_read(janc_grid_t g, double* ms, long long* launches) {
+  if (!g || !ms || !launches) return fail(JANC_E_INVALID, "null argument");
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "janc_profile_read");
+  for (int c = 0; c < 3; ++c) { ms[c] = 0.0; launches[c] = 0; }
+  for (auto& m : g->marks) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess && m.cls >= 0 && m.cls < 3) {
+      ms[m.cls] += t;
+      launches[m.cls] += 1;
+    }
+    g->pool.push_back(m.a);
+    g->pool.push_back(m.b);
+  }
+  g->marks.clear();
+  return JANC_OK;
+}
+
+int janc_status(janc_grid_t g, janc_status_info* s) {
+  if (!g || !s) return fail(JANC_E_INVALID, "null argument");
+  int st = 0;
+  double c2[2];
+  unsigned long long a[2];
+  cudaError_t e = cudaMemcpyAsync(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c2, g->clock2, sizeof(c2), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(a, g->alpha, sizeof(a), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "janc_status");
+  s->status = st;
+  s->steps_done = g->steps_done;
+  s->t = c2[0];
+  s->dt_last = c2[1];
+  std::memcpy(s->alpha, a, sizeof(s->alpha));
+  return JANC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+// First-order point-implicit chemistry (arXiv 2504.13750, Eq. 4.12-4.13) on
+// every cell, after the flux RK3 of the step (advance_source_term, Sec. 4.3).
+//
+// Per cell: molar concentrations X_j (the ns-th species takes what is left of
+// rho), forward rates k_f = A T^b exp(-Ea/(Ru T)) (Eq. 4.8), reverse rates
+// through the equilibrium constant of Eq. 4.9, rates of progress with the
+// third-body factor (Eq. 4.7), and the analytic Jacobian of the carried
+// sources with respect to rho Y_1..rho Y_{ns-1} at fixed T and rho (text after
+// Eq. 4.13). The linear system is solved in molar unknowns
+// dx_l = d(rho Y_l) / M_l, where it reads
+//   (I - dt J'') dx = dt wdot,  J''_kl = dWk/dX_l - (M_l / M_ns) dWk/dX_ns,
+// (row k of the mass-based system divided by M_k), with an unrolled LU
+// factorisation and partial pivoting whose search and row swaps are integer
+// compares and selects. Then Newton T for the new state, aux planes and the
+// alpha max for the next step.
+//
+// exp(G_k) is formed once per species so that each reverse rate costs a few
+// multiplications instead of a second exponential per reaction.
+#include "janc_device.cuh"
+#include "janc_internal.h"
+
+namespace janc {
+
+constexpr int CHEM_THREADS = 128;
+
+template <int NS>
+__global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, const MechDev* __restrict__ mech,
+                                                       StepCtl ctl, const unsigned long long* __restrict__ alpha_step,
+                                                       unsigned long long* alpha_out, int* status) {
+  constexpr int NSP = NS - 1;
+  constexpr int NV = NS + 3;
+  const MechDev& m = *mech;
+  const long long n = g.n;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double dt = step_dt(ctl, alpha_step);
+  unsigned long long sx = 0, sy = 0;
+  int st = 0;
+  if (idx < n) {
+    double u[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) u[k] = S.plane(k, n)[idx];
+    const double T = S.plane(NV, n)[idx];
+
+    // concentrations (Eq. 4.7 uses molar concentrations X_j)
+    double X[NS];
+    double rest = u[0];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      X[k] = u[4 + k] * m.invM[k];
+      rest -= u[4 + k];
+    }
+    X[NSP] = rest * m.invM[NSP];
+    double Ctot = X[0];
+#pragma unroll
+    for (int k = 1; k < NS; ++k) Ctot += X[k];
+
+    const double lnT = log(T);
+    const double rT = rcp(T);
+    // exp(G_k) and exp(-G_k), G_k = s_k/R - h_k/(RT) (Eq. 4.9 bracket)
+    double eG[NS], reG[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const double* c = m.gc[k];
+      const double G = fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6])));
+      eG[k] = exp(G);
+      reG[k] = rcp(eG[k]);
+    }
+    const double cref = (P_REF / RU) * rT;   // P_ref / (Ru T)
+    const double rcref = (RU / P_REF) * T;
+
+    double wd[NSP];        // molar production rates of the carried species
+    double J[NSP][NSP];    // J'' of the header comment
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      wd[k] = 0.0;
+#pragma unroll
+      for (int l = 0; l < NSP; ++l) J[k][l] = 0.0;
+    }
+
+    for (int i = 0; i < m.nr; ++i) {
+      const int nre = m.nre[i], npr = m.npr[i];
+      const double kf = exp(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
+      // k_b = k_f / K_eq,  K_eq = prod_j exp(G_j)^{nu_j} (P_ref/(Ru T))^{dnu}
+      double kb = kf;
+      for (int r = 0; r < nre; ++r)
+        for (int q = 0; q < m.rnu[i][r]; ++q) kb *= eG[m.rsp[i][r]];
+      for (int r = 0; r < npr; ++r)
+        for (int q = 0; q < m.pnu[i][r]; ++q) kb *= reG[m.psp[i][r]];
+      const int dn = m.dnu[i];
+      for (int q = 0; q < dn; ++q) kb *= rcref;
+      for (int q = 0; q < -dn; ++q) kb *= cref;
+      // law of mass action and its derivatives with respect to each participant
+      double xr[MAX_SIDE], xp[MAX_SIDE];
+      double fwd = kf, bwd = kb;
+      for (int r = 0; r < nre; ++r) {
+        xr[r] = X[m.rsp[i][r]];
+        for (int q = 0; q < m.rnu[i][r]; ++q) fwd *= xr[r];
+      }
+      for (int r = 0; r < npr; ++r) {
+        xp[r] = X[m.psp[i][r]];
+        for (int q = 0; q < m.pnu[i][r]; ++q) bwd *= xp[r];
+      }
+      double Mi = 1.0;
+      if (m.tb[i]) {
+        Mi = Ctot;
+        for (int j = 0; j < NS; ++j) Mi = fma(m.effm1[i][j], X[j], Mi);
+      }
+      const double net = fwd - bwd;
+      const double q = Mi * net;
+      // sources: wdot_k += nu_ki q
+      for (int r = 0; r < nre; ++r) {
+        const int k = m.rsp[i][r];
+        if (k < NSP) wd[k] = fma(-(double)m.rnu[i][r], q, wd[k]);
+      }
+      for (int r = 0; r < npr; ++r) {
+        const int k = m.psp[i][r];
+        if (k < NSP) wd[k] = fma((double)m.pnu[i][r], q, wd[k]);
+      }
+      // dq/dX_j for the participants (third-body factor held fixed here)
+      double dq[2 * MAX_SIDE];
+      int dsp[2 * MAX_SIDE];
+      int nd = 0;
+      for (int r = 0; r < nre; ++r) {
+        double d = kf * (double)m.rnu[i][r];
+        for (int s = 0; s < nre; ++s) {
+          const int pw = m.rnu[i][s] - (s == r ? 1 : 0);
+          for (int t = 0; t < pw; ++t) d *= xr[s];
+        }
+        dq[nd] = Mi * d;
+        dsp[nd++] = m.rsp[i][r];
+      }
+      for (int r = 0; r < npr; ++r) {
+        double d = kb * (double)m.pnu[i][r];
+        for (int s = 0; s < npr; ++s) {
+          const int pw = m.pnu[i][s] - (s == r ? 1 : 0);
+          for (int t = 0; t < pw; ++t) d *= xp[s];
+        }
+        dq[nd] = -Mi * d;
+        dsp[nd++] = m.psp[i][r];
+      }
+      // rows: every carried species with nonzero net coefficient
+      for (int side = 0; side < 2; ++side) {
+        const int cnt = side ? npr : nre;
+        for (int r = 0; r < cnt; ++r) {
+          const int k = side ? m.psp[i][r] : m.rsp[i][r];
+          if (k >= NSP) continue;
+          const double nu = side ? (double)m.pnu[i][r] : -(double)m.rnu[i][r];
+          for (int d = 0; d < nd; ++d) {
+            const int j = dsp[d];
+            const double v = nu * dq[d];
+            if (j < NSP) {
+              J[k][j] += v;
+            } else {
+#pragma unroll
+              for (int l = 0; l < NSP; ++l) J[k][l] = fma(-m.mratio[l], v, J[k][l]);
+            }
+          }
+          if (m.tb[i]) {
+            const double v = nu * net;
+#pragma unroll
+            for (int l = 0; l < NSP; ++l) J[k][l] = fma(v, m.ceff[i][l], J[k][l]);
+          }
+        }
+      }
+    }
+
+    // (I - dt J'') dx = dt wd
+    double A[NSP][NSP], b[NSP], ip[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      b[k] = dt * wd[k];
+#pragma unroll
+      for (int l = 0; l < NSP; ++l) A[k][l] = fma(-dt, J[k][l], k == l ? 1.0 : 0.0);
+    }
+    bool singular = false;
+#pragma unroll
+    for (int c = 0; c < NSP; ++c) {
+      int piv = c;
+      unsigned long long best = dbits(A[c][c]) & 0x7fffffffffffffffull;
+#pragma unroll
+      for (int r = c + 1; r < NSP; ++r) {
+        const unsigned long long v = dbits(A[r][c]) & 0x7fffffffffffffffull;
+        if (v > best) { best = v; piv = r; }
+      }
+#pragma unroll
+      for (int r = c + 1; r < NSP; ++r) {
+        const bool s = (piv == r);
+#pragma unroll
+        for (int k = c; k < NSP; ++k) {
+          const double a0 = A[c][k], a1 = A[r][k];
+          A[c][k] = s ? a1 : a0;
+          A[r][k] = s ? a0 : a1;
+        }
+        const double b0 = b[c], b1 = b[r];
+        b[c] = s ? b1 : b0;
+        b[r] = s ? b0 : b1;
+      }
+      if (best == 0ull) singular = true;
+      ip[c] = rcp(A[c][c]);
+#pragma unroll
+      for (int r = c + 1; r < NSP; ++r) {
+        const double f = A[r][c] * ip[c];
+#pragma unroll
+        for (int k = c + 1; k < NSP; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
+        b[r] = fma(-f, b[c], b[r]);
+      }
+    }
+#pragma unroll
+    for (int r = NSP - 1; r >= 0; --r) {
+      double s = b[r];
+#pragma unroll
+      for (int k = r + 1; k < NSP; ++k) s = fma(-A[r][k], b[k], s);
+      b[r] = s * ip[r];
+    }
+    if (singular) {
+      st |= ST_SINGULAR;
+    } else {
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) u[4 + k] = fma(m.M[k], b[k], u[4 + k]);
+    }
+#pragma unroll
+    for (int k = 4; k < NV; ++k) S.plane(k, n)[idx] = u[k];
+    double Tn, p, c, rrho;
+    st |= newton_cell<NS>(u, T, m, g.newton_tol, g.newton_maxit, Tn, p, c, rrho);
+    const double vx = u[1] * rrho, vy = u[2] * rrho;
+    S.plane(NV, n)[idx] = Tn;
+    S.plane(NV + 1, n)[idx] = vx;
+    S.plane(NV + 2, n)[idx] = vy;
+    S.plane(NV + 3, n)[idx] = p;
+    sx = dbits(dabs(vx) + c);
+    sy = dbits(dabs(vy) + c);
+  }
+  block_reduce_alpha_status(sx, sy, st, alpha_out, status);
+}
+
+cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
+                        const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,
+                        cudaStream_t st) {
+  const unsigned blocks = (unsigned)((g.n + CHEM_THREADS - 1) / CHEM_THREADS);
+  switch (ns) {
+    case 3: k_chem<3><<<blocks, CHEM_THREADS, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
+    case 9: k_chem<9><<<blocks, CHEM_THREADS, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace janc

@@ -1,0 +1,36 @@
+// Host-side launchers shared between the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "janc_device.cuh"
+
+namespace janc {
+
+// LF-split WENO5 face fluxes of state S (janc_flux.cu).
+cudaError_t launch_face_flux(int nv, const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
+                             const GridDev& g, cudaStream_t st);
+
+// RK3 stage `stage` (1..3): Sout = combination of S0 and Sin + dt L(Sin), then
+// Newton T warm-started from Sin's T, aux planes, and the alpha max of Sout
+// into alpha_out (janc_update.cu). alpha_step holds the step's starting alpha.
+cudaError_t launch_rk_update(int ns, int stage, const StateView& Sin, const StateView& S0, const StateView& Sout,
+                             const double* Fx, const double* Gy, const GridDev& g, const MechDev* mech,
+                             const StepCtl& ctl, const unsigned long long* alpha_step, unsigned long long* alpha_out,
+                             int* status, double* clock2, cudaStream_t st);
+
+// Point-implicit chemistry in place on S (janc_chem.cu).
+cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
+                        const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,
+                        cudaStream_t st);
+
+// State set-up kernels (janc_update.cu).
+cudaError_t launch_set_primitive(int ns, const StateView& S, const double* T, const double* p, const double* u,
+                                 const double* v, const double* Y, const GridDev& g, const MechDev* mech,
+                                 unsigned long long* alpha_out, int* status, cudaStream_t st);
+cudaError_t launch_set_conserved(int ns, const StateView& S, const double* T0, const GridDev& g, const MechDev* mech,
+                                 unsigned long long* alpha_out, int* status, cudaStream_t st);
+// L = -(dF/dx + dG/dy) from the face fluxes.
+cudaError_t launch_rhs_L(int nv, const double* Fx, const double* Gy, double* L, const GridDev& g, cudaStream_t st);
+
+}  // namespace janc

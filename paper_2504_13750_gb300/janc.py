@@ -1,0 +1,294 @@
+"""Thin Python binding of the C ABI in include/janc.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all work runs in libjanc.so. Arrays may be numpy
+arrays (host) or CUDA torch tensors (device); the ``where`` argument of the C
+call is chosen from the array type. Errors raise ``JancError`` with the
+library's message. The library must have been built (``build.build()``); a
+missing library is an error, never a silent fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+JANC_HOST, JANC_DEVICE = 0, 1
+BC_WALL, BC_ZEROGRAD, BC_PERIODIC = 0, 1, 2
+ST_NONFINITE, ST_NONPOSITIVE, ST_NEWTON_FAIL, ST_SINGULAR = 1, 2, 4, 8
+
+_lock = threading.Lock()
+_lib = None
+
+
+class JancError(RuntimeError):
+    def __init__(self, rc, msg):
+        super().__init__(f"janc error {rc}: {msg}")
+        self.rc = rc
+
+
+class janc_grid_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("bc", ctypes.c_int * 4), ("chemistry", ctypes.c_int), ("weno_eps", ctypes.c_double),
+                ("newton_tol", ctypes.c_double), ("newton_maxit", ctypes.c_int)]
+
+
+class janc_mechanism(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int), ("nr", ctypes.c_int)] + [
+        (k, ctypes.c_void_p) for k in ("M", "nasa", "A", "b", "Ea", "nuf", "nub", "tb", "eff")]
+
+
+class janc_status_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_int), ("t", ctypes.c_double),
+                ("dt_last", ctypes.c_double), ("alpha", ctypes.c_double * 2)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libjanc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: run paper_2504_13750_gb300.build.build() first")
+            L = ctypes.CDLL(path)
+            p, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            L.janc_last_error.restype = ctypes.c_char_p
+            L.janc_workspace_bytes.argtypes = [p, p, ctypes.POINTER(ctypes.c_size_t)]
+            L.janc_create_grid.argtypes = [p, p, p, ctypes.c_size_t, p, ctypes.POINTER(p)]
+            L.janc_set_state.argtypes = [p, p, p, i]
+            L.janc_set_state_primitive.argtypes = [p, p, p, p, p, p, i]
+            L.janc_step.argtypes = [p, i, d, d, p, p]
+            L.janc_get_state.argtypes = [p, p, p, i]
+            L.janc_rhs.argtypes = [p, p, p, p, p, i]
+            L.janc_status.argtypes = [p, p]
+            L.janc_destroy_grid.argtypes = [p]
+            L.janc_destroy_grid.restype = None
+            L.janc_fp64_peak.argtypes = [p, i, ctypes.POINTER(d)]
+            L.janc_selfcheck_rcp.argtypes = [p, i, ctypes.POINTER(ctypes.c_longlong)]
+            L.janc_profile.argtypes = [p, i]
+            L.janc_profile_read.argtypes = [p, p, p]
+            _lib = L
+        return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise JancError(rc, lib().janc_last_error().decode())
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _arg(a, writable=False):
+    """(pointer, where, keepalive) for a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, JANC_HOST, None
+    if _is_torch(a):
+        import torch
+
+        if not a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("device arrays must be contiguous float64 CUDA tensors")
+        return ctypes.c_void_p(a.data_ptr()), JANC_DEVICE, a
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise ValueError("host arrays must be C-contiguous float64 numpy arrays")
+    if writable and not a.flags.writeable:
+        raise ValueError("output array is read-only")
+    return a.ctypes.data_as(ctypes.c_void_p), JANC_HOST, a
+
+
+def _where(*args):
+    ws = {w for (_, w, k) in args if k is not None}
+    if len(ws) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return ws.pop() if ws else JANC_HOST
+
+
+def make_desc(nx, ny, dx, dy, bc, chemistry=True, weno_eps=1e-6, newton_tol=1e-12, newton_maxit=50):
+    d = janc_grid_desc()
+    d.nx, d.ny, d.dx, d.dy = int(nx), int(ny), float(dx), float(dy)
+    for k in range(4):
+        d.bc[k] = int(bc[k])
+    d.chemistry = int(bool(chemistry))
+    d.weno_eps, d.newton_tol, d.newton_maxit = float(weno_eps), float(newton_tol), int(newton_maxit)
+    return d
+
+
+class Mechanism:
+    """ctypes view of a mechanism dict (flat arrays, see inputs.load_mechanism)."""
+
+    def __init__(self, mech):
+        self.ns, self.nr = int(mech["ns"]), int(mech["nr"])
+        self._a = {
+            "M": np.ascontiguousarray(mech["M"], np.float64), "nasa": np.ascontiguousarray(mech["nasa"], np.float64),
+            "A": np.ascontiguousarray(mech["A"], np.float64), "b": np.ascontiguousarray(mech["b"], np.float64),
+            "Ea": np.ascontiguousarray(mech["Ea"], np.float64),
+            "nuf": np.ascontiguousarray(mech["nuf"], np.int32), "nub": np.ascontiguousarray(mech["nub"], np.int32),
+            "tb": np.ascontiguousarray(mech["tb"], np.int32), "eff": np.ascontiguousarray(mech["eff"], np.float64),
+        }
+        self.c = janc_mechanism(self.ns, self.nr, *[self._a[k].ctypes.data_as(ctypes.c_void_p) for k in
+                                                    ("M", "nasa", "A", "b", "Ea", "nuf", "nub", "tb", "eff")])
+
+
+def janc_workspace_bytes(desc, mech: Mechanism) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().janc_workspace_bytes(ctypes.byref(desc), ctypes.byref(mech.c), ctypes.byref(out)))
+    return out.value
+
+
+def janc_create_grid(desc, mech: Mechanism, workspace_ptr=None, workspace_bytes=0, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().janc_create_grid(ctypes.byref(desc), ctypes.byref(mech.c),
+                                  ctypes.c_void_p(workspace_ptr) if workspace_ptr else None,
+                                  int(workspace_bytes), ctypes.c_void_p(stream) if stream else None,
+                                  ctypes.byref(h)))
+    return h
+
+
+def janc_set_state(g, U, T0=None):
+    a, b = _arg(U), _arg(T0)
+    _check(lib().janc_set_state(g, a[0], b[0], _where(a, b)))
+
+
+def janc_set_state_primitive(g, T, p, u, v, Y):
+    args = [_arg(x) for x in (T, p, u, v, Y)]
+    _check(lib().janc_set_state_primitive(g, *[x[0] for x in args], _where(*args)))
+
+
+def janc_step(g, n_steps, dt=0.0, cfl=0.0, want_time=False):
+    """Returns (t, dt_last) when want_time (synchronises), else None."""
+    if want_time:
+        t, dl = ctypes.c_double(), ctypes.c_double()
+        _check(lib().janc_step(g, int(n_steps), float(dt), float(cfl), ctypes.byref(t), ctypes.byref(dl)))
+        return t.value, dl.value
+    _check(lib().janc_step(g, int(n_steps), float(dt), float(cfl), None, None))
+    return None
+
+
+def janc_get_state(g, U=None, T=None, check=True):
+    a, b = _arg(U, True), _arg(T, True)
+    rc = lib().janc_get_state(g, a[0], b[0], _where(a, b))
+    if check:
+        _check(rc)
+    return rc
+
+
+def janc_rhs(g, Fx=None, Gy=None, L=None, alpha=None):
+    args = [_arg(x, True) for x in (Fx, Gy, L, alpha)]
+    _check(lib().janc_rhs(g, *[x[0] for x in args], _where(*args)))
+
+
+def janc_status(g):
+    s = janc_status_info()
+    _check(lib().janc_status(g, ctypes.byref(s)))
+    return {"status": s.status, "steps_done": s.steps_done, "t": s.t, "dt_last": s.dt_last,
+            "alpha": (s.alpha[0], s.alpha[1])}
+
+
+def janc_profile(g, enable=True):
+    _check(lib().janc_profile(g, int(bool(enable))))
+
+
+KERNEL_CLASSES = ("face_flux", "rk_update", "chemistry")
+
+
+def janc_profile_read(g):
+    """{class: (ms, launches)} since the last read (synchronises)."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_longlong * 3)()
+    _check(lib().janc_profile_read(g, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p)))
+    return {KERNEL_CLASSES[c]: (ms[c], n[c]) for c in range(3)}
+
+
+def janc_last_error() -> str:
+    return lib().janc_last_error().decode()
+
+
+def janc_destroy_grid(g):
+    lib().janc_destroy_grid(g)
+
+
+def janc_fp64_peak(stream=None, n_iter=4000) -> float:
+    out = ctypes.c_double()
+    _check(lib().janc_fp64_peak(ctypes.c_void_p(stream) if stream else None, int(n_iter), ctypes.byref(out)))
+    return out.value
+
+
+def janc_selfcheck_rcp(x) -> int:
+    x = np.ascontiguousarray(x, np.float64)
+    out = ctypes.c_longlong()
+    _check(lib().janc_selfcheck_rcp(x.ctypes.data_as(ctypes.c_void_p), int(x.size), ctypes.byref(out)))
+    return out.value
+
+
+class Grid:
+    """Convenience owner of one grid: a torch workspace on the current CUDA
+    device and stream, and the C handle. Arrays go in and out as numpy (host)
+    or CUDA torch tensors (device)."""
+
+    def __init__(self, mech: dict, nx, ny, dx, dy, bc, chemistry=True, stream=None, **kw):
+        import torch
+
+        self.mech = Mechanism(mech)
+        self.ns = self.mech.ns
+        self.nv = self.ns + 3
+        self.nx, self.ny = int(nx), int(ny)
+        self.desc = make_desc(nx, ny, dx, dy, bc, chemistry=chemistry, **kw)
+        nbytes = janc_workspace_bytes(self.desc, self.mech)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.handle = janc_create_grid(self.desc, self.mech, aligned, nbytes, self.stream.cuda_stream)
+
+    @classmethod
+    def from_grid_dict(cls, mech, g, chemistry=True, **kw):
+        return cls(mech, g["nx"], g["ny"], g["dx"], g["dy"], g["bc"], chemistry=chemistry,
+                   weno_eps=g.get("weno_eps", 1e-6), newton_tol=g.get("newton_tol", 1e-12),
+                   newton_maxit=g.get("newton_maxit", 50), **kw)
+
+    def set_state(self, U, T0=None):
+        janc_set_state(self.handle, U, T0)
+
+    def set_primitive(self, T, p, u, v, Y):
+        janc_set_state_primitive(self.handle, T, p, u, v, Y)
+
+    def step(self, n, dt=0.0, cfl=0.0, want_time=False):
+        return janc_step(self.handle, n, dt=dt, cfl=cfl, want_time=want_time)
+
+    def get_state(self, check=True):
+        U = np.zeros((self.nv, self.ny, self.nx))
+        T = np.zeros((self.ny, self.nx))
+        janc_get_state(self.handle, U, T, check=check)
+        return U, T
+
+    def rhs(self):
+        Fx = np.zeros((self.nv, self.ny, self.nx + 1))
+        Gy = np.zeros((self.nv, self.ny + 1, self.nx))
+        L = np.zeros((self.nv, self.ny, self.nx))
+        al = np.zeros(2)
+        janc_rhs(self.handle, Fx, Gy, L, al)
+        return L, Fx, Gy, al
+
+    def status(self):
+        return janc_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            janc_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

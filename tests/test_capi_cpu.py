@@ -1,0 +1,81 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, and
+exports every entry point include/janc.h declares; the Python binding has a
+function of the same name for each; argument validation fails cleanly."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2504_13750_gb300 import build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "janc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(janc_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libjanc():
+    try:
+        build.nvcc()
+    except RuntimeError:
+        pytest.skip("no nvcc")
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_symbols_exported(libjanc):
+    names = declared_symbols()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(libjanc, n), n
+
+
+def test_binding_names_match_header():
+    from paper_2504_13750_gb300 import janc
+
+    for n in declared_symbols():
+        assert callable(getattr(janc, n, None)), n
+
+
+def test_workspace_and_validation_without_gpu(libjanc):
+    from paper_2504_13750_gb300 import janc
+
+    mech = janc.Mechanism(inputs.load_mechanism("h2air_synth"))
+    d = janc.make_desc(4096, 512, 1e-5, 1e-5, [0, 0, 0, 0])
+    nbytes = janc.janc_workspace_bytes(d, mech)
+    n = 4096 * 512
+    # 3 states of 16 planes + 2 face-flux arrays of 12 planes, plus small tables
+    assert 3 * 16 * n * 8 + 2 * 12 * n * 8 <= nbytes < 3 * 16 * n * 8 + 2 * 12 * (n + 4096 + 512) * 8 + (1 << 20)
+    bad = janc.make_desc(2, 4, 1e-5, 1e-5, [0, 0, 0, 0])  # walls need >= 3 cells
+    with pytest.raises(janc.JancError) as e:
+        janc.janc_workspace_bytes(bad, mech)
+    assert e.value.rc == -1 and "nx >= 3" in str(e.value)
+    m5 = inputs.load_mechanism("h2air_synth")
+    m5 = dict(m5, ns=5)
+    with pytest.raises(janc.JancError) as e:
+        janc.janc_workspace_bytes(d, janc.Mechanism({**m5, "M": m5["M"][:5], "nasa": m5["nasa"][:5]}))
+    assert e.value.rc == -2
+    per = janc.make_desc(16, 16, 1e-5, 1e-5, [2, 0, 0, 0])
+    with pytest.raises(janc.JancError):
+        janc.janc_workspace_bytes(per, mech)
+
+
+def test_oracle_and_product_share_no_code():
+    """The oracle and the CUDA path import nothing from each other."""
+    pkg = os.path.join(ROOT, "paper_2504_13750_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.findall(r"^\s*(?:import|from)\s+(\w+)", text, flags=re.M), f
+                assert "janc_oracle" not in text, f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".cpp", ".hpp")):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "csrc" not in text and "janc_device" not in text and "import janc" not in text, f
