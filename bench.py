@@ -30,7 +30,12 @@ sys.path.insert(0, ROOT)
 
 NX, NY = 4096, 512
 CFL = 0.5
-WORKLOAD = "h2air_detonation_tube_4096x512_9sp19r_cfl0.5"
+
+
+def workload_name():
+    return f"h2air_detonation_tube_{NX}x{NY}_9sp19r_cfl0.5"
+
+
 METRIC = "FP64 cell-steps/s per GB300"
 UNIT = "cell-steps/s"
 
@@ -144,7 +149,7 @@ def run_reference(args):
 
     orc.build()
     mech = inputs.load_mechanism("h2air_synth")
-    # each step: one oracle step on a 4096 x 32 slab of the same tube (the
+    # each step: one oracle step on an nx x 32 slab of the same tube (the
     # bottom rows, slip walls), so the whole run stays within minutes
     rows = 32
     st = inputs.tube(mech, NX, rows, perturb_seed=0)
@@ -163,7 +168,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "sample_rows": rows},
+        "config": {"workload": workload_name(), "nx": NX, "ny": NY, "sample_rows": rows},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -228,24 +233,26 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with pinned host buffers ----
     nv = g.nv
-    Uh = torch.empty((nv, NY, NX), dtype=torch.float64, pin_memory=True).numpy()
-    Th = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True).numpy()
-    janc.janc_get_state(g.handle, Uh, Th)
-    e2e_steps = max(3, args.steps // 4)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        janc.janc_set_state(g.handle, Uh, Th)
-        janc.janc_step(g.handle, 1, cfl=CFL)
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.empty((nv, NY, NX), dtype=torch.float64, pin_memory=True).numpy()
+        Th = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True).numpy()
         janc.janc_get_state(g.handle, Uh, Th)
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(Uh.nbytes + Th.nbytes), "d2h_bytes_per_step": int(Uh.nbytes + Th.nbytes),
-           "steps": e2e_steps}
+        e2e_steps = max(3, args.steps // 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            janc.janc_set_state(g.handle, Uh, Th)
+            janc.janc_step(g.handle, 1, cfl=CFL)
+            janc.janc_get_state(g.handle, Uh, Th)
+        e2e_s = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(Uh.nbytes + Th.nbytes), "d2h_bytes_per_step": int(Uh.nbytes + Th.nbytes),
+               "steps": e2e_steps}
 
     # ---- roofline of the dominant kernel (face fluxes: FP64-pipe bound) ----
     ff_ms, ff_n = prof["face_flux"]
@@ -273,9 +280,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "cells": cells, "species": 9, "reactions": 19,
+        "config": {"workload": workload_name(), "nx": NX, "ny": NY, "cells": cells, "species": 9, "reactions": 19,
                    "cfl": CFL, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2: each state buffer is 16 planes x 2.1 M cells = 268 MB"},
+                   "l2": f"inputs larger than L2 (129 MB): each state buffer is 16 planes x {cells} cells = {16 * 8 * cells / 1e6:.0f} MB"},
         "e2e": e2e,
         "roofline": roof,
         "roofline_hbm": roof_hbm,
@@ -300,7 +307,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nx", type=int, default=NX, help="tube cells along x (default: the 4096 x 512 workload)")
+    ap.add_argument("--ny", type=int, default=NY)
     args = ap.parse_args()
+    globals()["NX"], globals()["NY"] = args.nx, args.ny
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
