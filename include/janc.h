@@ -176,6 +176,28 @@ int janc_fp64_peak(void* cuda_stream, int n_iter, double* dfma_per_s);
  * in units in the last place. Synchronous; allocates scratch. */
 int janc_selfcheck_rcp(const double* x, int n, long long* max_ulp);
 
+/* Size of the device array behind janc_rhs_static (32 MiB per GPU). */
+#define JANC_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* Right-hand side without device allocation. The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc, such as code running
+ * inside another framework's memory pool, loops that forbid allocation after
+ * start-up, and plug-ins that only receive device buffers.
+ * Same result as janc_rhs for the state (U, T): U[nv][ny][nx] and T[ny][nx]
+ * (the Newton warm start) are device inputs, L[nv][ny][nx] and alpha[2]
+ * (may be NULL) device outputs; the caller owns all four. Scratch comes from
+ * one file-scope device array of JANC_STATIC_SCRATCH_BYTES that every GPU
+ * loading the library holds until exit; a grid whose scratch
+ * ((nv + 4) nx ny + nv (2 nx ny + nx + ny) doubles plus small tables) does
+ * not fit is rejected with JANC_E_INVALID. No allocation of any kind. The
+ * first call on each device looks up the array's device address, so make it
+ * before any stream capture. All calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller. Synchronises
+ * cuda_stream before returning; JANC_E_DEVICE if the state's Newton T
+ * recovery flagged a bad cell. */
+int janc_rhs_static(const janc_grid_desc* d, const janc_mechanism* m, const double* U, const double* T,
+                    double* L, double* alpha, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -144,6 +144,11 @@ int build_mech(const janc_mechanism* m, MechDev* h) {
 
 }  // namespace
 
+namespace janc {
+int build_mech_table(const janc_mechanism* m, MechDev* h) { return build_mech(m, h); }
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace janc
+
 struct janc_grid_s {
   janc_grid_desc d;
   int ns, nv;

@@ -3,9 +3,15 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/janc.h"
 #include "janc_device.cuh"
 
 namespace janc {
+
+// Kernel-form mechanism table from the C-ABI description (janc_capi.cu).
+int build_mech_table(const janc_mechanism* m, MechDev* h);
+// Sets the text janc_last_error() returns on this thread (janc_capi.cu).
+void set_last_error(const char* msg);
 
 // LF-split WENO5 face fluxes of state S (janc_flux.cu).
 cudaError_t launch_face_flux(int nv, const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,

@@ -74,6 +74,7 @@ def lib():
             L.janc_destroy_grid.restype = None
             L.janc_fp64_peak.argtypes = [p, i, ctypes.POINTER(d)]
             L.janc_selfcheck_rcp.argtypes = [p, i, ctypes.POINTER(ctypes.c_longlong)]
+            L.janc_rhs_static.argtypes = [p, p, p, p, p, p, p]
             L.janc_profile.argtypes = [p, i]
             L.janc_profile_read.argtypes = [p, p, p]
             _lib = L
@@ -192,6 +193,17 @@ def janc_status(g):
     _check(lib().janc_status(g, ctypes.byref(s)))
     return {"status": s.status, "steps_done": s.steps_done, "t": s.t, "dt_last": s.dt_last,
             "alpha": (s.alpha[0], s.alpha[1])}
+
+
+def janc_rhs_static(desc, mech: Mechanism, U, T, L, alpha=None, stream=None):
+    """Right-hand side with no device allocation (see include/janc.h): for
+    callers that cannot allocate, e.g. inside another framework's memory pool.
+    U, T, L (and alpha) must be CUDA tensors the caller owns."""
+    args = [_arg(x, True) for x in (U, T, L, alpha)]
+    if any(a[2] is not None and a[1] != JANC_DEVICE for a in args):
+        raise ValueError("janc_rhs_static takes device tensors only")
+    _check(lib().janc_rhs_static(ctypes.byref(desc), ctypes.byref(mech.c), args[0][0], args[1][0], args[2][0],
+                                 args[3][0], ctypes.c_void_p(stream) if stream else None))
 
 
 def janc_profile(g, enable=True):
