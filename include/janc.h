@@ -170,11 +170,17 @@ void janc_destroy_grid(janc_grid_t g);
  * (a measured FP64 peak for roofline fractions). Synchronous. */
 int janc_fp64_peak(void* cuda_stream, int n_iter, double* dfma_per_s);
 
-/* Accuracy check of the library's FP64 reciprocal (MUFU seed refined by two
- * Newton-Raphson steps) against IEEE division on the device, over the n host
+/* Accuracy check of the library's FP64 reciprocal (MUFU seed refined by one
+ * third-order iteration step) against IEEE division on the device, over the n host
  * values x (positive normal doubles): max_ulp receives the largest distance
  * in units in the last place. Synchronous; allocates scratch. */
 int janc_selfcheck_rcp(const double* x, int n, long long* max_ulp);
+
+/* Accuracy check of the library's FP64 exponential (P. T. P. Tang's
+ * table-driven method, used by the chemistry kernel) against CUDA's exp on
+ * the device, over the n host values x: max_ulp receives the largest
+ * distance in units in the last place. Synchronous; allocates scratch. */
+int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
 
 /* Size of the device array behind janc_rhs_static (32 MiB per GPU). */
 #define JANC_STATIC_SCRATCH_BYTES (32u << 20)

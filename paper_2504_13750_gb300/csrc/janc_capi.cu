@@ -129,9 +129,16 @@ int build_mech(const janc_mechanism* m, MechDev* h) {
     h->npr[i] = npr;
     h->dnu[i] = dn;
     h->tb[i] = m->tb[i] ? 1 : 0;
+    for (int r = 0; r < nre; ++r) h->rnud[i][r] = (double)h->rnu[i][r];
+    for (int r = 0; r < npr; ++r) h->pnud[i][r] = (double)h->pnu[i][r];
+    h->neff[i] = 0;
     for (int j = 0; j < ns; ++j) {
       const double e = m->tb[i] ? m->eff[i * ns + j] : 0.0;
       h->effm1[i][j] = e - 1.0;
+      if (m->tb[i] && e != 1.0) {
+        h->effsp[i][h->neff[i]] = j;
+        h->effv[i][h->neff[i]++] = e - 1.0;
+      }
     }
     for (int l = 0; l < ns - 1; ++l) {
       const double el = m->tb[i] ? m->eff[i * ns + l] : 0.0;

@@ -15,7 +15,9 @@
 // alpha max for the next step.
 //
 // exp(G_k) is formed once per species so that each reverse rate costs a few
-// multiplications instead of a second exponential per reaction.
+// multiplications instead of a second exponential per reaction; the
+// exponentials use the table-driven exp_t (about half the FP64 instructions
+// of the library exp).
 #include "janc_device.cuh"
 #include "janc_internal.h"
 
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, c
     for (int k = 0; k < NS; ++k) {
       const double* c = m.gc[k];
       const double G = fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6])));
-      eG[k] = exp(G);
+      eG[k] = exp_t(G);
       reG[k] = rcp(eG[k]);
     }
     const double cref = (P_REF / RU) * rT;   // P_ref / (Ru T)
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, c
 
     for (int i = 0; i < m.nr; ++i) {
       const int nre = m.nre[i], npr = m.npr[i];
-      const double kf = exp(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
+      const double kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
       // k_b = k_f / K_eq,  K_eq = prod_j exp(G_j)^{nu_j} (P_ref/(Ru T))^{dnu}
       double kb = kf;
       for (int r = 0; r < nre; ++r)
@@ -103,25 +105,25 @@ __global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, c
       double Mi = 1.0;
       if (m.tb[i]) {
         Mi = Ctot;
-        for (int j = 0; j < NS; ++j) Mi = fma(m.effm1[i][j], X[j], Mi);
+        for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
       }
       const double net = fwd - bwd;
       const double q = Mi * net;
       // sources: wdot_k += nu_ki q
       for (int r = 0; r < nre; ++r) {
         const int k = m.rsp[i][r];
-        if (k < NSP) wd[k] = fma(-(double)m.rnu[i][r], q, wd[k]);
+        if (k < NSP) wd[k] = fma(-m.rnud[i][r], q, wd[k]);
       }
       for (int r = 0; r < npr; ++r) {
         const int k = m.psp[i][r];
-        if (k < NSP) wd[k] = fma((double)m.pnu[i][r], q, wd[k]);
+        if (k < NSP) wd[k] = fma(m.pnud[i][r], q, wd[k]);
       }
       // dq/dX_j for the participants (third-body factor held fixed here)
       double dq[2 * MAX_SIDE];
       int dsp[2 * MAX_SIDE];
       int nd = 0;
       for (int r = 0; r < nre; ++r) {
-        double d = kf * (double)m.rnu[i][r];
+        double d = m.rnu[i][r] == 1 ? kf : kf * m.rnud[i][r];
         for (int s = 0; s < nre; ++s) {
           const int pw = m.rnu[i][s] - (s == r ? 1 : 0);
           for (int t = 0; t < pw; ++t) d *= xr[s];
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, c
         dsp[nd++] = m.rsp[i][r];
       }
       for (int r = 0; r < npr; ++r) {
-        double d = kb * (double)m.pnu[i][r];
+        double d = m.pnu[i][r] == 1 ? kb : kb * m.pnud[i][r];
         for (int s = 0; s < npr; ++s) {
           const int pw = m.pnu[i][s] - (s == r ? 1 : 0);
           for (int t = 0; t < pw; ++t) d *= xp[s];
@@ -144,13 +146,13 @@ __global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, c
         for (int r = 0; r < cnt; ++r) {
           const int k = side ? m.psp[i][r] : m.rsp[i][r];
           if (k >= NSP) continue;
-          const double nu = side ? (double)m.pnu[i][r] : -(double)m.rnu[i][r];
+          const double nu = side ? m.pnud[i][r] : -m.rnud[i][r];
           for (int d = 0; d < nd; ++d) {
             const int j = dsp[d];
-            const double v = nu * dq[d];
             if (j < NSP) {
-              J[k][j] += v;
+              J[k][j] = fma(nu, dq[d], J[k][j]);
             } else {
+              const double v = nu * dq[d];
 #pragma unroll
               for (int l = 0; l < NSP; ++l) J[k][l] = fma(-m.mratio[l], v, J[k][l]);
             }

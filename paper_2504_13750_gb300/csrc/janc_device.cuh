@@ -44,6 +44,11 @@ struct MechDev {
   int npr[MAX_NR], psp[MAX_NR][MAX_SIDE], pnu[MAX_NR][MAX_SIDE];
   int dnu[MAX_NR];  // sum of (nu_b - nu_f)
   int tb[MAX_NR];
+  double rnud[MAX_NR][MAX_SIDE], pnud[MAX_NR][MAX_SIDE];  // the coefficients as doubles
+  // Third-body factor as sum_j X_j + sum over the few species whose
+  // coefficient differs from one: neff entries of (species, eff - 1).
+  int neff[MAX_NR], effsp[MAX_NR][MAX_NS];
+  double effv[MAX_NR][MAX_NS];
   double effm1[MAX_NR][MAX_NS];  // third-body coefficient minus one
   // Column factor for the Jacobian in carried variables (text after Eq. 4.13):
   // eff_il - (M_l / M_ns) eff_i,ns for l < ns - 1.
@@ -85,17 +90,67 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return ((dbits(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
-// Reciprocal of a normal double: MUFU approximation refined by two
-// Newton-Raphson steps for 1/x (x_{k+1} = x_k (2 - d x_k), written as two
-// FMAs per step), which square the relative error each time.
+// Reciprocal of a normal double: the MUFU approximation (relative error
+// below 2^-20) refined by one third-order step of the iteration for 1/d,
+// x' = x (1 + e + e^2) with e = 1 - d x, which cubes the relative error
+// (2^-60, below double rounding) in three FMAs.
 __device__ __forceinline__ double rcp(double d) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  return r;
+  const double e = fma(-d, r, 1.0);
+  const double e2 = fma(e, e, e);
+  return fma(r, e2, r);
+}
+
+// 2^(j/64), j = 0..63, rounded to double (computed to 200 bits).
+static __device__ const double kExp2Tab[64] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0, 0x1.0874518759bc8p+0,
+    0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0, 0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0,
+    0x1.172b83c7d517bp+0, 0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0, 0x1.2d285a6e4030bp+0,
+    0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0, 0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0,
+    0x1.3dea64c123422p+0, 0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0, 0x1.56f4736b527dap+0,
+    0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0, 0x1.6247eb03a5585p+0, 0x1.6623882552225p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0, 0x1.868d99b4492edp+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0, 0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0,
+    0x1.9c49182a3f090p+0, 0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0, 0x1.bcc1e904bc1d2p+0,
+    0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0, 0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0,
+    0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0};
+
+// FP64 exponential by P. T. P. Tang's table-driven method (ACM TOMS 15(2),
+// 1989): x = (64 m + j) ln2/64 + r with |r| <= ln2/128, the reduction split
+// Cody-Waite style (L1 carries 32 significant bits, so n L1 is exact),
+// exp(r) - 1 from its Taylor series through r^5/120 (truncation below
+// 4e-17), then 2^(j/64) from the table and 2^m added to the exponent field
+// with integer instructions. 10 FP64 instructions; about 1 ulp. Results that
+// would overflow give +inf, underflow gives 0, NaN stays NaN.
+__device__ __forceinline__ double exp_t(double x) {
+  constexpr double kInv = 0x1.71547652b82fep+6;  // 64 / ln 2
+  constexpr double kL1 = 0x1.62e42fee00000p-7;   // ln 2 / 64, leading part
+  constexpr double kL2 = 0x1.a39ef35793c76p-39;  // ln 2 / 64 - kL1
+  constexpr double kMagic = 0x1.8p52;            // rounds to an integer in the low mantissa bits
+  const double t = fma(x, kInv, kMagic);
+  const int n = __double2loint(t);
+  const double nd = t - kMagic;
+  double r = fma(nd, -kL1, x);
+  r = fma(nd, -kL2, r);
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(r, q, 1.0 / 6.0);
+  q = fma(r, q, 0.5);
+  const double p = fma(r * r, q, r);
+  const double T = __ldg(&kExp2Tab[n & 63]);
+  const double y = fma(T, p, T);
+  const int m = n >> 6;
+  double out = bitsd(dbits(y) + ((unsigned long long)(long long)m << 52));
+  const unsigned xe = (unsigned)(dbits(x) >> 52) & 0x7ffu;
+  if (m > 1023) out = bitsd(0x7ff0000000000000ull);
+  if (m < -1021) out = 0.0;
+  if (xe == 0x7ffu) out = (dbits(x) & 0xfffffffffffffull) ? x : ((long long)dbits(x) < 0 ? 0.0 : x);
+  return out;
 }
 
 // dt of the step from the alpha slot of its starting state (cfl() of Sec. 4.3).

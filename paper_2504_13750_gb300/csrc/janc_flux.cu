@@ -7,9 +7,10 @@
 // rest take y-face tiles. A tile is LINES grid lines (rows for x, columns for
 // y) by FACES consecutive faces along them. Its cells, with the 5-cell stencil
 // margin, are staged in shared memory once; every thread then owns one
-// (line, variable, sign) and slides a 5-point window along its line, so the
-// first and second differences and the 13/3 S^2 part of the smoothness
-// indicators are computed once per point instead of once per face.
+// (line, variable) and slides two 5-point windows (F+ and F-) along its line,
+// so the first and second differences and the 13/3 S^2 part of the
+// smoothness indicators are computed once per point instead of once per
+// face, and each thread carries two independent dependency chains.
 //
 // Per face and sign the reconstruction costs 27 FP64 instructions plus 5 per
 // new point (Jiang-Shu weights in divide-free form, one reciprocal).
@@ -63,52 +64,65 @@ __device__ __forceinline__ double weno_face(double F2, double D1, double D2, dou
   return fma(num, rcp(den), F2);
 }
 
-// Slides the window over `nf` faces of one line and writes the reconstructed
-// half fluxes to out[0..nf).
-template <bool MINUS>
-__device__ __forceinline__ void slide_line(const double* __restrict__ Ul, const double* __restrict__ lam,
-                                           const double* __restrict__ pt, double eps4, int nf,
-                                           double* __restrict__ out) {
-  const int w0 = MINUS ? 1 : 0;
-  auto Fv = [&](int w) -> double {
-    return pt ? fma(lam[w], Ul[w], pt[w]) : lam[w] * Ul[w];
-  };
-  double F0 = Fv(w0), F1 = Fv(w0 + 1), F2 = Fv(w0 + 2), F3 = Fv(w0 + 3), F4 = Fv(w0 + 4);
-  double D1 = F1 - F0, D2 = F2 - F1, D3 = F3 - F2, D4 = F4 - F3;
-  double S1 = D2 - D1, S2 = D3 - D2, S3 = D4 - D3;
-  constexpr double c13 = 13.0 / 3.0;
-  double T1 = fma(c13 * S1, S1, eps4), T2 = fma(c13 * S2, S2, eps4), T3 = fma(c13 * S3, S3, eps4);
+// Sliding-window state of one sign along a line: the 5 split-flux values
+// F_0..F_4 of the current face held as centre F2, differences D1..D4,
+// second differences S1, S2, S3 and the shared indicator parts T1..T3.
+struct Win {
+  double F2, F3, F4, D1, D2, D3, D4, S1, S2, S3, T1, T2, T3;
+  __device__ __forceinline__ void init(double F0, double F1, double f2, double f3, double f4, double eps4) {
+    constexpr double c13 = 13.0 / 3.0;
+    F2 = f2; F3 = f3; F4 = f4;
+    D1 = F1 - F0; D2 = F2 - F1; D3 = F3 - F2; D4 = F4 - F3;
+    S1 = D2 - D1; S2 = D3 - D2; S3 = D4 - D3;
+    T1 = fma(c13 * S1, S1, eps4); T2 = fma(c13 * S2, S2, eps4); T3 = fma(c13 * S3, S3, eps4);
+  }
+  __device__ __forceinline__ void push(double Fn, double eps4) {
+    constexpr double c13 = 13.0 / 3.0;
+    const double Dn = Fn - F4;
+    F2 = F3; F3 = F4; F4 = Fn;
+    D1 = D2; D2 = D3; D3 = D4; D4 = Dn;
+    S1 = S2; S2 = S3; S3 = D4 - D3;
+    T1 = T2; T2 = T3; T3 = fma(c13 * S3, S3, eps4);
+  }
+};
+
+// One (variable, line): reconstructs F+ (window starting at cell w = 0) and
+// F- (window starting at w = 1) at every face of the line, two independent
+// dependency chains per thread, and stores F^ = F+^ + F-^ at out[t * stride].
+__device__ __forceinline__ void slide_line2(const double* __restrict__ Ul, const double* __restrict__ lp,
+                                            const double* __restrict__ lm, const double* __restrict__ pt,
+                                            double eps4, int nf, double* __restrict__ out, long long stride) {
+  auto Fp = [&](int w) -> double { return pt ? fma(lp[w], Ul[w], pt[w]) : lp[w] * Ul[w]; };
+  auto Fm = [&](int w) -> double { return pt ? fma(lm[w], Ul[w], pt[w]) : lm[w] * Ul[w]; };
+  Win P, M;
+  P.init(Fp(0), Fp(1), Fp(2), Fp(3), Fp(4), eps4);
+  M.init(Fm(1), Fm(2), Fm(3), Fm(4), Fm(5), eps4);
   for (int t = 0; t < nf; ++t) {
-    out[t] = weno_face<MINUS>(F2, D1, D2, D3, D4, S1, S3, T1, T2, T3);
+    const double rp = weno_face<false>(P.F2, P.D1, P.D2, P.D3, P.D4, P.S1, P.S3, P.T1, P.T2, P.T3);
+    const double rm = weno_face<true>(M.F2, M.D1, M.D2, M.D3, M.D4, M.S1, M.S3, M.T1, M.T2, M.T3);
+    out[(long long)t * stride] = rp + rm;
     if (t + 1 < nf) {
-      const double Fn = Fv(w0 + t + 5);
-      F2 = F3;
-      F3 = F4;
-      const double Dn = Fn - F4;
-      F4 = Fn;
-      D1 = D2; D2 = D3; D3 = D4; D4 = Dn;
-      S1 = S2; S2 = S3; S3 = D4 - D3;
-      T1 = T2; T2 = T3; T3 = fma(c13 * S3, S3, eps4);
+      P.push(Fp(t + 5), eps4);
+      M.push(Fm(t + 6), eps4);
     }
   }
 }
 
 template <int NV>
-__global__ void __launch_bounds__(16 * NV) k_face_flux(StateView S, const unsigned long long* __restrict__ alpha,
-                                                       double* __restrict__ Fx, double* __restrict__ Gy, GridDev g,
-                                                       int nbx, int ntx_x, int ntx_y) {
+__global__ void __launch_bounds__(LINES * NV) k_face_flux(StateView S, const unsigned long long* __restrict__ alpha,
+                                                          double* __restrict__ Fx, double* __restrict__ Gy,
+                                                          GridDev g, int nbx, int ntx_x, int ntx_y) {
   extern __shared__ double smem[];
   double* sU = smem;                       // [NV][LINES][WIN]
   double* sLp = sU + NV * LINES * WIN;     // lambda+ = (u_n + alpha) / 2
   double* sLm = sLp + LINES * WIN;         // lambda- = (u_n - alpha) / 2
   double* sHp = sLm + LINES * WIN;         // p / 2
   double* sHpu = sHp + LINES * WIN;        // p u_n / 2
-  double* sR = sHpu + LINES * WIN;         // [2][NV][LINES][FACES] half fluxes
 
   const bool xdir = (int)blockIdx.x < nbx;
   const int tile = xdir ? blockIdx.x : blockIdx.x - nbx;
   const int ntl = xdir ? ntx_x : ntx_y;
-  const int ta = tile % ntl;  // tile index along the lines' perpendicular / along direction
+  const int ta = tile % ntl;
   const int tb = tile / ntl;
   const long long n = g.n;
   const int nx = g.nx, ny = g.ny;
@@ -155,40 +169,25 @@ __global__ void __launch_bounds__(16 * NV) k_face_flux(StateView S, const unsign
   }
   __syncthreads();
 
-  // ---- reconstruct: thread = (sign, variable, line) ----
+  // ---- reconstruct and store: thread = (variable, line), both signs ----
   const int nf = min(FACES, nfaces - f0);
-  const int tid = threadIdx.x;
-  const int sign = tid / (NV * LINES);
-  const int rem = tid % (NV * LINES);
-  const int var = rem / LINES;
-  const int line = rem % LINES;
-  if (l0 + line < nlines) {
+  const int var = threadIdx.x / LINES;
+  const int line = threadIdx.x % LINES;
+  const int lg = l0 + line;
+  if (lg < nlines) {
     const double* Ul = sU + (var * LINES + line) * WIN;
     const double* pt = (var == nmom) ? sHp + line * WIN : (var == 3 ? sHpu + line * WIN : nullptr);
-    double* out = sR + ((sign * NV + var) * LINES + line) * FACES;
-    if (sign == 0) slide_line<false>(Ul, sLp + line * WIN, pt, g.eps4, nf, out);
-    else slide_line<true>(Ul, sLm + line * WIN, pt, g.eps4, nf, out);
-  }
-  __syncthreads();
-
-  // ---- write F^ = F+^ + F-^ (coalesced along the faces for x, lines for y) ----
-  for (int q = threadIdx.x; q < NV * LINES * FACES; q += nthr) {
-    int var2, line2, t;
-    if (xdir) { t = q % FACES; line2 = (q / FACES) % LINES; var2 = q / (FACES * LINES); }
-    else { line2 = q % LINES; t = (q / LINES) % FACES; var2 = q / (FACES * LINES); }
-    if (t >= nf || l0 + line2 >= nlines) continue;
-    const double vp = sR[((0 * NV + var2) * LINES + line2) * FACES + t];
-    const double vm = sR[((1 * NV + var2) * LINES + line2) * FACES + t];
-    const int f = f0 + t;
-    const int lg = l0 + line2;
-    if (xdir) Fx[((long long)var2 * ny + lg) * (nx + 1) + f] = vp + vm;
-    else Gy[((long long)var2 * (ny + 1) + f) * nx + lg] = vp + vm;
+    double* out;
+    long long stride;
+    if (xdir) { out = Fx + ((long long)var * ny + lg) * (nx + 1) + f0; stride = 1; }
+    else { out = Gy + ((long long)var * (ny + 1) + f0) * nx + lg; stride = nx; }
+    slide_line2(Ul, sLp + line * WIN, sLm + line * WIN, pt, g.eps4, nf, out, stride);
   }
 }
 
 template <int NV>
 static size_t flux_smem_bytes() {
-  return sizeof(double) * ((size_t)(NV + 4) * LINES * WIN + 2ull * NV * LINES * FACES);
+  return sizeof(double) * (size_t)(NV + 4) * LINES * WIN;
 }
 
 template <int NV>
@@ -207,7 +206,7 @@ static cudaError_t launch_face_flux_t(const StateView& S, const unsigned long lo
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_face_flux<NV><<<nbx + nby, 16 * NV, smem, st>>>(S, alpha, Fx, Gy, g, nbx, ntx_x, ntx_y);
+  k_face_flux<NV><<<nbx + nby, LINES * NV, smem, st>>>(S, alpha, Fx, Gy, g, nbx, ntx_x, ntx_y);
   return cudaGetLastError();
 }
 

@@ -33,6 +33,16 @@ __global__ void k_rcp_check(const double* __restrict__ x, int n, unsigned long l
   atomicMax(max_ulp, d);
 }
 
+__global__ void k_exp_check(const double* __restrict__ x, int n, unsigned long long* max_ulp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double r = exp_t(x[i]);
+  const double q = exp(x[i]);
+  long long a = __double_as_longlong(r), b = __double_as_longlong(q);
+  unsigned long long d = (unsigned long long)(a > b ? a - b : b - a);
+  atomicMax(max_ulp, d);
+}
+
 }  // namespace
 
 extern "C" {
@@ -64,7 +74,7 @@ int janc_fp64_peak(void* cuda_stream, int n_iter, double* dfma_per_s) {
   return JANC_OK;
 }
 
-int janc_selfcheck_rcp(const double* x_host, int n, long long* max_ulp) {
+static int run_check(const double* x_host, int n, long long* max_ulp, bool is_exp) {
   if (!x_host || n <= 0 || !max_ulp) return JANC_E_INVALID;
   double* dx = nullptr;
   unsigned long long* dm = nullptr;
@@ -73,7 +83,8 @@ int janc_selfcheck_rcp(const double* x_host, int n, long long* max_ulp) {
   cudaError_t e = cudaMemcpy(dx, x_host, sizeof(double) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(dm, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) {
-    k_rcp_check<<<(n + 255) / 256, 256>>>(dx, n, dm);
+    if (is_exp) k_exp_check<<<(n + 255) / 256, 256>>>(dx, n, dm);
+    else k_rcp_check<<<(n + 255) / 256, 256>>>(dx, n, dm);
     e = cudaGetLastError();
   }
   unsigned long long h = 0;
@@ -83,6 +94,14 @@ int janc_selfcheck_rcp(const double* x_host, int n, long long* max_ulp) {
   if (e != cudaSuccess) return JANC_E_CUDA;
   *max_ulp = (long long)h;
   return JANC_OK;
+}
+
+int janc_selfcheck_exp(const double* x_host, int n, long long* max_ulp) {
+  return run_check(x_host, n, max_ulp, true);
+}
+
+int janc_selfcheck_rcp(const double* x_host, int n, long long* max_ulp) {
+  return run_check(x_host, n, max_ulp, false);
 }
 
 }  // extern "C"

@@ -75,6 +75,7 @@ def lib():
             L.janc_fp64_peak.argtypes = [p, i, ctypes.POINTER(d)]
             L.janc_selfcheck_rcp.argtypes = [p, i, ctypes.POINTER(ctypes.c_longlong)]
             L.janc_rhs_static.argtypes = [p, p, p, p, p, p, p]
+            L.janc_selfcheck_exp.argtypes = [p, i, ctypes.POINTER(ctypes.c_longlong)]
             L.janc_profile.argtypes = [p, i]
             L.janc_profile_read.argtypes = [p, p, p]
             _lib = L
@@ -239,6 +240,13 @@ def janc_selfcheck_rcp(x) -> int:
     x = np.ascontiguousarray(x, np.float64)
     out = ctypes.c_longlong()
     _check(lib().janc_selfcheck_rcp(x.ctypes.data_as(ctypes.c_void_p), int(x.size), ctypes.byref(out)))
+    return out.value
+
+
+def janc_selfcheck_exp(x) -> int:
+    x = np.ascontiguousarray(x, np.float64)
+    out = ctypes.c_longlong()
+    _check(lib().janc_selfcheck_exp(x.ctypes.data_as(ctypes.c_void_p), int(x.size), ctypes.byref(out)))
     return out.value
 
 

@@ -196,3 +196,10 @@ def test_status_word_reports_bad_state(J):
 def test_fp64_peak_probe(J):
     r = J.janc_fp64_peak(n_iter=2000)
     assert 1e11 < r < 1e13
+
+
+def test_exponential_within_two_ulp(J):
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(-700, 700, 100000), rng.uniform(-40, 40, 100000), rng.normal(0, 1e-3, 10000),
+                        np.linspace(-30, 30, 6001)])
+    assert J.janc_selfcheck_exp(x) <= 2
