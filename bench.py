@@ -177,6 +177,85 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+def serve_stream(janc, mech_c, reqs, states, arrivals, max_active, pool_bytes, stream):
+    """Replays the request stream in real time through one server: a request
+    is submitted once its arrival time has passed. Returns per-request
+    latencies (completion - arrival, s) and the makespan."""
+    s = janc.janc_server_create(mech_c, chemistry=True, pool_bytes=pool_bytes, max_active=max_active,
+                                stream=stream.cuda_stream)
+    try:
+        n = len(reqs)
+        ids = [None] * n
+        done_t = [None] * n
+        nxt = 0
+        t0 = time.perf_counter()
+        finished = 0
+        while finished < n:
+            now = time.perf_counter() - t0
+            while nxt < n and arrivals[nxt] <= now:
+                st, rq = states[nxt], reqs[nxt]
+                g = st["grid"]
+                d = janc.make_desc(g["nx"], g["ny"], g["dx"], g["dy"], g["bc"], chemistry=True)
+                ids[nxt] = janc.janc_server_submit(s, d, st["T"], st["p"], st["u"], st["v"], st["Y"], rq["steps"],
+                                                   cfl=CFL)
+                nxt += 1
+            info = janc.janc_server_run(s, 1)
+            now = time.perf_counter() - t0
+            for k in range(nxt):
+                if done_t[k] is None and ids[k] is not None:
+                    r = janc.janc_server_poll(s, ids[k])
+                    if r["state"] in (janc.REQ_DONE, janc.REQ_FAILED):
+                        if r["state"] == janc.REQ_FAILED or r["status"] != 0:
+                            raise RuntimeError(f"request {k} failed with status {r['status']}")
+                        done_t[k] = now
+                        finished += 1
+                        janc.janc_server_fetch(s, ids[k])
+            if info["n_active"] == 0 and info["n_queued"] == 0 and info["n_copying"] == 0 and nxt < n:
+                time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.01)))
+        lat = [done_t[k] - arrivals[k] for k in range(n)]
+        return lat, max(done_t) - arrivals[0]
+    finally:
+        janc.janc_server_destroy(s)
+
+
+def run_serving(janc, stream, n_req, steps_range, seed=1):
+    """Serving leg: solves of mixed size and mixture arriving as a Poisson
+    stream at 1.5x the one-at-a-time capacity, served by the batched server
+    and by a one-slot server running the same kernels."""
+    from paper_2504_13750_gb300 import inputs
+
+    mech = inputs.load_mechanism("h2air_synth")
+    mech_c = janc.Mechanism(mech)
+    reqs = inputs.serving_requests(mech, n=n_req, seed=seed, steps_range=steps_range)
+    states = [inputs.request_state(mech, r) for r in reqs]
+    cell_steps = [r["nx"] * r["ny"] * r["steps"] for r in reqs]
+    pool = 16 << 30
+    zero = [0.0] * n_req
+    # closed system (everything queued at t = 0): the capacity of each mode
+    _, span_seq = serve_stream(janc, mech_c, reqs, states, zero, 1, pool, stream)
+    _, span_bat = serve_stream(janc, mech_c, reqs, states, zero, 256, pool, stream)
+    cap_seq = n_req / span_seq
+    # open system: Poisson arrivals at 1.5x the one-at-a-time capacity
+    rate = 1.5 * cap_seq
+    rng = np.random.default_rng(seed + 100)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    arrivals = list(arrivals - arrivals[0])
+    out = {"requests": n_req, "steps_range": list(steps_range), "grids": [list(g) for g in inputs.SERVING_GRIDS],
+           "cell_steps": int(sum(cell_steps)),
+           "capacity_solves_per_s": {"batched": n_req / span_bat, "one_at_a_time": cap_seq},
+           "capacity_cell_steps_per_s": {"batched": sum(cell_steps) / span_bat,
+                                         "one_at_a_time": sum(cell_steps) / span_seq},
+           "offered_rate_per_s": rate, "offered_load_vs_one_at_a_time": 1.5}
+    for name, slots in (("batched", 256), ("one_at_a_time", 1)):
+        lat, span = serve_stream(janc, mech_c, reqs, states, arrivals, slots, pool, stream)
+        out[name] = {"solves_per_s": n_req / span, "cell_steps_per_s": sum(cell_steps) / span,
+                     "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                     "makespan_s": span, "max_active": slots}
+    out["batched_vs_one_at_a_time_solves"] = out["batched"]["solves_per_s"] / out["one_at_a_time"]["solves_per_s"]
+    out["batched_vs_one_at_a_time_capacity"] = span_seq / span_bat
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -293,6 +372,8 @@ def run_ours(args):
         "t_sim_s": stt["t"],
     }
     g.close()
+    if not args.no_serving:
+        line["serving"] = run_serving(janc, stream, args.serving_requests, tuple(args.serving_steps))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
@@ -308,6 +389,10 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=32,
+                    help="requests in the serving leg (the full stream is 256 with --serving-steps 100 1000)")
+    ap.add_argument("--serving-steps", type=int, nargs=2, default=(50, 150))
     ap.add_argument("--nx", type=int, default=NX, help="tube cells along x (default: the 4096 x 512 workload)")
     ap.add_argument("--ny", type=int, default=NY)
     args = ap.parse_args()

@@ -182,6 +182,76 @@ int janc_selfcheck_rcp(const double* x, int n, long long* max_ulp);
  * distance in units in the last place. Synchronous; allocates scratch. */
 int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching server: many independent solves of one mechanism on
+ * one GPU. Each request is a grid (janc_grid_desc) with primitive initial
+ * fields, a step count and dt or cfl; it advances by advance_one_step
+ * (Sec. 4.3) exactly as janc_step would run it alone. Requests are queued,
+ * admitted in arrival order (skipping ahead over ones that do not fit) when
+ * their device footprint fits the free part of the server's HBM pool and one
+ * of max_active slots is free, then advanced together: every janc_server_run
+ * macro-step moves each active request one step with one batched persistent
+ * kernel per phase over all of them. A finished request leaves the active set
+ * at once; its result goes to pinned host memory on a second stream and its
+ * pool memory is reused when that copy is done. Single host thread.
+ * ---------------------------------------------------------------------- */
+typedef struct janc_server_s* janc_server_t;
+
+#define JANC_REQ_QUEUED 0
+#define JANC_REQ_ACTIVE 1
+#define JANC_REQ_COPYING 2
+#define JANC_REQ_DONE 3
+#define JANC_REQ_FAILED 4
+#define JANC_REQ_FETCHED 5
+
+typedef struct {
+  int n_queued, n_active, n_copying, n_done;
+  size_t pool_used, pool_bytes;
+  long long macro_steps;
+} janc_server_info;
+
+typedef struct {
+  int state;          /* JANC_REQ_* */
+  int steps_done, n_steps;
+  int status;         /* device status word of the finished request */
+  double t, dt_last;  /* simulated time and last dt of the finished request */
+  double latency_s;   /* completion - submission (host clock), -1 before */
+  double queue_s;     /* admission - submission, -1 before */
+} janc_request_info;
+
+/* Create a server. pool_bytes of device memory hold all admitted requests
+ * (pass a 256-byte aligned caller allocation in `pool`, or NULL to let the
+ * server allocate it); max_active bounds the active set; chemistry as in
+ * janc_grid_desc and shared by every request. */
+int janc_server_create(const janc_mechanism* m, int chemistry, size_t pool_bytes, void* pool, int max_active,
+                       void* cuda_stream, janc_server_t* out);
+
+/* Device bytes a request of this grid occupies while active. */
+int janc_server_footprint(janc_server_t s, const janc_grid_desc* d, size_t* bytes);
+
+/* Queue a request: primitive initial fields (host) T, p, u, v [ny][nx] and
+ * Y [ns][ny][nx] (copied at once), n_steps > 0 and exactly one of dt > 0 or
+ * cfl > 0. *id receives the request id. JANC_E_NOMEM if the request can
+ * never fit the pool. */
+int janc_server_submit(janc_server_t s, const janc_grid_desc* d, const double* T, const double* p, const double* u,
+                       const double* v, const double* Y, int n_steps, double dt, double cfl, int* id);
+
+/* Run up to macro_steps macro-steps (admission, one batched step of every
+ * active request, retirement); stops early when nothing is active or queued.
+ * Asynchronous with respect to the GPU except for admission bookkeeping. */
+int janc_server_run(janc_server_t s, int macro_steps, janc_server_info* info);
+
+/* State and timing of one request. */
+int janc_server_poll(janc_server_t s, int id, janc_request_info* r);
+
+/* Copy a finished request's final U [nv][ny][nx] and T [ny][nx] to host
+ * memory (either may be NULL) and release it. JANC_E_DEVICE if its status
+ * word was non-zero (after copying). */
+int janc_server_fetch(janc_server_t s, int id, double* U, double* T);
+
+/* Release the server (waits for its streams). */
+void janc_server_destroy(janc_server_t s);
+
 /* Size of the device array behind janc_rhs_static (32 MiB per GPU). */
 #define JANC_STATIC_SCRATCH_BYTES (32u << 20)
 

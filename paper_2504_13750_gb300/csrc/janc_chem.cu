@@ -25,15 +25,17 @@ namespace janc {
 
 constexpr int CHEM_THREADS = 128;
 
+// One CHEM_THREADS block `blk` of cells; shared by the single-grid and the
+// batched kernels.
 template <int NS>
-__global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, const MechDev* __restrict__ mech,
-                                                       StepCtl ctl, const unsigned long long* __restrict__ alpha_step,
-                                                       unsigned long long* alpha_out, int* status) {
+__device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g, const MechDev* __restrict__ mech,
+                                           const StepCtl& ctl, const unsigned long long* __restrict__ alpha_step,
+                                           unsigned long long* alpha_out, int* status, long long blk) {
   constexpr int NSP = NS - 1;
   constexpr int NV = NS + 3;
   const MechDev& m = *mech;
   const long long n = g.n;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long idx = blk * CHEM_THREADS + threadIdx.x;
   const double dt = step_dt(ctl, alpha_step);
   unsigned long long sx = 0, sy = 0;
   int st = 0;
@@ -234,6 +236,43 @@ __global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, c
   }
   block_reduce_alpha_status(sx, sy, st, alpha_out, status);
 }
+
+template <int NS>
+__global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, const MechDev* __restrict__ mech,
+                                                       StepCtl ctl, const unsigned long long* __restrict__ alpha_step,
+                                                       unsigned long long* alpha_out, int* status) {
+  chem_block<NS>(S, g, mech, ctl, alpha_step, alpha_out, status, blockIdx.x);
+}
+
+// Batched chemistry over the flattened (request, block) list: in place on
+// each request's S[0], output alpha in slot 4.
+template <int NS>
+__global__ void __launch_bounds__(CHEM_THREADS) k_chem_batch(const BatchReq* __restrict__ reqs,
+                                                             const int* __restrict__ first, int nreq) {
+  const int total = first[nreq];
+  for (int e = blockIdx.x; e < total; e += gridDim.x) {
+    const int r = batch_owner(first, nreq, e);
+    const BatchReq& q = reqs[r];
+    chem_block<NS>(q.S[0], q.g, q.mech, q.ctl, q.alpha, q.alpha + 8, q.status, e - first[r]);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = total < sms * 16 ? total : sms * 16;
+  if (grid <= 0) return cudaSuccess;
+  switch (ns) {
+    case 3: k_chem_batch<3><<<grid, CHEM_THREADS, 0, st>>>(reqs, first, nreq); break;
+    case 9: k_chem_batch<9><<<grid, CHEM_THREADS, 0, st>>>(reqs, first, nreq); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int chem_blocks(const GridDev& g) { return (int)((g.n + CHEM_THREADS - 1) / CHEM_THREADS); }
 
 cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
                         const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,

@@ -81,6 +81,23 @@ struct StepCtl {
   double hmin;  // min(dx, dy)
 };
 
+// One request of a batched (serving) launch: its grid constants and buffers.
+// Alpha slots (2 x u64 each): 0 = U^n, 1 = U^1, 2 = U^2, 3 = U^*, 4 = U^{n+1}.
+struct BatchReq {
+  GridDev g;
+  StateView S[3];
+  double* Fx;
+  double* Gy;
+  unsigned long long* alpha;
+  double* clock2;
+  int* status;
+  const MechDev* mech;
+  StepCtl ctl;
+  int nbx, ntx_x, ntx_y;  // face-flux tiling
+  int ubx, uby;           // update-kernel blocks in x and y
+  int fresh;              // 1 until the first batched step after admission
+};
+
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
@@ -175,6 +192,17 @@ __device__ __forceinline__ int ghost_src(int i, int n, int bc_lo, int bc_hi, boo
     return i - n;
   }
   return i;
+}
+
+// Request that owns entry e of a flattened list with per-request starts
+// first[0..nreq] (first[0] = 0): the last r with first[r] <= e.
+__device__ __forceinline__ int batch_owner(const int* __restrict__ first, int nreq, int e) {
+  int lo = 0, hi = nreq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 // Block-wide max of two non-negative doubles (as bits) and OR of a status

@@ -108,19 +108,20 @@ __device__ __forceinline__ void slide_line2(const double* __restrict__ Ul, const
   }
 }
 
+// One tile of the face-flux launch; `blk` is the tile's index in the
+// launch (x tiles first). Shared by the single-grid and the batched kernels.
 template <int NV>
-__global__ void __launch_bounds__(LINES * NV) k_face_flux(StateView S, const unsigned long long* __restrict__ alpha,
-                                                          double* __restrict__ Fx, double* __restrict__ Gy,
-                                                          GridDev g, int nbx, int ntx_x, int ntx_y) {
-  extern __shared__ double smem[];
+__device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigned long long* __restrict__ alpha,
+                                               double* __restrict__ Fx, double* __restrict__ Gy, const GridDev& g,
+                                               int blk, int nbx, int ntx_x, int ntx_y, double* smem) {
   double* sU = smem;                       // [NV][LINES][WIN]
   double* sLp = sU + NV * LINES * WIN;     // lambda+ = (u_n + alpha) / 2
   double* sLm = sLp + LINES * WIN;         // lambda- = (u_n - alpha) / 2
   double* sHp = sLm + LINES * WIN;         // p / 2
   double* sHpu = sHp + LINES * WIN;        // p u_n / 2
 
-  const bool xdir = (int)blockIdx.x < nbx;
-  const int tile = xdir ? blockIdx.x : blockIdx.x - nbx;
+  const bool xdir = blk < nbx;
+  const int tile = xdir ? blk : blk - nbx;
   const int ntl = xdir ? ntx_x : ntx_y;
   const int ta = tile % ntl;
   const int tb = tile / ntl;
@@ -186,6 +187,30 @@ __global__ void __launch_bounds__(LINES * NV) k_face_flux(StateView S, const uns
 }
 
 template <int NV>
+__global__ void __launch_bounds__(LINES * NV) k_face_flux(StateView S, const unsigned long long* __restrict__ alpha,
+                                                          double* __restrict__ Fx, double* __restrict__ Gy,
+                                                          GridDev g, int nbx, int ntx_x, int ntx_y) {
+  extern __shared__ double smem[];
+  face_flux_tile<NV>(S, alpha, Fx, Gy, g, blockIdx.x, nbx, ntx_x, ntx_y, smem);
+}
+
+// Batched form: a persistent grid walks the flattened (request, tile) list;
+// request r owns entries [first[r], first[r+1]).
+template <int NV>
+__global__ void __launch_bounds__(LINES * NV) k_face_flux_batch(const BatchReq* __restrict__ reqs,
+                                                                const int* __restrict__ first, int nreq, int state) {
+  extern __shared__ double smem[];
+  const int total = first[nreq];
+  for (int e = blockIdx.x; e < total; e += gridDim.x) {
+    const int r = batch_owner(first, nreq, e);
+    const BatchReq& q = reqs[r];
+    face_flux_tile<NV>(q.S[state], q.alpha + 2 * state, q.Fx, q.Gy, q.g, e - first[r], q.nbx, q.ntx_x, q.ntx_y,
+                       smem);
+    __syncthreads();
+  }
+}
+
+template <int NV>
 static size_t flux_smem_bytes() {
   return sizeof(double) * (size_t)(NV + 4) * LINES * WIN;
 }
@@ -208,6 +233,43 @@ static cudaError_t launch_face_flux_t(const StateView& S, const unsigned long lo
   }
   k_face_flux<NV><<<nbx + nby, LINES * NV, smem, st>>>(S, alpha, Fx, Gy, g, nbx, ntx_x, ntx_y);
   return cudaGetLastError();
+}
+
+void face_flux_tiles(const GridDev& g, int* nbx, int* ntx_x, int* ntx_y, int* total) {
+  *ntx_x = (g.nx + 1 + FACES - 1) / FACES;
+  const int nty_x = (g.ny + LINES - 1) / LINES;
+  *ntx_y = (g.nx + LINES - 1) / LINES;
+  const int nty_y = (g.ny + 1 + FACES - 1) / FACES;
+  *nbx = *ntx_x * nty_x;
+  *total = *nbx + *ntx_y * nty_y;
+}
+
+template <int NV>
+static cudaError_t launch_face_flux_batch_t(const BatchReq* reqs, const int* first, int nreq, int total, int state,
+                                            cudaStream_t st) {
+  const size_t smem = flux_smem_bytes<NV>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_face_flux_batch<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = total < sms * 8 ? total : sms * 8;
+  if (grid > 0) k_face_flux_batch<NV><<<grid, LINES * NV, smem, st>>>(reqs, first, nreq, state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_flux_batch(int nv, const BatchReq* reqs, const int* first, int nreq, int total, int state,
+                                   cudaStream_t st) {
+  switch (nv) {
+    case 4: return launch_face_flux_batch_t<4>(reqs, first, nreq, total, state, st);
+    case 6: return launch_face_flux_batch_t<6>(reqs, first, nreq, total, state, st);
+    case 12: return launch_face_flux_batch_t<12>(reqs, first, nreq, total, state, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_face_flux(int nv, const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,

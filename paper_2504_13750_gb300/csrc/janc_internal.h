@@ -36,6 +36,18 @@ cudaError_t launch_set_primitive(int ns, const StateView& S, const double* T, co
                                  unsigned long long* alpha_out, int* status, cudaStream_t st);
 cudaError_t launch_set_conserved(int ns, const StateView& S, const double* T0, const GridDev& g, const MechDev* mech,
                                  unsigned long long* alpha_out, int* status, cudaStream_t st);
+// Batched launches over a flattened (request, block) list; first[0..nreq]
+// holds each request's first entry, first[nreq] the total (device memory).
+void face_flux_tiles(const GridDev& g, int* nbx, int* ntx_x, int* ntx_y, int* total);
+void update_blocks(const GridDev& g, int* ubx, int* uby);
+int chem_blocks(const GridDev& g);
+cudaError_t launch_batch_prep(BatchReq* reqs, int nreq, cudaStream_t st);
+cudaError_t launch_face_flux_batch(int nv, const BatchReq* reqs, const int* first, int nreq, int total, int state,
+                                   cudaStream_t st);
+cudaError_t launch_rk_update_batch(int ns, int stage, const BatchReq* reqs, const int* first, int nreq, int total,
+                                   int chem, cudaStream_t st);
+cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, cudaStream_t st);
+
 // L = -(dF/dx + dG/dy) from the face fluxes.
 cudaError_t launch_rhs_L(int nv, const double* Fx, const double* Gy, double* L, const GridDev& g, cudaStream_t st);
 

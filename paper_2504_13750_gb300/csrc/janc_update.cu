@@ -25,20 +25,21 @@ __device__ __forceinline__ void finish_cell(const StateView& S, long long n, lon
   sy = dbits(dabs(vy) + c);
 }
 
+// One UPD_BX x UPD_BY block (bx, by) of the stage update; shared by the
+// single-grid and the batched kernels.
 template <int NS, int STAGE>
-__global__ void __launch_bounds__(UPD_BX* UPD_BY) k_rk_update(StateView Sin, StateView S0, StateView Sout,
-                                                              const double* __restrict__ Fx,
-                                                              const double* __restrict__ Gy, GridDev g,
-                                                              const MechDev* __restrict__ mech, StepCtl ctl,
-                                                              const unsigned long long* __restrict__ alpha_step,
-                                                              unsigned long long* alpha_out, int* status,
-                                                              double* clock2) {
+__device__ __forceinline__ void rk_update_block(const StateView& Sin, const StateView& S0, const StateView& Sout,
+                                                const double* __restrict__ Fx, const double* __restrict__ Gy,
+                                                const GridDev& g, const MechDev* __restrict__ mech,
+                                                const StepCtl& ctl, const unsigned long long* __restrict__ alpha_step,
+                                                unsigned long long* alpha_out, int* status, double* clock2, int bx,
+                                                int by) {
   constexpr int NV = NS + 3;
-  const int i = blockIdx.x * UPD_BX + threadIdx.x;
-  const int j = blockIdx.y * UPD_BY + threadIdx.y;
+  const int i = bx * UPD_BX + threadIdx.x;
+  const int j = by * UPD_BY + threadIdx.y;
   const long long n = g.n;
   const double dt = step_dt(ctl, alpha_step);
-  if (STAGE == 1 && clock2 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+  if (STAGE == 1 && clock2 && bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
     clock2[0] += dt;  // simulated time
     clock2[1] = dt;   // last dt
   }
@@ -69,6 +70,90 @@ __global__ void __launch_bounds__(UPD_BX* UPD_BY) k_rk_update(StateView Sin, Sta
     finish_cell<NS>(Sout, n, idx, u, T, p, c, rrho, sx, sy);
   }
   block_reduce_alpha_status(sx, sy, st, alpha_out, status);
+}
+
+template <int NS, int STAGE>
+__global__ void __launch_bounds__(UPD_BX* UPD_BY) k_rk_update(StateView Sin, StateView S0, StateView Sout,
+                                                              const double* __restrict__ Fx,
+                                                              const double* __restrict__ Gy, GridDev g,
+                                                              const MechDev* __restrict__ mech, StepCtl ctl,
+                                                              const unsigned long long* __restrict__ alpha_step,
+                                                              unsigned long long* alpha_out, int* status,
+                                                              double* clock2) {
+  rk_update_block<NS, STAGE>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, alpha_step, alpha_out, status, clock2, blockIdx.x,
+                             blockIdx.y);
+}
+
+// Batched stage update over the flattened (request, block) list. Stage s
+// reads S[s-1] (s = 1, 2) or S[2] (s = 3) and writes S[s] (S[0] for s = 3);
+// the output alpha goes to slot s, or slot 4 for stage 3 without chemistry.
+template <int NS, int STAGE>
+__global__ void __launch_bounds__(UPD_BX* UPD_BY) k_rk_update_batch(const BatchReq* __restrict__ reqs,
+                                                                    const int* __restrict__ first, int nreq,
+                                                                    int chem) {
+  const int total = first[nreq];
+  for (int e = blockIdx.x; e < total; e += gridDim.x) {
+    const int r = batch_owner(first, nreq, e);
+    const BatchReq& q = reqs[r];
+    const int local = e - first[r];
+    const int out = STAGE == 3 ? 0 : STAGE;
+    const int aslot = STAGE == 3 ? (chem ? 3 : 4) : STAGE;
+    rk_update_block<NS, STAGE>(q.S[STAGE - 1], q.S[0], q.S[out], q.Fx, q.Gy, q.g, q.mech, q.ctl, q.alpha,
+                               q.alpha + 2 * aslot, q.status, STAGE == 1 ? q.clock2 : nullptr, local % q.ubx,
+                               local / q.ubx);
+    __syncthreads();
+  }
+}
+
+// Start of a batched step: for every request, the previous step's final
+// alpha becomes the step's starting alpha (except on its first step, whose
+// alpha was set when the state was loaded), and slots 1..4 are cleared.
+__global__ void k_batch_prep(BatchReq* reqs, int nreq) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nreq) return;
+  unsigned long long* a = reqs[r].alpha;
+  if (!reqs[r].fresh) {
+    a[0] = a[8];
+    a[1] = a[9];
+  }
+  for (int k = 2; k < 10; ++k) a[k] = 0ull;
+  reqs[r].fresh = 0;
+}
+
+template <int NS>
+static cudaError_t launch_rk_update_batch_t(int stage, const BatchReq* reqs, const int* first, int nreq, int total,
+                                            int chem, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = total < sms * 8 ? total : sms * 8;
+  if (grid <= 0) return cudaSuccess;
+  dim3 blk(UPD_BX, UPD_BY);
+  if (stage == 1) k_rk_update_batch<NS, 1><<<grid, blk, 0, st>>>(reqs, first, nreq, chem);
+  else if (stage == 2) k_rk_update_batch<NS, 2><<<grid, blk, 0, st>>>(reqs, first, nreq, chem);
+  else k_rk_update_batch<NS, 3><<<grid, blk, 0, st>>>(reqs, first, nreq, chem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rk_update_batch(int ns, int stage, const BatchReq* reqs, const int* first, int nreq, int total,
+                                   int chem, cudaStream_t st) {
+  switch (ns) {
+    case 1: return launch_rk_update_batch_t<1>(stage, reqs, first, nreq, total, chem, st);
+    case 3: return launch_rk_update_batch_t<3>(stage, reqs, first, nreq, total, chem, st);
+    case 9: return launch_rk_update_batch_t<9>(stage, reqs, first, nreq, total, chem, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_batch_prep(BatchReq* reqs, int nreq, cudaStream_t st) {
+  if (nreq <= 0) return cudaSuccess;
+  k_batch_prep<<<(nreq + 127) / 128, 128, 0, st>>>(reqs, nreq);
+  return cudaGetLastError();
+}
+
+void update_blocks(const GridDev& g, int* ubx, int* uby) {
+  *ubx = (g.nx + UPD_BX - 1) / UPD_BX;
+  *uby = (g.ny + UPD_BY - 1) / UPD_BY;
 }
 
 template <int NS>

@@ -42,6 +42,21 @@ class janc_mechanism(ctypes.Structure):
         (k, ctypes.c_void_p) for k in ("M", "nasa", "A", "b", "Ea", "nuf", "nub", "tb", "eff")]
 
 
+class janc_server_info(ctypes.Structure):
+    _fields_ = [("n_queued", ctypes.c_int), ("n_active", ctypes.c_int), ("n_copying", ctypes.c_int),
+                ("n_done", ctypes.c_int), ("pool_used", ctypes.c_size_t), ("pool_bytes", ctypes.c_size_t),
+                ("macro_steps", ctypes.c_longlong)]
+
+
+class janc_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("steps_done", ctypes.c_int), ("n_steps", ctypes.c_int),
+                ("status", ctypes.c_int), ("t", ctypes.c_double), ("dt_last", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double)]
+
+
+REQ_QUEUED, REQ_ACTIVE, REQ_COPYING, REQ_DONE, REQ_FAILED, REQ_FETCHED = range(6)
+
+
 class janc_status_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_int), ("t", ctypes.c_double),
                 ("dt_last", ctypes.c_double), ("alpha", ctypes.c_double * 2)]
@@ -76,6 +91,14 @@ def lib():
             L.janc_selfcheck_rcp.argtypes = [p, i, ctypes.POINTER(ctypes.c_longlong)]
             L.janc_rhs_static.argtypes = [p, p, p, p, p, p, p]
             L.janc_selfcheck_exp.argtypes = [p, i, ctypes.POINTER(ctypes.c_longlong)]
+            L.janc_server_create.argtypes = [p, i, ctypes.c_size_t, p, i, p, ctypes.POINTER(p)]
+            L.janc_server_footprint.argtypes = [p, p, ctypes.POINTER(ctypes.c_size_t)]
+            L.janc_server_submit.argtypes = [p, p, p, p, p, p, p, i, d, d, ctypes.POINTER(i)]
+            L.janc_server_run.argtypes = [p, i, p]
+            L.janc_server_poll.argtypes = [p, i, p]
+            L.janc_server_fetch.argtypes = [p, i, p, p]
+            L.janc_server_destroy.argtypes = [p]
+            L.janc_server_destroy.restype = None
             L.janc_profile.argtypes = [p, i]
             L.janc_profile_read.argtypes = [p, p, p]
             _lib = L
@@ -241,6 +264,55 @@ def janc_selfcheck_rcp(x) -> int:
     out = ctypes.c_longlong()
     _check(lib().janc_selfcheck_rcp(x.ctypes.data_as(ctypes.c_void_p), int(x.size), ctypes.byref(out)))
     return out.value
+
+
+def janc_server_create(mech: Mechanism, chemistry=True, pool_bytes=1 << 30, pool_ptr=None, max_active=64,
+                       stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().janc_server_create(ctypes.byref(mech.c), int(bool(chemistry)), int(pool_bytes),
+                                    ctypes.c_void_p(pool_ptr) if pool_ptr else None, int(max_active),
+                                    ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+    return h
+
+
+def janc_server_footprint(s, desc) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().janc_server_footprint(s, ctypes.byref(desc), ctypes.byref(out)))
+    return out.value
+
+
+def janc_server_submit(s, desc, T, p, u, v, Y, n_steps, dt=0.0, cfl=0.0) -> int:
+    arrs = [_arg(np.ascontiguousarray(x, np.float64)) for x in (T, p, u, v, Y)]
+    if any(a[1] != JANC_HOST for a in arrs):
+        raise ValueError("janc_server_submit takes host arrays")
+    rid = ctypes.c_int()
+    _check(lib().janc_server_submit(s, ctypes.byref(desc), *[a[0] for a in arrs], int(n_steps), float(dt),
+                                    float(cfl), ctypes.byref(rid)))
+    return rid.value
+
+
+def janc_server_run(s, macro_steps=1) -> dict:
+    info = janc_server_info()
+    _check(lib().janc_server_run(s, int(macro_steps), ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in janc_server_info._fields_}
+
+
+def janc_server_poll(s, rid) -> dict:
+    ri = janc_request_info()
+    _check(lib().janc_server_poll(s, int(rid), ctypes.byref(ri)))
+    return {k: getattr(ri, k) for k, _ in janc_request_info._fields_}
+
+
+def janc_server_fetch(s, rid, U=None, T=None, check=True) -> int:
+    a, b = _arg(U, True), _arg(T, True)
+    rc = lib().janc_server_fetch(s, int(rid), a[0], b[0])
+    if check:
+        _check(rc)
+    return rc
+
+
+def janc_server_destroy(s):
+    lib().janc_server_destroy(s)
 
 
 def janc_selfcheck_exp(x) -> int:
