@@ -62,10 +62,20 @@ extern "C" {
 
 typedef struct janc_grid_s* janc_grid_t;
 
+/* Operator splitting of one step (Sec. 4.3). advance_one_step as written
+ * there runs the flux RK3 over dt and then the point-implicit chemistry
+ * (Eq. 4.12-4.13) over dt (JANC_CHEM_LIE); the text of the same section names
+ * Strang splitting, chemistry over dt/2, flux over dt, chemistry over dt/2
+ * (JANC_CHEM_STRANG). dt is the step's, from the CFL of its starting state. */
+#define JANC_CHEM_OFF 0
+#define JANC_CHEM_LIE 1
+#define JANC_CHEM_STRANG 2
+
 /* Grid description.
  * nx, ny >= 1 cells; dx, dy > 0 m; bc = {left, right, bottom, top};
- * chemistry = 1 runs advance_source_term (Eq. 4.12-4.13) after the flux RK3,
- * 0 runs the explicit variant of advance_one_step (Sec. 4.3);
+ * chemistry = JANC_CHEM_* (above): JANC_CHEM_OFF runs the flux terms only,
+ * the explicit variant of advance_one_step (Sec. 4.3). The server and the
+ * adjoint take JANC_CHEM_OFF or JANC_CHEM_LIE only (JANC_E_UNSUPPORTED);
  * weno_eps = epsilon of the WENO5-JS weights (1e-6 if <= 0);
  * newton_tol / newton_maxit = stop when |dT| <= tol * T (1e-12 / 50 if <= 0). */
 typedef struct {
@@ -181,6 +191,49 @@ int janc_selfcheck_rcp(const double* x, int n, long long* max_ulp);
  * the device, over the n host values x: max_ulp receives the largest
  * distance in units in the last place. Synchronous; allocates scratch. */
 int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
+
+/* ------------------------------------------------------------------------
+ * Discrete adjoint. The gradient of a loss of a fixed-dt trajectory of
+ * advance_one_step (Sec. 4.3) with respect to its initial conserved state,
+ * by reverse-mode differentiation of every operation the forward kernels do
+ * (flux splitting and WENO5, the global LF speeds through their arg-max
+ * cells, Newton T recovery by its implicit derivative, TVD-RK3, point-
+ * implicit chemistry), with checkpoint-and-recompute: the state is stored
+ * every ckpt_every steps and each segment is recomputed (bit for bit) during
+ * the reverse sweep. Memory: ceil(n/ckpt_every) + 4 ckpt_every + 1 states of
+ * (nv + 4) planes, 7 cotangent arrays and the face-contribution buffers; see
+ * janc_adjoint_workspace_bytes. The continuous adjoint of Sec. 6.1 (Eq. 6.5)
+ * is replaced by this exact discrete one.
+ * ---------------------------------------------------------------------- */
+#define JANC_LOSS_ENDWALL_P 0  /* L = sum_n dt * mean_j p(nx-1, j) of U^{n+1} */
+#define JANC_LOSS_SEEDED 1     /* L = <seed, U^N> (seed: nv planes) */
+
+/* Device bytes janc_step_adjoint needs as workspace. */
+int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, size_t* bytes);
+
+/* From the grid's current state U^0 (set beforehand), run n_steps fixed-dt
+ * steps, computing the loss (*loss_out, host, may be NULL) and, when dL_dU0
+ * is not NULL, the cotangent dL/dU^0 [nv][ny][nx] (host or device, `where`).
+ * seed: nv planes for JANC_LOSS_SEEDED, else ignored (host or device).
+ * workspace: device memory of janc_adjoint_workspace_bytes (256-byte
+ * aligned), or NULL to let the call allocate and free it. On return the
+ * grid holds U^N. Synchronous. */
+int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int loss_kind, const double* seed,
+                      double* dL_dU0, double* loss_out, void* workspace, size_t workspace_bytes, int where);
+
+/* Vector-Jacobian product of the right-hand side L(U) (Eq. 4.10-4.11 with
+ * WENO5, the ghost layers and the global LF speeds) at the grid's current
+ * state: nu = (dL/dU)^T mu, both [nv][ny][nx], host or device. workspace:
+ * device memory for 2 nv planes plus 10 nv values per x- and y-face, each
+ * piece rounded up to 256 bytes, plus 256 bytes (NULL: allocated here).
+ * Synchronous. */
+int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, size_t workspace_bytes, int where);
+
+/* dL/dT [ny][nx] of the primitive initialisation of Eq. 4.2 at fixed p, u,
+ * v, Y (device pointers, the layout of janc_set_state_primitive), given
+ * dL/dU [nv][ny][nx] (device). Synchronous. */
+int janc_primitive_T_vjp(janc_grid_t g, const double* T, const double* p, const double* u, const double* v,
+                         const double* Y, const double* dL_dU, double* dL_dT);
 
 /* ------------------------------------------------------------------------
  * Continuous-batching server: many independent solves of one mechanism on

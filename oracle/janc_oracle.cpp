@@ -82,6 +82,49 @@ static void store_field(const Field<double>& F, double* U, double* T) {
   std::memcpy(T, F.T.data(), F.T.size() * sizeof(double));
 }
 
+// Tangent of an n-step fixed-dt trajectory along up to LANES directions at
+// once. dU0: [nl][nv][ny][nx]; the temperature tangents are made consistent
+// by a Newton solve. Outputs: dUN [nl][nv][ny][nx] and loss[0..nl] = the value
+// and the tangents of L = sum_n dt mean_j p(nx-1, j) of U^{n+1}.
+template <int LANES>
+static int trajectory_tangent(const orc_mech_c* mc, const orc_grid_c* gc, const double* U, const double* T,
+                              const double* dU0, int nl, int nsteps, double dt, int chem, double* dUN, double* loss) {
+  using D = Dual<double, LANES>;
+  if (nl < 1 || nl > LANES) return -1;
+  Mech m = to_mech(mc);
+  Grid g = to_grid(gc);
+  Field<D> F;
+  F.resize(nvar_of(m), g.nx, g.ny);
+  const size_t N = F.U.size();
+  for (size_t q = 0; q < N; ++q) {
+    F.U[q] = D(U[q]);
+    for (int l = 0; l < nl; ++l) F.U[q].d[l] = dU0[(size_t)l * N + q];
+  }
+  int st = 0;
+  for (int j = 0; j < g.ny; ++j)
+    for (int i = 0; i < g.nx; ++i) {
+      D u[16];
+      for (int k = 0; k < F.nv; ++k) u[k] = F.u(k, i, j);
+      F.t(i, j) = newton_T(m, g, u, D(T[(size_t)j * g.nx + i]), &st);
+    }
+  D L(0.0);
+  for (int n = 0; n < nsteps; ++n) {
+    st |= advance_one_step(m, g, F, dt, chem);
+    D s(0.0);
+    for (int j = 0; j < g.ny; ++j) {
+      D u[16];
+      for (int k = 0; k < F.nv; ++k) u[k] = F.u(k, g.nx - 1, j);
+      s = s + primitives(m, u, F.t(g.nx - 1, j)).p;
+    }
+    L = L + (dt / g.ny) * s;
+  }
+  for (size_t q = 0; q < N; ++q)
+    for (int l = 0; l < nl; ++l) dUN[(size_t)l * N + q] = F.U[q].d[l];
+  loss[0] = L.v;
+  for (int l = 0; l < nl; ++l) loss[1 + l] = L.d[l];
+  return st;
+}
+
 extern "C" {
 
 // Sets the OpenMP thread count (n <= 0 keeps the default); returns the count in use.
@@ -216,7 +259,7 @@ int orc_step(const orc_mech_c* mc, const orc_grid_c* gc, double* U, double* T, i
   double t = 0.0;
   for (int n = 0; n < nsteps; ++n) {
     double h = dt > 0.0 ? dt : cfl_dt(m, g, F, cfl);
-    st |= advance_one_step(m, g, F, h, chem != 0);
+    st |= advance_one_step(m, g, F, h, chem);
     t += h;
     if (dt_log) dt_log[n] = h;
   }
@@ -238,10 +281,39 @@ int orc_step_tangent(const orc_mech_c* mc, const orc_grid_c* gc, double* U, doub
   for (size_t q = 0; q < F.U.size(); ++q) { F.U[q] = D(U[q]); F.U[q].d[0] = dU[q]; }
   for (size_t q = 0; q < F.T.size(); ++q) { F.T[q] = D(T[q]); F.T[q].d[0] = dT[q]; }
   int st = 0;
-  for (int n = 0; n < nsteps; ++n) st |= advance_one_step(m, g, F, dt, chem != 0);
+  for (int n = 0; n < nsteps; ++n) st |= advance_one_step(m, g, F, dt, chem);
   for (size_t q = 0; q < F.U.size(); ++q) { U[q] = F.U[q].v; dU[q] = F.U[q].d[0]; }
   for (size_t q = 0; q < F.T.size(); ++q) { T[q] = F.T[q].v; dT[q] = F.T[q].d[0]; }
   return st;
+}
+
+// Tangent of the right-hand side at (U, T) along dU: dL = (dL/dU) dU, with the
+// temperature tangent made consistent by a Newton solve on dual numbers.
+int orc_rhs_tangent(const orc_mech_c* mc, const orc_grid_c* gc, const double* U, const double* T, const double* dU,
+                    double* dL) {
+  using D = Dual<double, 1>;
+  Mech m = to_mech(mc);
+  Grid g = to_grid(gc);
+  Field<D> F;
+  F.resize(nvar_of(m), g.nx, g.ny);
+  for (size_t q = 0; q < F.U.size(); ++q) { F.U[q] = D(U[q]); F.U[q].d[0] = dU[q]; }
+  int st = 0;
+  for (int j = 0; j < g.ny; ++j)
+    for (int i = 0; i < g.nx; ++i) {
+      D u[16];
+      for (int k = 0; k < F.nv; ++k) u[k] = F.u(k, i, j);
+      F.t(i, j) = newton_T(m, g, u, D(T[(size_t)j * g.nx + i]), &st);
+    }
+  std::vector<D> L;
+  rhs(m, g, F, L);
+  for (size_t q = 0; q < L.size(); ++q) dL[q] = L[q].d[0];
+  return st;
+}
+
+int orc_trajectory_tangent8(const orc_mech_c* mc, const orc_grid_c* gc, const double* U, const double* T,
+                            const double* dU0, int nl, int nsteps, double dt, int chem, double* dUN, double* loss) {
+  if (nl == 1) return trajectory_tangent<1>(mc, gc, U, T, dU0, nl, nsteps, dt, chem, dUN, loss);
+  return trajectory_tangent<8>(mc, gc, U, T, dU0, nl, nsteps, dt, chem, dUN, loss);
 }
 
 // Operation counts (add, mul, div, sqrt, exp, log) of the plain algorithm.

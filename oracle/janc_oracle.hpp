@@ -27,7 +27,8 @@
 // Readings where the paper is silent or ambiguous (each one is applied the
 // same way in the CUDA path and listed in the design notes):
 //   * splitting order: flux(dt) then chemistry(dt), as advance_one_step is
-//     written in Sec. 4.3 (Lie order);
+//     written in Sec. 4.3 (Lie order); the Strang order the text of Sec. 4.3
+//     names is the CHEM_STRANG variant (chemistry dt/2, flux dt, chemistry dt/2);
 //   * alpha in Eq. 4.11: global max over interior cells, per direction
 //     (|u|+c for x, |v|+c for y), recomputed from each RK stage's input;
 //   * WENO5-JS (Jiang & Shu 1996) with epsilon = weno_eps and power 2,
@@ -654,12 +655,45 @@ template <class S> double cfl_dt(const Mech& m, const Grid& g, const Field<S>& F
   return cfl * std::min(g.dx, g.dy) / amax;
 }
 
-// One time step (advance_one_step of Sec. 4.3): CFL, TVD-RK3 of the flux
-// terms (Shu-Osher form), then the point-implicit chemistry (Eq. 4.12-4.13).
-// F holds U^n and its T on entry and U^{n+1} and its T on exit.
-template <class S> int advance_one_step(const Mech& m, const Grid& g, Field<S>& F, double dt, bool chem) {
+// The point-implicit chemistry step (Eq. 4.12-4.13) over dt applied to every
+// cell of F, followed by the Newton T of the new state warm-started from the
+// old one.
+template <class S> int chemistry_step(const Mech& m, const Grid& g, Field<S>& F, double dt) {
+  int st = 0;
+  Field<S> Un = F;
+  #pragma omp parallel for schedule(static) reduction(| : st)
+  for (int j = 0; j < F.ny; ++j)
+    for (int i = 0; i < F.nx; ++i) {
+      S u[16];
+      for (int k = 0; k < F.nv; ++k) u[k] = F.u(k, i, j);
+      int s = 0;
+      point_implicit(m, u, F.t(i, j), dt, &s);
+      for (int k = 0; k < F.nv; ++k) Un.u(k, i, j) = u[k];
+      st |= s;
+    }
+  st |= update_T(m, g, Un, F);
+  F = Un;
+  return st;
+}
+
+// Splitting of the chemistry and flux operators within one step.
+enum : int {
+  CHEM_OFF = 0,     // flux terms only (the explicit variant without sources)
+  CHEM_LIE = 1,     // flux(dt) then chemistry(dt): advance_one_step as coded in Sec. 4.3
+  CHEM_STRANG = 2,  // chemistry(dt/2), flux(dt), chemistry(dt/2): the Strang
+                    // splitting named in the text of Sec. 4.3
+};
+
+// One time step (advance_one_step of Sec. 4.3): TVD-RK3 of the flux terms
+// (Shu-Osher form) and the point-implicit chemistry (Eq. 4.12-4.13) in the
+// order given by chem (CHEM_*; a bool true means CHEM_LIE). dt is the step's
+// (from the CFL of its starting state when the caller asks for it). F holds
+// U^n and its T on entry and U^{n+1} and its T on exit.
+template <class S> int advance_one_step(const Mech& m, const Grid& g, Field<S>& F, double dt, int chem) {
   const size_t N = F.U.size();
   int st = 0;
+  const bool reacting = m.nr > 0 && m.ns > 1;
+  if (chem == CHEM_STRANG && reacting) st |= chemistry_step(m, g, F, 0.5 * dt);
   std::vector<S> L;
   Field<S> U1 = F, U2 = F;
   // stage 1: U1 = U^n + dt L(U^n)
@@ -675,23 +709,9 @@ template <class S> int advance_one_step(const Mech& m, const Grid& g, Field<S>& 
   Field<S> Us = F;
   for (size_t q = 0; q < N; ++q) Us.U[q] = (1.0 / 3.0) * F.U[q] + (2.0 / 3.0) * (U2.U[q] + dt * L[q]);
   st |= update_T(m, g, Us, U2);
-  if (chem && m.nr > 0 && m.ns > 1) {
-    Field<S> Un = Us;
-    #pragma omp parallel for schedule(static) reduction(| : st)
-    for (int j = 0; j < F.ny; ++j)
-      for (int i = 0; i < F.nx; ++i) {
-        S u[16];
-        for (int k = 0; k < F.nv; ++k) u[k] = Us.u(k, i, j);
-        int s = 0;
-        point_implicit(m, u, Us.t(i, j), dt, &s);
-        for (int k = 0; k < F.nv; ++k) Un.u(k, i, j) = u[k];
-        st |= s;
-      }
-    st |= update_T(m, g, Un, Us);
-    F = Un;
-  } else {
-    F = Us;
-  }
+  if (chem == CHEM_LIE && reacting) st |= chemistry_step(m, g, Us, dt);
+  if (chem == CHEM_STRANG && reacting) st |= chemistry_step(m, g, Us, 0.5 * dt);
+  F = Us;
   st |= check_state(m, F);
   return st;
 }

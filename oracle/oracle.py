@@ -87,6 +87,8 @@ def lib():
             _lib.orc_lu_solve.argtypes = [i, p, p]
             _lib.orc_thermo.argtypes = [p, i, d, p, p, p]
             _lib.orc_opcount.argtypes = [p, p, i, p, p, d, p]
+            _lib.orc_rhs_tangent.argtypes = [p, p, p, p, p, p]
+            _lib.orc_trajectory_tangent8.argtypes = [p, p, p, p, p, i, i, d, i, p, p]
         return _lib
 
 
@@ -241,15 +243,29 @@ def cfl_dt(mech, grid, U, T, cfl):
     return lib().orc_cfl_dt(mh.ref, ctypes.byref(_grid(grid)), _ptr(_f64(U)), _ptr(_f64(T)), float(cfl))
 
 
+CHEM_OFF, CHEM_LIE, CHEM_STRANG = 0, 1, 2
+
+
+def _chem_mode(chem) -> int:
+    """False/True -> off/Lie; or one of CHEM_OFF, CHEM_LIE, CHEM_STRANG."""
+    if isinstance(chem, bool):
+        return CHEM_LIE if chem else CHEM_OFF
+    mode = int(chem)
+    if mode not in (CHEM_OFF, CHEM_LIE, CHEM_STRANG):
+        raise ValueError(f"chemistry mode {chem!r}")
+    return mode
+
+
 def step(mech, grid, U, T, nsteps, dt=0.0, cfl=0.0, chem=True):
-    """Advance n steps. Returns (U, T, status, t, dt_log)."""
+    """Advance n steps (chem: False/True or a CHEM_* splitting mode).
+    Returns (U, T, status, t, dt_log)."""
     mh = _MechHandle(mech)
     U = _f64(U).copy()
     T = _f64(T).copy()
     t = ctypes.c_double()
     dts = np.zeros(max(int(nsteps), 1))
     st = lib().orc_step(mh.ref, ctypes.byref(_grid(grid)), _ptr(U), _ptr(T), int(nsteps), float(dt), float(cfl),
-                        int(bool(chem)), ctypes.byref(t), _ptr(dts))
+                        _chem_mode(chem), ctypes.byref(t), _ptr(dts))
     return U, T, st, t.value, dts[:nsteps]
 
 
@@ -258,8 +274,31 @@ def step_tangent(mech, grid, U, T, dU, dT, nsteps, dt, chem=True):
     mh = _MechHandle(mech)
     U, T, dU, dT = (_f64(a).copy() for a in (U, T, dU, dT))
     st = lib().orc_step_tangent(mh.ref, ctypes.byref(_grid(grid)), _ptr(U), _ptr(T), _ptr(dU), _ptr(dT),
-                                int(nsteps), float(dt), int(bool(chem)))
+                                int(nsteps), float(dt), _chem_mode(chem))
     return U, T, dU, dT, st
+
+
+def rhs_tangent(mech, grid, U, T, dU):
+    """(dL/dU) dU at (U, T), with the T tangent from a dual Newton solve."""
+    mh = _MechHandle(mech)
+    U, T, dU = _f64(U), _f64(T), _f64(dU)
+    dL = np.zeros_like(U)
+    st = lib().orc_rhs_tangent(mh.ref, ctypes.byref(_grid(grid)), _ptr(U), _ptr(T), _ptr(dU), _ptr(dL))
+    return dL, st
+
+
+def trajectory_tangent(mech, grid, U, T, dU0, nsteps, dt, chem=True):
+    """Tangents of U^N and of the end-wall pressure loss along up to 8
+    directions dU0[l]. Returns (dUN [nl, ...], loss value, dloss [nl], status)."""
+    mh = _MechHandle(mech)
+    U, T = _f64(U), _f64(T)
+    dU0 = _f64(dU0)
+    nl = dU0.shape[0]
+    dUN = np.zeros_like(dU0)
+    loss = np.zeros(1 + nl)
+    st = lib().orc_trajectory_tangent8(mh.ref, ctypes.byref(_grid(grid)), _ptr(U), _ptr(T), _ptr(dU0), int(nl),
+                                       int(nsteps), float(dt), _chem_mode(chem), _ptr(dUN), _ptr(loss))
+    return dUN, loss[0], loss[1:], st
 
 
 OPS_NAMES = ("add", "mul", "div", "sqrt", "exp", "log")

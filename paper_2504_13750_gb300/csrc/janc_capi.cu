@@ -12,11 +12,13 @@
 //   flux(S0) -> update1 -> S1, flux(S1) -> update2 -> S2,
 //   flux(S2) -> update3 -> S0 (in place), [chem on S0 in place],
 // with dt computed on the device from the alpha slot of the step's start.
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/janc.h"
@@ -39,7 +41,7 @@ int fail_cuda(cudaError_t e, const char* where) {
 }
 
 constexpr int CHUNK = 256;  // steps per alpha-slot chunk
-constexpr int SLOTS_PER_STEP = 4;
+constexpr int SLOTS_PER_STEP = 5;
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -79,6 +81,8 @@ int check_desc(const janc_grid_desc* d, const janc_mechanism* m) {
   if (!m->M || !m->nasa) return fail(JANC_E_INVALID, "null molar masses or NASA-7 table");
   if (m->nr > 0 && (!m->A || !m->b || !m->Ea || !m->nuf || !m->nub || !m->tb || !m->eff))
     return fail(JANC_E_INVALID, "null reaction table");
+  if (d->chemistry != JANC_CHEM_OFF && d->chemistry != JANC_CHEM_LIE && d->chemistry != JANC_CHEM_STRANG)
+    return fail(JANC_E_INVALID, "chemistry must be JANC_CHEM_OFF, JANC_CHEM_LIE or JANC_CHEM_STRANG");
   if (d->chemistry && (m->nr == 0 || m->ns < 3)) return fail(JANC_E_INVALID, "chemistry needs reactions and ns >= 3");
   return JANC_OK;
 }
@@ -371,6 +375,8 @@ int janc_step(janc_grid_t g, int n_steps, double dt, double cfl, double* t_out, 
   ctl.dt_fixed = dt > 0.0 ? dt : 0.0;
   ctl.cfl = cfl > 0.0 ? cfl : 0.0;
   ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
+  const bool strang = g->d.chemistry == JANC_CHEM_STRANG;
+  ctl.chem_frac = strang ? 0.5 : 1.0;
   double t_before = 0.0;
   if (t_out) {
     cudaError_t e = cudaMemcpyAsync(&t_before, g->clock2, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
@@ -385,12 +391,22 @@ int janc_step(janc_grid_t g, int n_steps, double dt, double cfl, double* t_out, 
     cudaError_t e = cudaMemsetAsync(g->alpha + 2, 0, sizeof(unsigned long long) * 2 * SLOTS_PER_STEP * nc, g->stream);
     if (e != cudaSuccess) return fail_cuda(e, "alpha reset");
     for (int s = 0; s < nc; ++s) {
+      // slots: a0 = U^n (dt source), aH = after the first half chemistry
+      // (Strang order only), a1, a2 = stages, a3 = U^*, a4 = U^{n+1} (the
+      // next step's a0)
       unsigned long long* a0 = g->alpha + 2 * (SLOTS_PER_STEP * s);
-      unsigned long long* a1 = a0 + 2;
-      unsigned long long* a2 = a0 + 4;
-      unsigned long long* a3 = a0 + 6;
-      unsigned long long* a4 = a0 + 8;  // next step's start
-      e = timed(g, 0, [&] { return launch_face_flux(g->nv, S0, a0, g->Fx, g->Gy, g->gd, g->stream); });
+      unsigned long long* aH = a0 + 2;
+      unsigned long long* a1 = a0 + 4;
+      unsigned long long* a2 = a0 + 6;
+      unsigned long long* a3 = a0 + 8;
+      unsigned long long* a4 = a0 + 10;
+      unsigned long long* aF = a0;  // alpha of the flux stage-1 input
+      if (strang) {
+        e = timed(g, 2, [&] { return launch_chem(g->ns, S0, g->gd, g->mech, ctl, a0, aH, g->status, g->stream); });
+        if (e != cudaSuccess) return fail_cuda(e, "step launch");
+        aF = aH;
+      }
+      e = timed(g, 0, [&] { return launch_face_flux(g->nv, S0, aF, g->Fx, g->Gy, g->gd, g->stream); });
       if (e == cudaSuccess)
         e = timed(g, 1, [&] {
           return launch_rk_update(g->ns, 1, S0, S0, S1, g->Fx, g->Gy, g->gd, g->mech, ctl, a0, a1, g->status,
@@ -525,6 +541,234 @@ int janc_status(janc_grid_t g, janc_status_info* s) {
   s->dt_last = c2[1];
   std::memcpy(s->alpha, a, sizeof(s->alpha));
   return JANC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint (see janc_adjoint.cu for the operator transposes).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjLayout {
+  size_t state, ckpt, seg, alog, lam, cfx, cfy, small, total;
+  int ncp, seglen;
+};
+
+AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every) {
+  AdjLayout L;
+  const size_t n = (size_t)g->n;
+  const int nv = g->nv;
+  L.seglen = ckpt_every;
+  L.ncp = n_steps > 0 ? (n_steps + ckpt_every - 1) / ckpt_every : 1;
+  L.state = align256(sizeof(double) * (size_t)(nv + 4) * n);
+  L.ckpt = (size_t)L.ncp * (L.state + 256);              // state + its alpha pair
+  L.seg = (size_t)(4 * ckpt_every + 1) * L.state;        // S0[0..len], S1, S2, S* per step
+  L.alog = align256(sizeof(unsigned long long) * 10 * ckpt_every);
+  L.lam = 7 * align256(sizeof(double) * (size_t)nv * n);
+  L.cfx = align256(sizeof(double) * (size_t)nv * g->gd.ny * (g->gd.nx + 1) * 10);
+  L.cfy = align256(sizeof(double) * (size_t)nv * (g->gd.ny + 1) * g->gd.nx * 10);
+  L.small = 256;
+  L.total = L.ckpt + L.seg + L.alog + L.lam + L.cfx + L.cfy + L.small;
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, size_t* bytes) {
+  if (!g || !bytes || n_steps < 0 || ckpt_every <= 0) return fail(JANC_E_INVALID, "bad argument");
+  *bytes = adj_layout(g, n_steps, ckpt_every).total;
+  return JANC_OK;
+}
+
+int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, size_t workspace_bytes, int where) {
+  if (!g || !mu || !nu) return fail(JANC_E_INVALID, "null argument");
+  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
+  const size_t nvn = (size_t)g->nv * g->n;
+  const size_t bx = align256(sizeof(double) * (size_t)g->nv * g->gd.ny * (g->gd.nx + 1) * 10);
+  const size_t by = align256(sizeof(double) * (size_t)g->nv * (g->gd.ny + 1) * g->gd.nx * 10);
+  const size_t need = 2 * align256(sizeof(double) * nvn) + bx + by + 256;
+  char* ws = (char*)workspace;
+  bool own = false;
+  if (!ws) {
+    if (cudaMalloc(&ws, need) != cudaSuccess) return fail(JANC_E_NOMEM, "janc_rhs_vjp: cudaMalloc failed");
+    own = true;
+  } else if (workspace_bytes < need) {
+    return fail(JANC_E_NOMEM, "janc_rhs_vjp: workspace too small");
+  }
+  double* dmu = (double*)ws;
+  double* dnu = (double*)(ws + align256(sizeof(double) * nvn));
+  double* cfx = (double*)(ws + 2 * align256(sizeof(double) * nvn));
+  double* cfy = (double*)((char*)cfx + bx);
+  double* scratch = (double*)((char*)cfy + by);
+  int rc = JANC_OK;
+  cudaError_t e = cudaMemcpyAsync(dmu, mu, sizeof(double) * nvn,
+                                  where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream);
+  if (e == cudaSuccess)
+    e = launch_rhs_vjp(g->ns, sv(g, 0), (const double*)g->alpha, dmu, dnu, cfx, cfy, scratch, g->gd, g->mech,
+                       g->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(nu, dnu, sizeof(double) * nvn,
+                        where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) rc = fail_cuda(e, "janc_rhs_vjp");
+  if (own) cudaFree(ws);
+  return rc;
+}
+
+int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int loss_kind, const double* seed,
+                      double* dL_dU0, double* loss_out, void* workspace, size_t workspace_bytes, int where) {
+  if (!g || n_steps < 0 || !(dt > 0.0) || ckpt_every <= 0) return fail(JANC_E_INVALID, "bad argument");
+  if (loss_kind != JANC_LOSS_ENDWALL_P && loss_kind != JANC_LOSS_SEEDED) return fail(JANC_E_INVALID, "loss kind");
+  if (loss_kind == JANC_LOSS_SEEDED && !seed) return fail(JANC_E_INVALID, "seeded loss needs a seed");
+  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
+  if (g->d.chemistry == JANC_CHEM_STRANG) return fail(JANC_E_UNSUPPORTED, "the adjoint reverses the Lie order only");
+  const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
+  char* ws = (char*)workspace;
+  bool own = false;
+  if (!ws) {
+    if (cudaMalloc(&ws, L.total) != cudaSuccess) return fail(JANC_E_NOMEM, "janc_step_adjoint: cudaMalloc failed");
+    own = true;
+  } else if (workspace_bytes < L.total || ((uintptr_t)ws & 255u)) {
+    return fail(JANC_E_NOMEM, "janc_step_adjoint: workspace too small or misaligned");
+  }
+  cudaStream_t st = g->stream;
+  const size_t n = (size_t)g->n;
+  const int nv = g->nv;
+  const size_t nvn = (size_t)nv * n;
+  const size_t lamb = align256(sizeof(double) * nvn);
+  char* p = ws;
+  char* ckpt = p; p += L.ckpt;
+  char* seg = p; p += L.seg;
+  unsigned long long* alog = (unsigned long long*)p; p += L.alog;
+  double* lam[7];
+  for (int k = 0; k < 7; ++k) { lam[k] = (double*)p; p += lamb; }
+  double* cfx = (double*)p; p += L.cfx;
+  double* cfy = (double*)p; p += L.cfy;
+  double* small = (double*)p;  // [0] loss, [8..15] vjp scratch
+  auto ckpt_state = [&](int c) { return StateView{(double*)(ckpt + (size_t)c * (L.state + 256))}; };
+  auto ckpt_alpha = [&](int c) { return (unsigned long long*)(ckpt + (size_t)c * (L.state + 256) + L.state); };
+  auto segS0 = [&](int m) { return StateView{(double*)(seg + (size_t)m * L.state)}; };
+  auto segS = [&](int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
+    return StateView{(double*)(seg + (size_t)(ckpt_every + 1 + 3 * m + which - 1) * L.state)};
+  };
+  const bool chem = g->d.chemistry != 0;
+  const double w_loss = dt / g->gd.ny;
+  StepCtl ctl;
+  ctl.dt_fixed = dt;
+  ctl.cfl = 0.0;
+  ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
+  ctl.chem_frac = 1.0;
+  int rc = JANC_OK;
+  cudaError_t e = cudaMemsetAsync(small, 0, 256, st);
+  // ---- forward with checkpoints and the loss ----
+  for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
+    if (s % ckpt_every == 0) {
+      const int c = s / ckpt_every;
+      e = cudaMemcpyAsync(ckpt_state(c).base, g->S[0], L.state, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ckpt_alpha(c), g->alpha, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+    }
+    if (e != cudaSuccess) break;
+    rc = janc_step(g, 1, dt, 0.0, nullptr, nullptr);
+    if (rc) break;
+    if (loss_kind == JANC_LOSS_ENDWALL_P) e = launch_loss_endwall(g->ns, sv(g, 0), g->gd, w_loss, small, st);
+  }
+  if (!rc && e == cudaSuccess && loss_kind == JANC_LOSS_SEEDED) {
+    double* dseed = lam[6];
+    e = cudaMemcpyAsync(dseed, seed, sizeof(double) * nvn,
+                        where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = launch_dot((long long)nvn, dseed, g->S[0], small, st);
+  }
+  // ---- reverse sweep over segments, recomputing each from its checkpoint ----
+  if (!rc && e == cudaSuccess && dL_dU0) {
+    double* lamN = lam[0];  // cotangent of U^{m+1}
+    double* lamS = lam[1];  // of U*
+    double* lam2 = lam[2];
+    double* lam1 = lam[3];
+    double* lam0 = lam[4];
+    double* mu = lam[5];
+    double* nu = lam[6];
+    if (loss_kind == JANC_LOSS_SEEDED) e = cudaMemcpyAsync(lamN, lam[6], sizeof(double) * nvn, cudaMemcpyDeviceToDevice, st);
+    else e = cudaMemsetAsync(lamN, 0, sizeof(double) * nvn, st);
+    for (int c = L.ncp - 1; c >= 0 && e == cudaSuccess && n_steps > 0; --c) {
+      const int m0 = c * ckpt_every;
+      const int len = (n_steps - m0) < ckpt_every ? (n_steps - m0) : ckpt_every;
+      // recompute the segment, keeping every stage state and its alpha
+      e = cudaMemcpyAsync(segS0(0).base, ckpt_state(c).base, L.state, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(alog, 0, L.alog, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(alog, ckpt_alpha(c), 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+      for (int m = 0; m < len && e == cudaSuccess; ++m) {
+        unsigned long long* a = alog + 10 * m;
+        if (m > 0) e = cudaMemcpyAsync(a, alog + 10 * (m - 1) + 8, 16, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = launch_face_flux(nv, segS0(m), a, g->Fx, g->Gy, g->gd, st);
+        if (e == cudaSuccess)
+          e = launch_rk_update(g->ns, 1, segS0(m), segS0(m), segS(m, 1), g->Fx, g->Gy, g->gd, g->mech, ctl, a, a + 2,
+                               g->status, nullptr, st);
+        if (e == cudaSuccess) e = launch_face_flux(nv, segS(m, 1), a + 2, g->Fx, g->Gy, g->gd, st);
+        if (e == cudaSuccess)
+          e = launch_rk_update(g->ns, 2, segS(m, 1), segS0(m), segS(m, 2), g->Fx, g->Gy, g->gd, g->mech, ctl, a,
+                               a + 4, g->status, nullptr, st);
+        if (e == cudaSuccess) e = launch_face_flux(nv, segS(m, 2), a + 4, g->Fx, g->Gy, g->gd, st);
+        if (e == cudaSuccess)
+          e = launch_rk_update(g->ns, 3, segS(m, 2), segS0(m), segS(m, 3), g->Fx, g->Gy, g->gd, g->mech, ctl, a,
+                               chem ? a + 6 : a + 8, g->status, nullptr, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(segS0(m + 1).base, segS(m, 3).base, L.state, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && chem)
+          e = launch_chem(g->ns, segS0(m + 1), g->gd, g->mech, ctl, a, a + 8, g->status, st);
+      }
+      // reverse through the segment
+      for (int m = len - 1; m >= 0 && e == cudaSuccess; --m) {
+        const unsigned long long* a = alog + 10 * m;
+        if (loss_kind == JANC_LOSS_ENDWALL_P)
+          e = launch_seed_endwall(g->ns, segS0(m + 1), g->gd, g->mech, w_loss, lamN, st);
+        if (e == cudaSuccess) {
+          if (chem) e = launch_chem_vjp(g->ns, segS(m, 3), g->gd, g->mech, dt, lamN, lamS, st);
+          else e = cudaMemcpyAsync(lamS, lamN, sizeof(double) * nvn, cudaMemcpyDeviceToDevice, st);
+        }
+        // stage 3: U* = U^n/3 + 2/3 (U2 + dt L(U2))
+        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 2.0 / 3.0 * dt, lamS, 0.0, nullptr, false, st);
+        if (e == cudaSuccess)
+          e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
+                             st);
+        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam2, 2.0 / 3.0, lamS, 1.0, nu, false, st);
+        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0 / 3.0, lamS, 0.0, nullptr, false, st);
+        // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
+        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 0.25 * dt, lam2, 0.0, nullptr, false, st);
+        if (e == cudaSuccess)
+          e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
+                             st);
+        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam1, 0.25, lam2, 1.0, nu, false, st);
+        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 0.75, lam2, 0.0, nullptr, true, st);
+        // stage 1: U1 = U^n + dt L(U^n)
+        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, dt, lam1, 0.0, nullptr, false, st);
+        if (e == cudaSuccess)
+          e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 8, g->gd, g->mech, st);
+        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0, lam1, 1.0, nu, true, st);
+        std::swap(lamN, lam0);
+      }
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dL_dU0, lamN, sizeof(double) * nvn,
+                          where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+  }
+  if (!rc && e == cudaSuccess && loss_out) e = cudaMemcpyAsync(loss_out, small, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (!rc && e != cudaSuccess) rc = fail_cuda(e, "janc_step_adjoint");
+  if (own) cudaFree(ws);
+  return rc;
+}
+
+int janc_primitive_T_vjp(janc_grid_t g, const double* T, const double* p, const double* u, const double* v,
+                         const double* Y, const double* dL_dU, double* dL_dT) {
+  if (!g || !T || !p || !u || !v || !Y || !dL_dU || !dL_dT) return fail(JANC_E_INVALID, "null argument");
+  cudaError_t e = launch_prim_T_vjp(g->ns, T, p, u, v, Y, dL_dU, dL_dT, g->gd, g->mech, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  return e == cudaSuccess ? JANC_OK : fail_cuda(e, "janc_primitive_T_vjp");
 }
 
 }  // extern "C"

@@ -36,7 +36,7 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
   const MechDev& m = *mech;
   const long long n = g.n;
   const long long idx = blk * CHEM_THREADS + threadIdx.x;
-  const double dt = step_dt(ctl, alpha_step);
+  const double dt = step_dt(ctl, alpha_step) * ctl.chem_frac;
   unsigned long long sx = 0, sy = 0;
   int st = 0;
   if (idx < n) {

@@ -78,7 +78,8 @@ struct StateView {
 struct StepCtl {
   double dt_fixed;
   double cfl;
-  double hmin;  // min(dx, dy)
+  double hmin;       // min(dx, dy)
+  double chem_frac;  // share of the step's dt taken by one chemistry launch: 1, or 1/2 in the Strang order
 };
 
 // One request of a batched (serving) launch: its grid constants and buffers.

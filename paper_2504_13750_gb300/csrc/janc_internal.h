@@ -48,6 +48,23 @@ cudaError_t launch_rk_update_batch(int ns, int stage, const BatchReq* reqs, cons
                                    int chem, cudaStream_t st);
 cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, cudaStream_t st);
 
+// Adjoint pieces (janc_adjoint.cu).
+cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const double* mu, double* nu,
+                           double* CFx, double* CFy, double* scratch, const GridDev& g, const MechDev* mech,
+                           cudaStream_t st);
+cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, const MechDev* mech, double dt,
+                            const double* lam, double* out, cudaStream_t st);
+cudaError_t launch_lincomb(long long count, double* out, double a, const double* x, double b, const double* y,
+                           bool accumulate, cudaStream_t st);
+cudaError_t launch_loss_endwall(int ns, const StateView& S, const GridDev& g, double w, double* loss,
+                                cudaStream_t st);
+cudaError_t launch_seed_endwall(int ns, const StateView& S, const GridDev& g, const MechDev* mech, double w,
+                                double* lam, cudaStream_t st);
+cudaError_t launch_dot(long long count, const double* a, const double* b, double* out, cudaStream_t st);
+cudaError_t launch_prim_T_vjp(int ns, const double* T, const double* p, const double* u, const double* v,
+                              const double* Y, const double* dLdU, double* out, const GridDev& g,
+                              const MechDev* mech, cudaStream_t st);
+
 // L = -(dF/dx + dG/dy) from the face fluxes.
 cudaError_t launch_rhs_L(int nv, const double* Fx, const double* Gy, double* L, const GridDev& g, cudaStream_t st);
 

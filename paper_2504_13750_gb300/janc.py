@@ -99,6 +99,10 @@ def lib():
             L.janc_server_fetch.argtypes = [p, i, p, p]
             L.janc_server_destroy.argtypes = [p]
             L.janc_server_destroy.restype = None
+            L.janc_adjoint_workspace_bytes.argtypes = [p, i, i, ctypes.POINTER(ctypes.c_size_t)]
+            L.janc_step_adjoint.argtypes = [p, i, d, i, i, p, p, p, p, ctypes.c_size_t, i]
+            L.janc_rhs_vjp.argtypes = [p, p, p, p, ctypes.c_size_t, i]
+            L.janc_primitive_T_vjp.argtypes = [p, p, p, p, p, p, p, p]
             L.janc_profile.argtypes = [p, i]
             L.janc_profile_read.argtypes = [p, p, p]
             _lib = L
@@ -138,12 +142,22 @@ def _where(*args):
     return ws.pop() if ws else JANC_HOST
 
 
+CHEM_OFF, CHEM_LIE, CHEM_STRANG = 0, 1, 2
+
+
+def chem_mode(chemistry) -> int:
+    """False/True -> JANC_CHEM_OFF/JANC_CHEM_LIE, or one of the JANC_CHEM_* values."""
+    if isinstance(chemistry, bool):
+        return CHEM_LIE if chemistry else CHEM_OFF
+    return int(chemistry)
+
+
 def make_desc(nx, ny, dx, dy, bc, chemistry=True, weno_eps=1e-6, newton_tol=1e-12, newton_maxit=50):
     d = janc_grid_desc()
     d.nx, d.ny, d.dx, d.dy = int(nx), int(ny), float(dx), float(dy)
     for k in range(4):
         d.bc[k] = int(bc[k])
-    d.chemistry = int(bool(chemistry))
+    d.chemistry = chem_mode(chemistry)
     d.weno_eps, d.newton_tol, d.newton_maxit = float(weno_eps), float(newton_tol), int(newton_maxit)
     return d
 
@@ -230,6 +244,39 @@ def janc_rhs_static(desc, mech: Mechanism, U, T, L, alpha=None, stream=None):
                                  args[3][0], ctypes.c_void_p(stream) if stream else None))
 
 
+LOSS_ENDWALL_P, LOSS_SEEDED = 0, 1
+
+
+def janc_adjoint_workspace_bytes(g, n_steps, ckpt_every) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().janc_adjoint_workspace_bytes(g, int(n_steps), int(ckpt_every), ctypes.byref(out)))
+    return out.value
+
+
+def janc_step_adjoint(g, n_steps, dt, ckpt_every, loss_kind=LOSS_ENDWALL_P, seed=None, dL_dU0=None,
+                      workspace_ptr=None, workspace_bytes=0):
+    """Returns the loss; fills dL_dU0 (numpy or CUDA tensor) when given."""
+    a, b = _arg(seed), _arg(dL_dU0, True)
+    loss = ctypes.c_double()
+    _check(lib().janc_step_adjoint(g, int(n_steps), float(dt), int(ckpt_every), int(loss_kind), a[0], b[0],
+                                   ctypes.byref(loss), ctypes.c_void_p(workspace_ptr) if workspace_ptr else None,
+                                   int(workspace_bytes), _where(a, b)))
+    return loss.value
+
+
+def janc_rhs_vjp(g, mu, nu, workspace_ptr=None, workspace_bytes=0):
+    a, b = _arg(mu), _arg(nu, True)
+    _check(lib().janc_rhs_vjp(g, a[0], b[0], ctypes.c_void_p(workspace_ptr) if workspace_ptr else None,
+                              int(workspace_bytes), _where(a, b)))
+
+
+def janc_primitive_T_vjp(g, T, p, u, v, Y, dL_dU, dL_dT):
+    args = [_arg(x, True) for x in (T, p, u, v, Y, dL_dU, dL_dT)]
+    if any(x[2] is not None and x[1] != JANC_DEVICE for x in args):
+        raise ValueError("janc_primitive_T_vjp takes device tensors")
+    _check(lib().janc_primitive_T_vjp(g, *[x[0] for x in args]))
+
+
 def janc_profile(g, enable=True):
     _check(lib().janc_profile(g, int(bool(enable))))
 
@@ -269,7 +316,7 @@ def janc_selfcheck_rcp(x) -> int:
 def janc_server_create(mech: Mechanism, chemistry=True, pool_bytes=1 << 30, pool_ptr=None, max_active=64,
                        stream=None):
     h = ctypes.c_void_p()
-    _check(lib().janc_server_create(ctypes.byref(mech.c), int(bool(chemistry)), int(pool_bytes),
+    _check(lib().janc_server_create(ctypes.byref(mech.c), chem_mode(chemistry), int(pool_bytes),
                                     ctypes.c_void_p(pool_ptr) if pool_ptr else None, int(max_active),
                                     ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
     return h

@@ -118,6 +118,39 @@ def test_200_steps_tube_config1(J):
     assert abs(Ug[0].sum() - U[0].sum()) / U[0].sum() < 1e-12
 
 
+@pytest.mark.parametrize("steps", [1, 60])
+def test_strang_splitting_tube(J, steps):
+    """The Strang order (chemistry dt/2, flux dt, chemistry dt/2) on a
+    256 x 32 tube with a ragged 37-cell-wide igniting band, CFL 0.5."""
+    st = inputs.tube(H2AIR, 256, 32, perturb_seed=4)
+    st["T"][:, :37] = 1500.0
+    U = _cons(H2AIR, st)
+    g = _grid(J, H2AIR, st, chem=J.CHEM_STRANG)
+    g.set_state(U, st["T"])
+    t, _ = g.step(steps, cfl=0.5, want_time=True)
+    Ug, Tg = g.get_state()
+    Uo, To, s, to, _ = orc.step(H2AIR, st["grid"], U, st["T"], steps, cfl=0.5, chem=orc.CHEM_STRANG)
+    assert s == 0
+    tol = 1e-10 if steps == 1 else 1e-8
+    assert abs(t - to) / to < 1e-12
+    assert rel_err(Ug, Uo) < tol
+    assert rel_err(Tg[None], To[None]) < tol
+    # and it is not the Lie result
+    Ul, _, _, _, _ = orc.step(H2AIR, st["grid"], U, st["T"], steps, cfl=0.5, chem=orc.CHEM_LIE)
+    assert rel_err(Ug, Ul) > 1e3 * tol
+
+
+def test_strang_rejected_by_server_and_adjoint(J):
+    st = inputs.tube(H2AIR, 16, 8)
+    g = _grid(J, H2AIR, st, chem=J.CHEM_STRANG)
+    g.set_state(_cons(H2AIR, st), st["T"])
+    with pytest.raises(RuntimeError):
+        J.janc_step_adjoint(g.handle, 2, 1e-8, 1, J.LOSS_ENDWALL_P, None, None)
+    with pytest.raises(RuntimeError):
+        J.janc_server_create(J.Mechanism(H2AIR), chemistry=J.CHEM_STRANG)
+    g.close()
+
+
 def test_sod_gpu(J):
     import ref_exact
 

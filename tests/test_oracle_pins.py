@@ -425,6 +425,126 @@ def test_tangent_model_matches_finite_differences():
         assert np.max(np.abs(fd[k] - dU[k])) <= 1e-5 * scale + 1e-12 * np.max(np.abs(U[k])), k
 
 
+def _smooth_reacting_state(nx, ny):
+    """Premixed H2-air at 1150 K with a smooth 80 K bump, smooth p, u, v:
+    no discontinuity anywhere, unique arg-max of the LF speeds."""
+    X, Yg = np.meshgrid((np.arange(nx) + 0.5) / nx, (np.arange(ny) + 0.5) / ny)
+    T = 1150 + 80 * np.exp(-((X - 0.3) ** 2 + (Yg - 0.4) ** 2) / 0.05)
+    p = 2 * inputs.ATM * (1 + 0.05 * np.cos(2 * np.pi * X))
+    u = 5 * np.sin(2 * np.pi * Yg)
+    v = 3 * np.cos(2 * np.pi * X)
+    Y = np.repeat(inputs.h2air_Y(H2AIR, 1.0)[:, None, None], ny, 1).repeat(nx, 2)
+    g = inputs.grid_dict(nx, ny, 1e-4, 1e-4, [0, 0, 1, 1])
+    return g, T, p, u, v, Y, X, Yg
+
+
+def test_trajectory_tangent_loss_and_lanes():
+    """The trajectory tangent (reference of the adjoint tests): its loss is
+    the time-integrated end-wall pressure recomputed step by step with
+    step() and primitives(); the 1-lane and 8-lane builds agree; the tangents
+    of the loss and of U^N match Richardson-extrapolated central differences.
+
+    The differences use steps of 1.25e-3 and 6.25e-4 K: WENO-JS with an
+    absolute eps = 1e-6 on SI-unit fluxes makes the weights nonlinear where
+    neighbouring fluxes differ by ~1e-3, so directions that vary across the
+    nearly uniform rows only converge below about 1e-2 K."""
+    g, T, p, u, v, Y, X, Yg = _smooth_reacting_state(12, 6)
+    U = orc.prim_to_cons(H2AIR, T, p, u, v, Y)
+    dt, n = 2e-8, 4
+    Uc, Tc, L_def = U.copy(), T.copy(), 0.0
+    for _ in range(n):
+        Uc, Tc, s, _, _ = orc.step(H2AIR, g, Uc, Tc, 1, dt=dt)
+        assert s == 0
+        L_def += dt * np.mean(orc.primitives(H2AIR, Uc, Tc)[0][:, -1])
+    dirs = [np.cos(np.pi * Yg), X, np.cos(np.pi * X) * np.cos(np.pi * Yg)]
+    h = 1e-3
+    V = np.stack([(orc.prim_to_cons(H2AIR, T + h * d, p, u, v, Y) - orc.prim_to_cons(H2AIR, T - h * d, p, u, v, Y))
+                  / (2 * h) for d in dirs])
+    dUN8, L8, dL8, s8 = orc.trajectory_tangent(H2AIR, g, U, T, V, n, dt)
+    assert s8 == 0
+    assert abs(L8 - L_def) <= 1e-13 * abs(L_def)
+    for l in range(len(dirs)):
+        dUN1, L1, dL1, s1 = orc.trajectory_tangent(H2AIR, g, U, T, V[l:l + 1], n, dt)
+        assert s1 == 0 and L1 == L8
+        assert abs(dL1[0] - dL8[l]) <= 1e-13 * abs(dL8[l])
+        assert np.allclose(dUN1[0], dUN8[l], rtol=1e-12, atol=0)
+
+    def loss_UN(eps, d):
+        Te = T + eps * d
+        Ue, L = orc.prim_to_cons(H2AIR, Te, p, u, v, Y), 0.0
+        for _ in range(n):
+            Ue, Te, _, _, _ = orc.step(H2AIR, g, Ue, Te, 1, dt=dt)
+            L += dt * np.mean(orc.primitives(H2AIR, Ue, Te)[0][:, -1])
+        return L, Ue
+
+    for l, d in enumerate(dirs):
+        fd = []
+        for hh in (1.25e-3, 6.25e-4):
+            (Lp, Up), (Lm, Um) = loss_UN(hh, d), loss_UN(-hh, d)
+            fd.append(((Lp - Lm) / (2 * hh), (Up - Um) / (2 * hh)))
+        fdL = (4 * fd[1][0] - fd[0][0]) / 3
+        fdU = (4 * fd[1][1] - fd[0][1]) / 3
+        assert abs(fdL - dL8[l]) <= 1e-5 * abs(dL8[l]), (l, fdL, dL8[l])
+        for k in range(U.shape[0]):
+            scale = np.max(np.abs(dUN8[l, k]))
+            if scale == 0.0:
+                continue
+            assert np.max(np.abs(fdU[k] - dUN8[l, k])) <= 1e-5 * scale + 1e-13 * np.max(np.abs(U[k])), (l, k)
+
+
+def _igniting_state(nx=10, ny=4, seed=5):
+    st = inputs.tube(H2AIR, nx, ny)
+    rng = np.random.default_rng(seed)
+    st["T"] = 1400.0 + 200.0 * rng.random(st["T"].shape)
+    st["p"] = np.full_like(st["T"], 5 * inputs.ATM)
+    st["u"] = rng.normal(0.0, 20.0, st["T"].shape)
+    return st, _cons(H2AIR, st)
+
+
+def test_strang_step_is_half_chemistry_flux_half_chemistry():
+    """CHEM_STRANG = chemistry(dt/2), flux RK3(dt), chemistry(dt/2) (the
+    Strang order Sec. 4.3 names), assembled here from the oracle's separate
+    entry points: point_implicit + newton, and a flux-only step."""
+    st, U = _igniting_state()
+    g, T = st["grid"], st["T"]
+    dt = 2e-8
+
+    def half_chem(U, T):
+        Uc, s1 = orc.point_implicit(H2AIR, U, T, 0.5 * dt)
+        Tc, s2 = orc.newton(H2AIR, g, Uc, T)
+        assert s1 == 0 and s2 == 0
+        return Uc, Tc
+
+    Ua, Ta = half_chem(U, T)
+    Ub, Tb, s, _, _ = orc.step(H2AIR, g, Ua, Ta, 1, dt=dt, chem=False)
+    assert s == 0
+    Uc, Tc = half_chem(Ub, Tb)
+    Us, Ts, s, _, _ = orc.step(H2AIR, g, U, T, 1, dt=dt, chem=orc.CHEM_STRANG)
+    assert s == 0
+    assert np.array_equal(Us, Uc) and np.array_equal(Ts, Tc)
+    # and the Lie step is flux then a full chemistry step
+    Ul, Tl, s, _, _ = orc.step(H2AIR, g, U, T, 1, dt=dt, chem=orc.CHEM_LIE)
+    Uf, Tf, _, _, _ = orc.step(H2AIR, g, U, T, 1, dt=dt, chem=False)
+    Uf2, _ = orc.point_implicit(H2AIR, Uf, Tf, dt)
+    assert np.array_equal(Ul, Uf2)
+
+
+def test_strang_and_lie_differ_at_second_order_per_step():
+    """Both orders split the same two operators, so one step of each differs
+    by O(dt^2) (the commutator term): halving dt divides the difference by
+    about 4. A missing or doubled half step would leave an O(dt) gap."""
+    st, U = _igniting_state()
+    g, T = st["grid"], st["T"]
+    diffs = []
+    for dt in (4e-8, 2e-8, 1e-8):
+        Ul, _, s1, _, _ = orc.step(H2AIR, g, U, T, 1, dt=dt, chem=orc.CHEM_LIE)
+        Us, _, s2, _, _ = orc.step(H2AIR, g, U, T, 1, dt=dt, chem=orc.CHEM_STRANG)
+        assert s1 == 0 and s2 == 0
+        diffs.append(np.max(np.abs(Ul[4:] - Us[4:])))
+    r1, r2 = diffs[0] / diffs[1], diffs[1] / diffs[2]
+    assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0, (diffs, r1, r2)
+
+
 def test_opcount_is_positive_and_fixed():
     g = inputs.grid_dict(8, 4, 1.0, 1.0, [0] * 4)
     ops = orc.opcount(H2AIR, g, 0)
