@@ -197,7 +197,7 @@ def test_config4_gradient_vs_oracle_tangent_and_differences(J):
 
     L0, ref = oracle_tangents(base)
     _, ref_shift = oracle_tangents(base + 1e-12 * np.random.default_rng(99).normal(size=base.shape))
-    assert abs(float(L) - L0) <= 1e-10 * abs(L0)
+    assert abs(float(L.detach()) - L0) <= 1e-10 * abs(L0)
     for l, (name, w) in enumerate(lanes.items()):
         ad = float(np.sum(grad * w))
         spread = abs(ref[l] - ref_shift[l])
@@ -245,5 +245,5 @@ def test_config4_500_step_loss_and_finite_gradient(J):
     orc.set_threads(0)
     _, L0, _, s = orc.trajectory_tangent(H2AIR, st["grid"], U0, base, np.zeros((1,) + U0.shape), 500, dt, chem=True)
     assert s == 0
-    assert abs(float(L) - L0) <= 1e-10 * abs(L0), (float(L), L0)
+    assert abs(float(L.detach()) - L0) <= 1e-10 * abs(L0), (float(L.detach()), L0)
     g.close()
