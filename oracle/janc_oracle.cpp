@@ -249,6 +249,38 @@ double orc_cfl_dt(const orc_mech_c* mc, const orc_grid_c* gc, const double* U, c
 
 // n time steps in place. Exactly one of dt > 0 (fixed step) or cfl > 0.
 // dt_log (may be null) receives the dt of every step.
+// Right-hand side of an nx x ny field given with its 3 ghost layers
+// (Up[nv][ny+6][nx+6], Tp[ny+6][nx+6]; corners ignored) and given LF speeds;
+// the building block of a refined block's update, whose ghosts come from its
+// neighbours. L: [nv][ny][nx].
+int orc_rhs_ghosted(const orc_mech_c* mc, const orc_grid_c* gc, const double* Up, const double* Tp, double ax,
+                    double ay, double* L) {
+  Mech m = to_mech(mc);
+  Grid g = to_grid(gc);
+  Field<double> P;
+  P.resize(nvar_of(m), g.nx + 6, g.ny + 6);
+  std::memcpy(P.U.data(), Up, sizeof(double) * P.U.size());
+  std::memcpy(P.T.data(), Tp, sizeof(double) * P.T.size());
+  std::vector<double> Lv;
+  rhs_ghosted(m, g, P, ax, ay, Lv);
+  std::memcpy(L, Lv.data(), sizeof(double) * Lv.size());
+  return 0;
+}
+
+// LF speeds (alpha_x, alpha_y) of Eq. 4.11 over n cells U[nv][n], T[n].
+int orc_lf_alpha(const orc_mech_c* mc, int n, const double* U, const double* T, double* alpha) {
+  Mech m = to_mech(mc);
+  Field<double> F;
+  F.resize(nvar_of(m), n, 1);
+  std::memcpy(F.U.data(), U, sizeof(double) * F.U.size());
+  std::memcpy(F.T.data(), T, sizeof(double) * F.T.size());
+  double ax, ay;
+  lf_alpha(m, F, &ax, &ay);
+  alpha[0] = ax;
+  alpha[1] = ay;
+  return 0;
+}
+
 int orc_step(const orc_mech_c* mc, const orc_grid_c* gc, double* U, double* T, int nsteps, double dt,
              double cfl, int chem, double* t_out, double* dt_log) {
   Mech m = to_mech(mc);

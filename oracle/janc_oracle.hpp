@@ -517,40 +517,38 @@ template <class S> void lf_alpha(const Mech& m, const Field<S>& F, S* ax, S* ay)
 }
 
 // Right-hand side L(U) = -(F_{i+1/2}-F_{i-1/2})/dx - (G_{j+1/2}-G_{j-1/2})/dy
-// (Eq. 4.10 without the source; the chemistry is split off), with the flux
+// (Eq. 4.10 without the source; the chemistry is split off) of a field whose
+// ghost layers and LF speeds alpha_x, alpha_y (Eq. 4.11) are given: the flux
 // split of Eq. 4.11 and WENO5 reconstruction of F+ and F- at every face.
 // Optionally returns the face fluxes Fx[nv][ny][nx+1] (face i-1/2 at index i)
 // and Gy[nv][ny+1][nx] (face j-1/2 at index j).
-template <class S> void rhs(const Mech& m, const Grid& g, const Field<S>& F, std::vector<S>& L,
-                            std::vector<S>* Fx_out = nullptr, std::vector<S>* Gy_out = nullptr,
-                            S* ax_out = nullptr, S* ay_out = nullptr) {
-  const int nv = F.nv, nx = F.nx, ny = F.ny;
-  S ax, ay;
-  lf_alpha(m, F, &ax, &ay);
-  if (ax_out) *ax_out = ax;
-  if (ay_out) *ay_out = ay;
+template <class S> void rhs_ghosted(const Mech& m, const Grid& g, const Field<S>& P, const S& ax, const S& ay,
+                                    std::vector<S>& L, std::vector<S>* Fx_out = nullptr,
+                                    std::vector<S>* Gy_out = nullptr) {
+  // P is the field extended by 3 ghost cells on every side (P.nx = nx + 6,
+  // P.ny = ny + 6; interior cell (i, j) at (i + 3, j + 3)). The x sweep reads
+  // the ghost columns of the interior rows, the y sweep the ghost rows of the
+  // interior columns; the corners are never read.
+  const int nv = P.nv, nx = P.nx - 6, ny = P.ny - 6;
   L.assign((size_t)nv * nx * ny, S(0.0));
   std::vector<S> Fx((size_t)nv * ny * (nx + 1)), Gy((size_t)nv * (ny + 1) * nx);
 
-  // x direction: one row at a time, extended by 3 ghost cells on each side.
+  // x direction: one row at a time.
   #pragma omp parallel for schedule(static)
   for (int j = 0; j < ny; ++j) {
     const int ne = nx + 6;
     std::vector<S> Fp((size_t)nv * ne), Fm((size_t)nv * ne);
     for (int ie = 0; ie < ne; ++ie) {
-      bool flip;
-      int si = ghost_src(ie - 3, nx, g.bc[0], g.bc[1], &flip);
       S u[16];
-      for (int k = 0; k < nv; ++k) u[k] = F.u(k, si, j);
-      if (flip) u[1] = -u[1];
-      Prim<S> P = primitives(m, u, F.t(si, j));
+      for (int k = 0; k < nv; ++k) u[k] = P.u(k, ie, j + 3);
+      Prim<S> Q = primitives(m, u, P.t(ie, j + 3));
       // flux F of Eq. 4.1
       S f[16];
       f[0] = u[1];
-      f[1] = u[1] * P.u + P.p;
-      f[2] = u[2] * P.u;
-      f[3] = (u[3] + P.p) * P.u;
-      for (int k = 4; k < nv; ++k) f[k] = u[k] * P.u;
+      f[1] = u[1] * Q.u + Q.p;
+      f[2] = u[2] * Q.u;
+      f[3] = (u[3] + Q.p) * Q.u;
+      for (int k = 4; k < nv; ++k) f[k] = u[k] * Q.u;
       for (int k = 0; k < nv; ++k) {
         Fp[(size_t)k * ne + ie] = 0.5 * (f[k] + ax * u[k]);
         Fm[(size_t)k * ne + ie] = 0.5 * (f[k] - ax * u[k]);
@@ -574,18 +572,15 @@ template <class S> void rhs(const Mech& m, const Grid& g, const Field<S>& F, std
     const int ne = ny + 6;
     std::vector<S> Gp((size_t)nv * ne), Gm((size_t)nv * ne);
     for (int je = 0; je < ne; ++je) {
-      bool flip;
-      int sj = ghost_src(je - 3, ny, g.bc[2], g.bc[3], &flip);
       S u[16];
-      for (int k = 0; k < nv; ++k) u[k] = F.u(k, i, sj);
-      if (flip) u[2] = -u[2];
-      Prim<S> P = primitives(m, u, F.t(i, sj));
+      for (int k = 0; k < nv; ++k) u[k] = P.u(k, i + 3, je);
+      Prim<S> Q = primitives(m, u, P.t(i + 3, je));
       S f[16];
       f[0] = u[2];
-      f[1] = u[1] * P.v;
-      f[2] = u[2] * P.v + P.p;
-      f[3] = (u[3] + P.p) * P.v;
-      for (int k = 4; k < nv; ++k) f[k] = u[k] * P.v;
+      f[1] = u[1] * Q.v;
+      f[2] = u[2] * Q.v + Q.p;
+      f[3] = (u[3] + Q.p) * Q.v;
+      for (int k = 4; k < nv; ++k) f[k] = u[k] * Q.v;
       for (int k = 0; k < nv; ++k) {
         Gp[(size_t)k * ne + je] = 0.5 * (f[k] + ay * u[k]);
         Gm[(size_t)k * ne + je] = 0.5 * (f[k] - ay * u[k]);
@@ -612,6 +607,48 @@ template <class S> void rhs(const Mech& m, const Grid& g, const Field<S>& F, std
       }
   if (Fx_out) *Fx_out = Fx;
   if (Gy_out) *Gy_out = Gy;
+}
+
+// The field extended by the 3 ghost layers of the physical boundaries (text
+// after Eq. 4.11): ghost_src along each axis; a wall mirror negates the
+// wall-normal momentum. Corners are left at zero (never read).
+template <class S> Field<S> pad_physical(const Grid& g, const Field<S>& F) {
+  Field<S> P;
+  P.resize(F.nv, F.nx + 6, F.ny + 6);
+  for (int j = 0; j < F.ny; ++j)
+    for (int ie = 0; ie < F.nx + 6; ++ie) {
+      bool flip;
+      int si = ghost_src(ie - 3, F.nx, g.bc[0], g.bc[1], &flip);
+      for (int k = 0; k < F.nv; ++k) P.u(k, ie, j + 3) = F.u(k, si, j);
+      if (flip) P.u(1, ie, j + 3) = -P.u(1, ie, j + 3);
+      P.t(ie, j + 3) = F.t(si, j);
+    }
+  for (int i = 0; i < F.nx; ++i)
+    for (int je = 0; je < F.ny + 6; ++je) {
+      if (je >= 3 && je < F.ny + 3) continue;
+      bool flip;
+      int sj = ghost_src(je - 3, F.ny, g.bc[2], g.bc[3], &flip);
+      for (int k = 0; k < F.nv; ++k) P.u(k, i + 3, je) = F.u(k, i, sj);
+      if (flip) P.u(2, i + 3, je) = -P.u(2, i + 3, je);
+      P.t(i + 3, je) = F.t(i, sj);
+    }
+  return P;
+}
+
+// Right-hand side L(U) = -(dF/dx + dG/dy) of the semi-discrete equation
+// (Eq. 4.10 without the source; the chemistry is split off), with the flux
+// split of Eq. 4.11 and WENO5 reconstruction of F+ and F- at every face:
+// the physical ghost layers, the global LF speeds of the interior cells, then
+// rhs_ghosted. Optionally returns the face fluxes Fx[nv][ny][nx+1] (face
+// i-1/2 at index i) and Gy[nv][ny+1][nx] (face j-1/2 at index j).
+template <class S> void rhs(const Mech& m, const Grid& g, const Field<S>& F, std::vector<S>& L,
+                            std::vector<S>* Fx_out = nullptr, std::vector<S>* Gy_out = nullptr,
+                            S* ax_out = nullptr, S* ay_out = nullptr) {
+  S ax, ay;
+  lf_alpha(m, F, &ax, &ay);
+  if (ax_out) *ax_out = ax;
+  if (ay_out) *ay_out = ay;
+  rhs_ghosted(m, g, pad_physical(g, F), ax, ay, L, Fx_out, Gy_out);
 }
 
 // Newton T for every cell of `out`, warm-started from `warm`'s T.

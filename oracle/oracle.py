@@ -89,6 +89,8 @@ def lib():
             _lib.orc_opcount.argtypes = [p, p, i, p, p, d, p]
             _lib.orc_rhs_tangent.argtypes = [p, p, p, p, p, p]
             _lib.orc_trajectory_tangent8.argtypes = [p, p, p, p, p, i, i, d, i, p, p]
+            _lib.orc_rhs_ghosted.argtypes = [p, p, p, p, d, d, p]
+            _lib.orc_lf_alpha.argtypes = [p, i, p, p, p]
         return _lib
 
 
@@ -236,6 +238,31 @@ def rhs(mech, grid, U, T):
     al = np.zeros(2)
     lib().orc_rhs(mh.ref, ctypes.byref(_grid(grid)), _ptr(U), _ptr(T), _ptr(L), _ptr(Fx), _ptr(Gy), _ptr(al))
     return L, Fx, Gy, al
+
+
+def rhs_ghosted(mech, nx, ny, dx, dy, Up, Tp, alpha, weno_eps=1e-6):
+    """L(U) of an nx x ny field given with its 3 ghost layers Up[nv, ny+6,
+    nx+6], Tp[ny+6, nx+6] (corners ignored) and given LF speeds alpha =
+    (alpha_x, alpha_y) of Eq. 4.11."""
+    mh = _MechHandle(mech)
+    nv = nvar(mech)
+    Up, Tp = _f64(Up), _f64(Tp)
+    assert Up.shape == (nv, ny + 6, nx + 6) and Tp.shape == (ny + 6, nx + 6)
+    g = {"nx": nx, "ny": ny, "dx": dx, "dy": dy, "bc": [0, 0, 0, 0], "weno_eps": weno_eps}
+    L = np.zeros((nv, ny, nx))
+    lib().orc_rhs_ghosted(mh.ref, ctypes.byref(_grid(g)), _ptr(Up), _ptr(Tp), float(alpha[0]), float(alpha[1]),
+                          _ptr(L))
+    return L
+
+
+def lf_alpha(mech, U, T):
+    """(alpha_x, alpha_y) of Eq. 4.11: max over the given cells of |u|+c and |v|+c."""
+    mh = _MechHandle(mech)
+    U = _f64(U)
+    n = U[0].size
+    a = np.zeros(2)
+    lib().orc_lf_alpha(mh.ref, n, _ptr(U.reshape(nvar(mech), n)), _ptr(_f64(T).ravel()), _ptr(a))
+    return a
 
 
 def cfl_dt(mech, grid, U, T, cfl):
