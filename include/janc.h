@@ -327,6 +327,58 @@ void janc_server_destroy(janc_server_t s);
 int janc_rhs_static(const janc_grid_desc* d, const janc_mechanism* m, const double* U, const double* T,
                     double* L, double* alpha, void* cuda_stream);
 
+/* ---- Block-structured adaptive mesh refinement (Sec. 3) -------------------------------------
+ * Layer 0 is the base grid of the descriptor (physical boundaries). Layer i
+ * (1 <= i <= levels) holds blocks of 16 x 16 cells at twice the resolution of
+ * layer i-1, at fixed positions (block (bx, by) covers the layer-i cells
+ * [16 bx, 16 bx + 16) x [16 by, 16 by + 16)), nested in the blocks of layer
+ * i-1 (Sec. 3.1.1). A block is refined where a cell of layer i-1 within
+ * n_buffer cells of its parent region has |grad T| > threshold (K/m; central
+ * differences, Sec. 3.1.2). Per base step (Algorithm 2): regrid every
+ * regrid_every steps (blocks kept across a regrid keep their data, new blocks
+ * copy their parent one-to-four), the crossover advance (layer i+1 takes two
+ * steps of dt/2 before each step of layer i), each layer solved as in
+ * Algorithm 3 (ghost blocks from the same-layer neighbours or the physical
+ * boundary; cells within 3 of a side with no neighbour take the layer-(i-1)
+ * values after every RK stage; chemistry over the layer's dt), then the
+ * four-to-one mean from the deepest layer up. The base dt is fixed or the CFL
+ * of layer 0 at the step's start; layer i uses dt / 2^i. Chemistry:
+ * JANC_CHEM_OFF or JANC_CHEM_LIE. nx, ny of the base must be multiples of 8. */
+typedef struct janc_amr_s* janc_amr_t;
+
+typedef struct {
+  int levels;         /* refined layers above the base, 0..6 */
+  int block;          /* block edge in cells; must be 16 */
+  double threshold;   /* refinement criterion |grad T| > threshold, K/m */
+  int n_buffer;       /* buffer cells around the masked cells (layer i-1 cells) */
+  int regrid_every;   /* base steps between regrids (>= 1); step 0 builds the layers */
+} janc_amr_desc;
+
+/* Create an AMR hierarchy over the base grid `base` (device memory owned by
+ * the object; the layers grow and shrink with the block count). */
+int janc_amr_create(const janc_grid_desc* base, const janc_mechanism* m, const janc_amr_desc* a, void* cuda_stream,
+                    janc_amr_t* out);
+/* Base-layer state from primitive fields, as janc_set_state_primitive; the
+ * refined layers are rebuilt at the next step. */
+int janc_amr_set_state_primitive(janc_amr_t a, const double* T, const double* p, const double* u, const double* v,
+                                 const double* Y, int where);
+/* n base steps with a fixed dt (> 0) or the CFL number (> 0); t_out (may be
+ * null) receives the simulated time advanced. */
+int janc_amr_step(janc_amr_t a, int n_steps, double dt, double cfl, double* t_out);
+/* Blocks of layer `level` (1..levels). */
+int janc_amr_layer_blocks(janc_amr_t a, int level, int* nblk);
+/* Host copy of layer `level`: pos[2 b] = bx, pos[2 b + 1] = by of block b
+ * (blocks in (by, bx) order), U [nblk][nv][16][16], T [nblk][16][16]; any
+ * pointer may be null. Synchronous. */
+int janc_amr_get_layer(janc_amr_t a, int level, int* pos, double* U, double* T);
+/* Base-layer state (after the last step's four-to-one means), as janc_get_state. */
+int janc_amr_get_base(janc_amr_t a, double* U, double* T, int where);
+/* OR of the JANC_ST_* bits of every layer since creation. Synchronous. */
+int janc_amr_status(janc_amr_t a, int* status);
+/* Cell updates of the last base step: base cells + sum over layers of 2^i x cells. */
+int janc_amr_cell_updates(janc_amr_t a, long long* per_step);
+void janc_amr_destroy(janc_amr_t a);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,8 @@ structure, in the paper's terms:
   in the same layer (EXTERNAL where there is none inside the domain,
   PHYSICAL where the side lies on a wall or zero-gradient boundary).
 * get_refinement_grid_mask: layer-(i-1) cells with |grad T| > threshold, by
-  central differences inside the grid or block (one-sided at its edges);
+  central differences over the layer, one-sided where the neighbouring cell
+  is outside the domain or outside the layer's valid blocks;
   buffer grids: the mask dilated by n_buffer cells (Chebyshev distance).
   get_refinement_block_mask: a subregion is refined when it holds a masked or
   buffer cell and its parent block is valid (Sec. 3.1.2).
@@ -146,27 +147,44 @@ class AMROracle:
 
     # ---- refinement (Sec. 3.1.2) ----------------------------------------------------------------
     @staticmethod
-    def grad_T(T, dx, dy):
-        """|grad T| by central differences, one-sided at the array's edges."""
+    def grad_T(T, dx, dy, valid=None):
+        """|grad T| by central differences; one-sided where the neighbour is
+        outside the array or not valid; 0 on invalid cells."""
         ny, nx = T.shape
-        ip, im = np.minimum(np.arange(nx) + 1, nx - 1), np.maximum(np.arange(nx) - 1, 0)
-        jp, jm = np.minimum(np.arange(ny) + 1, ny - 1), np.maximum(np.arange(ny) - 1, 0)
-        gx = (T[:, ip] - T[:, im]) / ((ip - im)[None, :] * dx) if nx > 1 else np.zeros_like(T)
-        gy = (T[jp, :] - T[jm, :]) / ((jp - jm)[:, None] * dy) if ny > 1 else np.zeros_like(T)
-        return np.sqrt(gx * gx + gy * gy)
+        if valid is None:
+            valid = np.ones(T.shape, dtype=bool)
+        g = np.zeros_like(T)
+        for j in range(ny):
+            for i in range(nx):
+                if not valid[j, i]:
+                    continue
+                ip = i + 1 if i + 1 < nx and valid[j, i + 1] else i
+                im = i - 1 if i > 0 and valid[j, i - 1] else i
+                jp = j + 1 if j + 1 < ny and valid[j + 1, i] else j
+                jm = j - 1 if j > 0 and valid[j - 1, i] else j
+                gx = (T[j, ip] - T[j, im]) / ((ip - im) * dx) if ip != im else 0.0
+                gy = (T[jp, i] - T[jm, i]) / ((jp - jm) * dy) if jp != jm else 0.0
+                g[j, i] = np.sqrt(gx * gx + gy * gy)
+        return g
+
+    def layer_T(self, i):
+        """T of layer i over its whole index space and the mask of valid cells."""
+        if i == 0:
+            return self.T0, np.ones(self.T0.shape, dtype=bool)
+        nx, ny = self.ncols(i)
+        T = np.zeros((ny, nx))
+        valid = np.zeros((ny, nx), dtype=bool)
+        L, B = self.layers[i], self.B
+        for k, (bx, by) in enumerate(L.pos):
+            T[by * B:(by + 1) * B, bx * B:(bx + 1) * B] = L.T[k]
+            valid[by * B:(by + 1) * B, bx * B:(bx + 1) * B] = True
+        return T, valid
 
     def refinement_grid_mask(self, i):
         """get_refinement_grid_mask on layer i-1, in layer-(i-1) global cells."""
-        nx, ny = self.ncols(i - 1)
         dx, dy = self.h(i - 1)
-        mask = np.zeros((ny, nx), dtype=bool)
-        if i - 1 == 0:
-            mask[:] = self.grad_T(self.T0, dx, dy) > self.threshold
-        else:
-            L, B = self.layers[i - 1], self.B
-            for k, (bx, by) in enumerate(L.pos):
-                mask[by * B:(by + 1) * B, bx * B:(bx + 1) * B] = self.grad_T(L.T[k], dx, dy) > self.threshold
-        return mask
+        T, valid = self.layer_T(i - 1)
+        return self.grad_T(T, dx, dy, valid) > self.threshold
 
     def refinement_block_mask(self, i):
         """get_refinement_block_mask: the set of (bx, by) of layer i to refine."""

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libjanc.so")
-SOURCES = ["janc_flux.cu", "janc_update.cu", "janc_chem.cu", "janc_capi.cu", "janc_probe.cu", "janc_static.cu", "janc_server.cu", "janc_adjoint.cu"]
+SOURCES = ["janc_flux.cu", "janc_update.cu", "janc_chem.cu", "janc_capi.cu", "janc_probe.cu", "janc_static.cu", "janc_server.cu", "janc_adjoint.cu", "janc_amr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -214,6 +214,22 @@ cudaError_t timed(janc_grid_s* g, int cls, F&& f) {
 
 static StateView sv(const janc_grid_s* g, int k) { return StateView{g->S[k]}; }
 
+namespace janc {
+GridParts grid_parts(janc_grid_t g) {
+  GridParts p;
+  p.S0 = StateView{g->S[0]};
+  p.gd = g->gd;
+  p.mech = g->mech;
+  p.alpha = g->alpha;
+  p.status = g->status;
+  p.stream = g->stream;
+  p.ns = g->ns;
+  p.nv = g->nv;
+  p.chemistry = g->d.chemistry;
+  return p;
+}
+}  // namespace janc
+
 extern "C" {
 
 const char* janc_last_error(void) { return g_err.c_str(); }

@@ -179,6 +179,37 @@ __device__ __forceinline__ double step_dt(const StepCtl& c, const unsigned long 
   return c.cfl * c.hmin / amax;
 }
 
+// Sound speed exactly as newton_cell finishes it, from the stored T.
+template <int NS>
+__device__ __forceinline__ double sound_speed(const double* u, double t, const MechDev& m) {
+  const double rrho = rcp(u[0]);
+  double z[NS];
+  double rest = u[0];
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) {
+    z[k] = u[4 + k] * m.invM[k];
+    rest -= u[4 + k];
+  }
+  z[NS - 1] = rest * m.invM[NS - 1];
+  double W = z[0];
+#pragma unroll
+  for (int k = 1; k < NS; ++k) W += z[k];
+  double h[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    double s = z[0] * m.hc[0][q];
+#pragma unroll
+    for (int k = 1; k < NS; ++k) s = fma(z[k], m.hc[k][q], s);
+    h[q] = s;
+  }
+  const double c1 = 2.0 * h[1], c2 = 3.0 * h[2], c3 = 4.0 * h[3], c4 = 5.0 * h[4];
+  const double K1 = h[0] - W;
+  const double Cv = fma(t, fma(t, fma(t, fma(t, c4, c3), c2), c1), K1);
+  const double Cp = Cv + W;
+  const double p = RU * W * t;
+  return sqrt(Cp * p * rrho * rcp(Cv));
+}
+
 // Ghost-cell source index along one axis (3 layers, text after Eq. 4.11).
 __device__ __forceinline__ int ghost_src(int i, int n, int bc_lo, int bc_hi, bool& flip) {
   flip = false;

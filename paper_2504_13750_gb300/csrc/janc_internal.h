@@ -13,6 +13,20 @@ int build_mech_table(const janc_mechanism* m, MechDev* h);
 // Sets the text janc_last_error() returns on this thread (janc_capi.cu).
 void set_last_error(const char* msg);
 
+// The device pieces of a grid object that other subsystems drive directly
+// (janc_capi.cu): its current state U^n, constants, mechanism table, alpha
+// slot 0 (the state's LF speeds), status word and stream.
+struct GridParts {
+  StateView S0;
+  GridDev gd;
+  const MechDev* mech;
+  unsigned long long* alpha;
+  int* status;
+  cudaStream_t stream;
+  int ns, nv, chemistry;
+};
+GridParts grid_parts(janc_grid_t g);
+
 // LF-split WENO5 face fluxes of state S (janc_flux.cu).
 cudaError_t launch_face_flux(int nv, const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
                              const GridDev& g, cudaStream_t st);

@@ -105,6 +105,16 @@ def lib():
             L.janc_primitive_T_vjp.argtypes = [p, p, p, p, p, p, p, p]
             L.janc_profile.argtypes = [p, i]
             L.janc_profile_read.argtypes = [p, p, p]
+            L.janc_amr_create.argtypes = [p, p, p, p, ctypes.POINTER(p)]
+            L.janc_amr_set_state_primitive.argtypes = [p, p, p, p, p, p, i]
+            L.janc_amr_step.argtypes = [p, i, d, d, ctypes.POINTER(d)]
+            L.janc_amr_layer_blocks.argtypes = [p, i, ctypes.POINTER(i)]
+            L.janc_amr_get_layer.argtypes = [p, i, p, p, p]
+            L.janc_amr_get_base.argtypes = [p, p, p, i]
+            L.janc_amr_status.argtypes = [p, ctypes.POINTER(i)]
+            L.janc_amr_cell_updates.argtypes = [p, ctypes.POINTER(ctypes.c_longlong)]
+            L.janc_amr_destroy.argtypes = [p]
+            L.janc_amr_destroy.restype = None
             _lib = L
         return _lib
 
@@ -424,6 +434,122 @@ class Grid:
     def close(self):
         if getattr(self, "handle", None):
             janc_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- block-structured AMR ------------------------------------------------------------------
+
+
+class AmrDesc(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("block", ctypes.c_int), ("threshold", ctypes.c_double),
+                ("n_buffer", ctypes.c_int), ("regrid_every", ctypes.c_int)]
+
+
+def janc_amr_create(desc, mech: Mechanism, amr: AmrDesc, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().janc_amr_create(ctypes.byref(desc), ctypes.byref(mech.c), ctypes.byref(amr),
+                                 ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+    return h
+
+
+def janc_amr_set_state_primitive(a, T, p, u, v, Y):
+    args = [_arg(x) for x in (T, p, u, v, Y)]
+    _check(lib().janc_amr_set_state_primitive(a, *[x[0] for x in args], _where(*args)))
+
+
+def janc_amr_step(a, n_steps, dt=0.0, cfl=0.0):
+    """Advances n base steps; returns the simulated time advanced."""
+    t = ctypes.c_double()
+    _check(lib().janc_amr_step(a, int(n_steps), float(dt), float(cfl), ctypes.byref(t)))
+    return t.value
+
+
+def janc_amr_layer_blocks(a, level):
+    n = ctypes.c_int()
+    _check(lib().janc_amr_layer_blocks(a, int(level), ctypes.byref(n)))
+    return n.value
+
+
+def janc_amr_get_layer(a, level, nv):
+    """(pos [nblk, 2] as (bx, by), U [nblk, nv, 16, 16], T [nblk, 16, 16]) on the host."""
+    nb = janc_amr_layer_blocks(a, level)
+    pos = np.zeros((nb, 2), dtype=np.int32)
+    U = np.zeros((nb, nv, 16, 16))
+    T = np.zeros((nb, 16, 16))
+    _check(lib().janc_amr_get_layer(a, int(level), pos.ctypes.data_as(ctypes.c_void_p),
+                                    U.ctypes.data_as(ctypes.c_void_p), T.ctypes.data_as(ctypes.c_void_p)))
+    return pos, U, T
+
+
+def janc_amr_get_base(a, U, T):
+    ua, ta = _arg(U, True), _arg(T, True)
+    _check(lib().janc_amr_get_base(a, ua[0], ta[0], _where(ua, ta)))
+
+
+def janc_amr_status(a):
+    s = ctypes.c_int()
+    _check(lib().janc_amr_status(a, ctypes.byref(s)))
+    return s.value
+
+
+def janc_amr_cell_updates(a):
+    n = ctypes.c_longlong()
+    _check(lib().janc_amr_cell_updates(a, ctypes.byref(n)))
+    return n.value
+
+
+def janc_amr_destroy(a):
+    lib().janc_amr_destroy(a)
+
+
+class Amr:
+    """Owner of one AMR hierarchy (janc_amr_*) on the current CUDA stream."""
+
+    def __init__(self, mech: dict, grid: dict, chemistry=True, levels=2, threshold=1e6, n_buffer=2,
+                 regrid_every=10, stream=None):
+        import torch
+
+        self.mech = Mechanism(mech)
+        self.nv = self.mech.ns + 3
+        self.nx, self.ny = int(grid["nx"]), int(grid["ny"])
+        self.levels = int(levels)
+        self.desc = make_desc(grid["nx"], grid["ny"], grid["dx"], grid["dy"], grid["bc"], chemistry=chemistry,
+                              weno_eps=grid.get("weno_eps", 1e-6), newton_tol=grid.get("newton_tol", 1e-12),
+                              newton_maxit=grid.get("newton_maxit", 50))
+        self.amr = AmrDesc(int(levels), 16, float(threshold), int(n_buffer), int(regrid_every))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = janc_amr_create(self.desc, self.mech, self.amr, self.stream.cuda_stream)
+
+    def set_primitive(self, T, p, u, v, Y):
+        janc_amr_set_state_primitive(self.handle, T, p, u, v, Y)
+
+    def step(self, n=1, dt=0.0, cfl=0.0):
+        return janc_amr_step(self.handle, n, dt=dt, cfl=cfl)
+
+    def base(self):
+        U = np.zeros((self.nv, self.ny, self.nx))
+        T = np.zeros((self.ny, self.nx))
+        janc_amr_get_base(self.handle, U, T)
+        return U, T
+
+    def layer(self, level):
+        return janc_amr_get_layer(self.handle, level, self.nv)
+
+    def status(self):
+        return janc_amr_status(self.handle)
+
+    def cell_updates(self):
+        return janc_amr_cell_updates(self.handle)
+
+    def close(self):
+        if self.handle:
+            janc_amr_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,116 @@
+"""Block-structured AMR on the GPU (janc_amr_*) against the AMR oracle
+(oracle/amr.py): the same block lists (bit-exact), the base layer and every
+refined layer within the per-step floating-point tolerance, on a reacting
+tube with walls and on a Riemann problem with zero-gradient and periodic
+sides."""
+import numpy as np
+import pytest
+
+import oracle as orc
+from amr import AMROracle
+from paper_2504_13750_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+H2AIR = inputs.load_mechanism("h2air_synth")
+GAS = inputs.load_mechanism("ideal_gamma14")
+
+
+@pytest.fixture(scope="module")
+def J():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_13750_gb300 import build, janc
+
+    build.build()
+    return janc
+
+
+def rel_err(a, b):
+    out = 0.0
+    for k in range(a.shape[0]):
+        s = max(float(np.max(np.abs(b[k]))), 1e-300)
+        out = max(out, float(np.max(np.abs(a[k] - b[k])) / s))
+    return out
+
+
+def _margin_ok(o: AMROracle):
+    """No cell of a parent layer sits within 1e-9 (relative) of the threshold,
+    so both sides take the same refinement decisions."""
+    for i in range(1, o.levels + 1):
+        dx, dy = o.h(i - 1)
+        T, valid = o.layer_T(i - 1)
+        x = o.grad_T(T, dx, dy, valid)[valid]
+        if x.size and np.min(np.abs(x - o.threshold)) <= 1e-9 * o.threshold:
+            return False
+    return True
+
+
+def _compare(J, mech, st, chem, levels, thr, nbuf, every, nsteps, cfl=0.5, dt=0.0, tol_step=1e-10):
+    if dt > 0.0:
+        cfl = 0.0
+    U = orc.prim_to_cons(mech, st["T"], st["p"], st["u"], st["v"], st["Y"])
+    o = AMROracle(mech, st["grid"], U, st["T"], levels=levels, threshold=thr, n_buffer=nbuf, regrid_every=every,
+                  chem=chem)
+    a = J.Amr(mech, st["grid"], chemistry=chem, levels=levels, threshold=thr, n_buffer=nbuf, regrid_every=every)
+    a.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    for n in range(nsteps):
+        if n % every == 0:
+            assert _margin_ok(o), "a gradient sits on the threshold: pick another"
+        t_o = o.step(dt=dt, cfl=cfl)
+        t_g = a.step(1, dt=dt, cfl=cfl)
+        assert abs(t_g - t_o) <= 1e-12 * t_o, (n, t_g, t_o)
+        tol = tol_step * (n + 1)
+        Ub, Tb = a.base()
+        assert rel_err(Ub, o.U0) < tol, (n, rel_err(Ub, o.U0))
+        assert rel_err(Tb[None], o.T0[None]) < tol
+        for i in range(1, levels + 1):
+            pos, UL, TL = a.layer(i)
+            assert [tuple(p) for p in pos] == o.layers[i].pos, (n, i)
+            if len(pos):
+                assert rel_err(UL.transpose(1, 0, 2, 3), o.layers[i].U.transpose(1, 0, 2, 3)) < tol, (n, i)
+                assert np.max(np.abs(TL - o.layers[i].T) / o.layers[i].T) < tol
+    assert a.status() == 0
+    assert a.cell_updates() == o.cell_updates_per_step()
+    return a, o
+
+
+def test_amr_reacting_tube_with_walls(J):
+    st = inputs.tube(H2AIR, 64, 16, Lx=0.05 * 64 / 256, perturb_seed=3)
+    dx = st["grid"]["dx"]
+    a, o = _compare(J, H2AIR, st, True, levels=2, thr=100.0 / dx, nbuf=2, every=2, nsteps=5)
+    assert o.layers[1].pos and o.layers[2].pos
+    a.close()
+
+
+def test_amr_riemann_zero_gradient_and_periodic(J):
+    nx, ny = 128, 16
+    st = inputs.sod(GAS, nx)
+    for k in ("T", "p", "u", "v"):
+        st[k] = np.repeat(st[k][:1], ny, 0)
+    st["Y"] = np.repeat(st["Y"][:, :1], ny, 1)
+    # a transverse wave so that the y direction does work
+    y = (np.arange(ny) + 0.5) / ny
+    st["v"] = st["v"] + 20.0 * np.sin(2 * np.pi * y)[:, None]
+    st["grid"].update(ny=ny, dy=st["grid"]["dx"], bc=[1, 1, 2, 2])
+    dt = 0.2 * st["grid"]["dx"] / 420.0
+    a, o = _compare(J, GAS, st, False, levels=2, thr=5.0 / st["grid"]["dx"], nbuf=3, every=3, nsteps=7, dt=dt)
+    assert len(o.layers[2].pos) > 2
+    a.close()
+
+
+def test_amr_without_refinement_is_the_grid_step(J):
+    st = inputs.tube(H2AIR, 64, 16, Lx=0.05 * 64 / 256, perturb_seed=3)
+    a = J.Amr(H2AIR, st["grid"], chemistry=True, levels=2, threshold=1e300, n_buffer=2, regrid_every=2)
+    a.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    g = J.Grid.from_grid_dict(H2AIR, st["grid"])
+    g.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    a.step(4, cfl=0.5)
+    g.step(4, cfl=0.5)
+    Ua, Ta = a.base()
+    Ug, Tg = g.get_state()
+    assert np.array_equal(Ua, Ug) and np.array_equal(Ta, Tg)
+    assert J.janc_amr_layer_blocks(a.handle, 1) == 0
+    a.close()
+    g.close()
