@@ -294,6 +294,45 @@ def run_adjoint(janc, stream, nsteps=500, ckpt=50):
             "note": "adjoint_s covers the forward with checkpoints, the segment recompute and the reverse sweep"}
 
 
+def run_amr(janc, stream, levels=3, warm=20, steps=40, every=10):
+    """AMR leg: 2048 x 256 H2-air tube base, `levels` layers of 16 x 16
+    blocks refined where |grad T| > 50 K per base cell (buffer 4), regrid every
+    `every` base steps, CFL 0.5 on the base. After `warm` base steps (the
+    igniter's blast develops its fronts) `steps` base steps are timed, regrids
+    included. Cell updates count base cells plus 2^i x the cells of layer i."""
+    import torch
+    from paper_2504_13750_gb300 import inputs
+
+    mech = inputs.load_mechanism("h2air_synth")
+    st = inputs.tube(mech, 2048, 256, perturb_seed=0)
+    thr = 50.0 / st["grid"]["dx"]
+    a = janc.Amr(mech, st["grid"], chemistry=True, levels=levels, threshold=thr, n_buffer=4, regrid_every=every,
+                 stream=stream)
+    a.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    a.step(warm, cfl=0.5)
+    torch.cuda.synchronize()
+    updates = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        a.step(1, cfl=0.5)
+        updates += a.cell_updates()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    status = a.status()
+    blocks = [janc.janc_amr_layer_blocks(a.handle, i) for i in range(1, levels + 1)]
+    nx0, ny0 = st["grid"]["nx"], st["grid"]["ny"]
+    uniform = nx0 * ny0 * 8 ** levels  # finest-resolution cells x 2^levels substeps per base step
+    a.close()
+    if status != 0:
+        raise RuntimeError(f"AMR status word {status:#x}")
+    return {"workload": f"h2air_tube_base{nx0}x{ny0}_{levels}layers_16x16blocks_grad50K_regrid{every}",
+            "base_steps_timed": steps, "warmup_base_steps": warm, "ms_per_base_step": 1e3 * wall / steps,
+            "cell_updates_per_s": updates / wall, "cell_updates_per_base_step": updates / steps,
+            "blocks_per_layer_at_end": blocks, "uniform_finest_updates_per_base_step": uniform,
+            "fraction_of_uniform_finest": updates / steps / uniform,
+            "note": "wall clock with host syncs (regrid block lists, CFL read) inside the timed region"}
+
+
 def run_ours(args):
     import torch
 
@@ -416,6 +455,8 @@ def run_ours(args):
     g.close()
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(janc, stream)
+    if rank == 0 and not args.no_amr:
+        line["amr"] = run_amr(janc, stream)
     if not args.no_serving:
         line["serving"] = run_serving(janc, stream, args.serving_requests, tuple(args.serving_steps))
     if rank == 0:
@@ -435,6 +476,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests in the serving leg (the full stream is 256 with --serving-steps 100 1000)")
     ap.add_argument("--serving-steps", type=int, nargs=2, default=(50, 150))
