@@ -166,6 +166,13 @@ int janc_rhs(janc_grid_t g, double* Fx, double* Gy, double* L, double* alpha, in
 int janc_profile(janc_grid_t g, int enable);
 int janc_profile_read(janc_grid_t g, double* ms, long long* launches);
 
+/* advance_source_term of Sec. 4.3 alone, n_steps times over dt: the
+ * point-implicit chemistry (Eq. 4.12-4.13) and the Newton T of every cell,
+ * no flux terms (so every cell is an independent constant-volume reactor, the
+ * 0-D ignition case of Sec. 5.1(2)). The simulated clock is not advanced.
+ * Asynchronous on the grid's stream; JANC_E_INVALID without chemistry. */
+int janc_source_step(janc_grid_t g, int n_steps, double dt);
+
 /* Read the status word and counters (synchronises the stream). */
 int janc_status(janc_grid_t g, janc_status_info* s);
 

@@ -464,6 +464,27 @@ int janc_step(janc_grid_t g, int n_steps, double dt, double cfl, double* t_out, 
   return JANC_OK;
 }
 
+int janc_source_step(janc_grid_t g, int n_steps, double dt) {
+  if (!g || n_steps < 0 || !(dt > 0.0)) return fail(JANC_E_INVALID, "janc_source_step: bad argument");
+  if (g->d.chemistry == JANC_CHEM_OFF) return fail(JANC_E_INVALID, "janc_source_step: the grid has no chemistry");
+  StepCtl ctl;
+  ctl.dt_fixed = dt;
+  ctl.cfl = 0.0;
+  ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
+  ctl.chem_frac = 1.0;
+  const StateView S0 = sv(g, 0);
+  unsigned long long* a1 = g->alpha + 2;  // the new state's LF speeds, then slot 0
+  for (int s = 0; s < n_steps; ++s) {
+    cudaError_t e = cudaMemsetAsync(a1, 0, 2 * sizeof(unsigned long long), g->stream);
+    if (e == cudaSuccess)
+      e = timed(g, 2, [&] { return launch_chem(g->ns, S0, g->gd, g->mech, ctl, g->alpha, a1, g->status, g->stream); });
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g->alpha, a1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "janc_source_step");
+  }
+  return JANC_OK;
+}
+
 int janc_get_state(janc_grid_t g, double* U, double* T, int where) {
   if (!g) return fail(JANC_E_INVALID, "null grid");
   if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");

@@ -105,6 +105,7 @@ def lib():
             L.janc_primitive_T_vjp.argtypes = [p, p, p, p, p, p, p, p]
             L.janc_profile.argtypes = [p, i]
             L.janc_profile_read.argtypes = [p, p, p]
+            L.janc_source_step.argtypes = [p, i, d]
             L.janc_amr_create.argtypes = [p, p, p, p, ctypes.POINTER(p)]
             L.janc_amr_set_state_primitive.argtypes = [p, p, p, p, p, p, i]
             L.janc_amr_step.argtypes = [p, i, d, d, ctypes.POINTER(d)]
@@ -221,6 +222,10 @@ def janc_step(g, n_steps, dt=0.0, cfl=0.0, want_time=False):
         return t.value, dl.value
     _check(lib().janc_step(g, int(n_steps), float(dt), float(cfl), None, None))
     return None
+
+
+def janc_source_step(g, n_steps, dt):
+    _check(lib().janc_source_step(g, int(n_steps), float(dt)))
 
 
 def janc_get_state(g, U=None, T=None, check=True):
