@@ -466,6 +466,21 @@ def run_ours(args):
     return 0
 
 
+def run_only(args):
+    import torch
+    from paper_2504_13750_gb300 import build, janc
+
+    build.build()
+    stream = torch.cuda.Stream()
+    if args.only == "adjoint":
+        n = args.leg_steps or 500
+        out = run_adjoint(janc, stream, nsteps=n, ckpt=max(1, n // 10))
+    else:
+        out = run_amr(janc, stream, steps=args.leg_steps or 40)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,12 +497,18 @@ def main():
     ap.add_argument("--serving-steps", type=int, nargs=2, default=(50, 150))
     ap.add_argument("--nx", type=int, default=NX, help="tube cells along x (default: the 4096 x 512 workload)")
     ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--only", choices=("adjoint", "amr"), default=None,
+                    help="run one side leg alone and print its JSON object (for profiling)")
+    ap.add_argument("--leg-steps", type=int, default=None,
+                    help="with --only: adjoint trajectory steps (checkpoint every steps/10) or timed AMR base steps")
     args = ap.parse_args()
     globals()["NX"], globals()["NY"] = args.nx, args.ny
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 

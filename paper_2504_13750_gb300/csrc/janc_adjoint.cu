@@ -12,10 +12,11 @@
 //    recovery. The global LF speeds alpha (Eq. 4.11) receive the summed
 //    cotangent, which flows to the cell that attains the maximum (ties:
 //    lowest linear index).
-//  * Point-implicit chemistry (Eq. 4.12-4.13): the 12 x 12 local Jacobian of
-//    the cell map U* -> U^{n+1} (through T* = T(U*), rates, Jacobian and the
-//    LU solve) by forward-mode dual numbers, 4 lanes per pass, then its
-//    transpose times the cotangent.
+//  * Point-implicit chemistry (Eq. 4.12-4.13): one transposed solve with the
+//    LU factors of the forward system, then the gradient of a scalar
+//    (sum over reactions of the weighted rate and its derivative along the
+//    solution) in reverse mode, chained through T* = T(U*) (see
+//    chem_vjp_rev).
 //  * TVD-RK3: the Shu-Osher stages reversed.
 // No atomics touch state cotangents: every cell gathers its own.
 #include <cmath>
@@ -283,219 +284,156 @@ __global__ void k_adj_alpha(StateView S, GridDev g, const MechDev* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Chemistry: forward-mode duals with L lanes.
+// Chemistry VJP in reverse mode.
+//
+// The point-implicit update (Eq. 4.12-4.13) is rho Y_k += M_k x_k with
+// A x = dt wd, A = I - dt J'', all at (T*, X(U*)), T* = T(U*). For the
+// cotangent lam of U^{n+1}, with r_k = M_k lam_{4+k} and mu = A^{-T} r,
+//   lam^T dU^{n+1} = lam^T dU* + mu^T (dt dwd + dt dJ'' x),
+// and J'' x is the derivative of wd along x_eff = (x_0..x_{ns-2},
+// -sum_l (M_l/M_ns) x_l) in concentration space. So the VJP is lam plus the
+// gradient with respect to U* of
+//   psi = dt sum_i m_i (q_i + Dq_i[x_eff]),  m_i = sum_k nu_ki mu_k,
+// at fixed mu and x. psi depends on T only through k_f and k_b, and on the
+// concentrations through the third-body sum (linear) and the mass-action
+// monomials; its gradient in (T, X) is written out per reaction below and
+// chained to U* through X(U*) and the implicit dT/dU* of the Newton recovery.
 // ---------------------------------------------------------------------------
-template <int L>
-struct Dn {
-  double v;
-  double d[L];
-};
-template <int L> __device__ __forceinline__ Dn<L> dconst(double x) {
-  Dn<L> r; r.v = x;
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = 0.0;
-  return r;
-}
-template <int L> __device__ __forceinline__ Dn<L> dadd(const Dn<L>& a, const Dn<L>& b) {
-  Dn<L> r; r.v = a.v + b.v;
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = a.d[l] + b.d[l];
-  return r;
-}
-template <int L> __device__ __forceinline__ Dn<L> dsub(const Dn<L>& a, const Dn<L>& b) {
-  Dn<L> r; r.v = a.v - b.v;
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = a.d[l] - b.d[l];
-  return r;
-}
-template <int L> __device__ __forceinline__ Dn<L> dmul(const Dn<L>& a, const Dn<L>& b) {
-  Dn<L> r; r.v = a.v * b.v;
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = fma(a.d[l], b.v, a.v * b.d[l]);
-  return r;
-}
-template <int L> __device__ __forceinline__ Dn<L> dscale(const Dn<L>& a, double s) {
-  Dn<L> r; r.v = a.v * s;
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = a.d[l] * s;
-  return r;
-}
-// a * b + c
-template <int L> __device__ __forceinline__ Dn<L> dfma(const Dn<L>& a, const Dn<L>& b, const Dn<L>& c) {
-  Dn<L> r; r.v = fma(a.v, b.v, c.v);
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = fma(a.d[l], b.v, fma(a.v, b.d[l], c.d[l]));
-  return r;
-}
-// s * a + c with a double s
-template <int L> __device__ __forceinline__ Dn<L> dsfma(double s, const Dn<L>& a, const Dn<L>& c) {
-  Dn<L> r; r.v = fma(s, a.v, c.v);
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = fma(s, a.d[l], c.d[l]);
-  return r;
-}
-template <int L> __device__ __forceinline__ Dn<L> drcp(const Dn<L>& a) {
-  Dn<L> r; r.v = rcp(a.v);
-  const double q = -r.v * r.v;
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = q * a.d[l];
-  return r;
-}
-template <int L> __device__ __forceinline__ Dn<L> dexp(const Dn<L>& a) {
-  Dn<L> r; r.v = exp_t(a.v);
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = r.v * a.d[l];
-  return r;
-}
-template <int L> __device__ __forceinline__ Dn<L> dlog(const Dn<L>& a) {
-  Dn<L> r; r.v = log(a.v);
-  const double q = rcp(a.v);
-#pragma unroll
-  for (int l = 0; l < L; ++l) r.d[l] = q * a.d[l];
-  return r;
+
+// A mass-action monomial prod_s X_{sp_s}^{a_s} over n <= MAX_SIDE distinct
+// species: the value, the gradient g_s, the derivative along e (D), and the
+// gradient of D (h_s = sum_t e_t d2/dX_t dX_s).
+__device__ __forceinline__ void monomial(const double* X, const int* sp, const int* a, int n, const double* e,
+                                         double& val, double* g, double& D, double* h) {
+  double P[MAX_SIDE], P1[MAX_SIDE], P2[MAX_SIDE];
+  for (int s = 0; s < n; ++s) {
+    const double x = X[sp[s]];
+    double pw = 1.0;
+    for (int q = 0; q < a[s] - 2; ++q) pw *= x;  // x^(a-2)
+    P2[s] = a[s] >= 2 ? a[s] * (a[s] - 1) * pw : 0.0;
+    const double pw1 = a[s] >= 2 ? pw * x : 1.0;  // x^(a-1)
+    P1[s] = a[s] * pw1;
+    P[s] = pw1 * x;
+  }
+  val = 1.0;
+  for (int s = 0; s < n; ++s) val *= P[s];
+  D = 0.0;
+  for (int s = 0; s < n; ++s) {
+    double ex = P1[s];
+    for (int t = 0; t < n; ++t)
+      if (t != s) ex *= P[t];
+    g[s] = ex;
+    D = fma(e[sp[s]], ex, D);
+  }
+  for (int s = 0; s < n; ++s) {
+    double hs = 0.0;
+    for (int t = 0; t < n; ++t) {
+      double v;
+      if (t == s) {
+        v = P2[s];
+        for (int w = 0; w < n; ++w)
+          if (w != s) v *= P[w];
+      } else {
+        v = P1[s] * P1[t];
+        for (int w = 0; w < n; ++w)
+          if (w != s && w != t) v *= P[w];
+      }
+      hs = fma(e[sp[t]], v, hs);
+    }
+    h[s] = hs;
+  }
 }
 
-// Cotangent of U* from the cotangent of U^{n+1} for one cell, lanes
-// [lane0, lane0 + L) of the input. The map: T* = T(U*) (Newton, from the
-// stored value), then the point-implicit update of the species.
-template <int NS, int L>
-__device__ void chem_vjp_lanes(const double* uval, double Tval, const MechDev& m, double dt, const double* lam,
-                               int lane0, double* out) {
+template <int NS>
+__device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double dt, const double* lam,
+                             double* out) {
   constexpr int NSP = NS - 1;
   constexpr int NV = NS + 3;
-  Dn<L> u[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    u[k] = dconst<L>(uval[k]);
-#pragma unroll
-    for (int l = 0; l < L; ++l) u[k].d[l] = (k == lane0 + l) ? 1.0 : 0.0;
-  }
-  // Newton T on duals from the converged value (the value part stays put,
-  // the tangent part becomes the implicit derivative).
-  Dn<L> z[NS];
-  Dn<L> rest = u[0];
+  double X[NS];
+  double rest = u[0];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
-    z[k] = dscale<L>(u[4 + k], m.invM[k]);
-    rest = dsub<L>(rest, u[4 + k]);
+    X[k] = u[4 + k] * m.invM[k];
+    rest -= u[4 + k];
   }
-  z[NSP] = dscale<L>(rest, m.invM[NSP]);
-  Dn<L> W = z[0];
+  X[NSP] = rest * m.invM[NSP];
+  double Ctot = X[0];
 #pragma unroll
-  for (int k = 1; k < NS; ++k) W = dadd<L>(W, z[k]);
-  Dn<L> h[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    Dn<L> s = dscale<L>(z[0], m.hc[0][q]);
-#pragma unroll
-    for (int k = 1; k < NS; ++k) s = dsfma<L>(m.hc[k][q], z[k], s);
-    h[q] = s;
-  }
-  const Dn<L> rrho = drcp<L>(u[0]);
-  const Dn<L> ke = dfma<L>(u[1], u[1], dmul<L>(u[2], u[2]));
-  const Dn<L> rhoe = dsub<L>(u[3], dscale<L>(dmul<L>(rrho, ke), 0.5));
-  const Dn<L> K0 = dsub<L>(h[5], dscale<L>(rhoe, 1.0 / RU));
-  const Dn<L> K1 = dsub<L>(h[0], W);
-  Dn<L> T = dconst<L>(Tval);
-  for (int it = 0; it < 2; ++it) {
-    Dn<L> F = dfma<L>(T, h[4], h[3]);
-    F = dfma<L>(T, F, h[2]);
-    F = dfma<L>(T, F, h[1]);
-    F = dfma<L>(T, F, K1);
-    F = dfma<L>(T, F, K0);
-    Dn<L> Fp = dfma<L>(T, dscale<L>(h[4], 5.0), dscale<L>(h[3], 4.0));
-    Fp = dfma<L>(T, Fp, dscale<L>(h[2], 3.0));
-    Fp = dfma<L>(T, Fp, dscale<L>(h[1], 2.0));
-    Fp = dfma<L>(T, Fp, K1);
-    T = dsub<L>(T, dmul<L>(F, drcp<L>(Fp)));
-  }
-  // rates (Eq. 4.7-4.9) on duals
-  Dn<L> X[NS];
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) X[k] = dscale<L>(u[4 + k], m.invM[k]);
-  X[NSP] = z[NSP];
-  Dn<L> Ctot = X[0];
-#pragma unroll
-  for (int k = 1; k < NS; ++k) Ctot = dadd<L>(Ctot, X[k]);
-  const Dn<L> lnT = dlog<L>(T);
-  const Dn<L> rT = drcp<L>(T);
-  Dn<L> eG[NS], reG[NS];
+  for (int k = 1; k < NS; ++k) Ctot += X[k];
+  const double lnT = log(T);
+  const double rT = rcp(T);
+  const double rT2 = rT * rT;
+  double eG[NS], reG[NS], dG[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     const double* c = m.gc[k];
-    Dn<L> G = dsfma<L>(c[4], T, dconst<L>(c[3]));
-    G = dfma<L>(T, G, dconst<L>(c[2]));
-    G = dfma<L>(T, G, dconst<L>(c[1]));
-    G = dfma<L>(T, G, dconst<L>(c[6]));
-    G = dsfma<L>(c[5], rT, G);
-    G = dsfma<L>(c[0], lnT, G);
-    eG[k] = dexp<L>(G);
-    reG[k] = drcp<L>(eG[k]);
+    const double G = fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6])));
+    eG[k] = exp_t(G);
+    reG[k] = rcp(eG[k]);
+    dG[k] = fma(c[0], rT, fma(-c[5], rT2, fma(T, fma(T, fma(T, 4.0 * c[4], 3.0 * c[3]), 2.0 * c[2]), c[1])));
   }
-  const Dn<L> cref = dscale<L>(rT, P_REF / RU);
-  const Dn<L> rcref = dscale<L>(T, RU / P_REF);
-  Dn<L> wd[NSP];
-  Dn<L> J[NSP][NSP];
+  const double cref = (P_REF / RU) * rT;
+  const double rcref = (RU / P_REF) * T;
+
+  // ---- forward: rates, J'' and the caches of the reverse pass ----
+  double kfa[MAX_NR], kba[MAX_NR], dkfa[MAX_NR], dkba[MAX_NR];
+  double wd[NSP], A[NSP][NSP];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
-    wd[k] = dconst<L>(0.0);
+    wd[k] = 0.0;
 #pragma unroll
-    for (int l = 0; l < NSP; ++l) J[k][l] = dconst<L>(0.0);
+    for (int l = 0; l < NSP; ++l) A[k][l] = 0.0;
   }
   for (int i = 0; i < m.nr; ++i) {
     const int nre = m.nre[i], npr = m.npr[i];
-    const Dn<L> kf = dexp<L>(dsfma<L>(m.b[i], lnT, dsfma<L>(-m.EaR[i], rT, dconst<L>(m.lnA[i]))));
-    Dn<L> kb = kf;
+    const double kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
+    const double dlkf = fma(m.b[i], rT, m.EaR[i] * rT2);
+    double kb = kf, dlkb = dlkf;
     for (int r = 0; r < nre; ++r)
-      for (int q = 0; q < m.rnu[i][r]; ++q) kb = dmul<L>(kb, eG[m.rsp[i][r]]);
+      for (int q = 0; q < m.rnu[i][r]; ++q) { kb *= eG[m.rsp[i][r]]; dlkb += dG[m.rsp[i][r]]; }
     for (int r = 0; r < npr; ++r)
-      for (int q = 0; q < m.pnu[i][r]; ++q) kb = dmul<L>(kb, reG[m.psp[i][r]]);
-    for (int q = 0; q < m.dnu[i]; ++q) kb = dmul<L>(kb, rcref);
-    for (int q = 0; q < -m.dnu[i]; ++q) kb = dmul<L>(kb, cref);
-    Dn<L> xr[MAX_SIDE], xp[MAX_SIDE];
-    Dn<L> fwd = kf, bwd = kb;
+      for (int q = 0; q < m.pnu[i][r]; ++q) { kb *= reG[m.psp[i][r]]; dlkb -= dG[m.psp[i][r]]; }
+    const int dn = m.dnu[i];
+    for (int q = 0; q < dn; ++q) kb *= rcref;
+    for (int q = 0; q < -dn; ++q) kb *= cref;
+    dlkb = fma((double)dn, rT, dlkb);
+    kfa[i] = kf; kba[i] = kb; dkfa[i] = dlkf; dkba[i] = dlkb;
+    double xr[MAX_SIDE], xp[MAX_SIDE];
+    double fwd = kf, bwd = kb;
     for (int r = 0; r < nre; ++r) {
       xr[r] = X[m.rsp[i][r]];
-      for (int q = 0; q < m.rnu[i][r]; ++q) fwd = dmul<L>(fwd, xr[r]);
+      for (int q = 0; q < m.rnu[i][r]; ++q) fwd *= xr[r];
     }
     for (int r = 0; r < npr; ++r) {
       xp[r] = X[m.psp[i][r]];
-      for (int q = 0; q < m.pnu[i][r]; ++q) bwd = dmul<L>(bwd, xp[r]);
+      for (int q = 0; q < m.pnu[i][r]; ++q) bwd *= xp[r];
     }
-    Dn<L> Mi = dconst<L>(1.0);
+    double Mi = 1.0;
     if (m.tb[i]) {
       Mi = Ctot;
-      for (int e = 0; e < m.neff[i]; ++e) Mi = dsfma<L>(m.effv[i][e], X[m.effsp[i][e]], Mi);
+      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
     }
-    const Dn<L> net = dsub<L>(fwd, bwd);
-    const Dn<L> q = dmul<L>(Mi, net);
-    for (int r = 0; r < nre; ++r) {
-      const int k = m.rsp[i][r];
-      if (k < NSP) wd[k] = dsfma<L>(-m.rnud[i][r], q, wd[k]);
-    }
-    for (int r = 0; r < npr; ++r) {
-      const int k = m.psp[i][r];
-      if (k < NSP) wd[k] = dsfma<L>(m.pnud[i][r], q, wd[k]);
-    }
-    Dn<L> dq[2 * MAX_SIDE];
+    const double net = fwd - bwd;
+    const double q = Mi * net;
+    double dq[2 * MAX_SIDE];
     int dsp[2 * MAX_SIDE];
     int nd = 0;
     for (int r = 0; r < nre; ++r) {
-      Dn<L> dd = dscale<L>(kf, m.rnud[i][r]);
-      for (int s = 0; s < nre; ++s) {
-        const int pw = m.rnu[i][s] - (s == r ? 1 : 0);
-        for (int t = 0; t < pw; ++t) dd = dmul<L>(dd, xr[s]);
+      double dd = kf * m.rnud[i][r];
+      for (int s2 = 0; s2 < nre; ++s2) {
+        const int pw = m.rnu[i][s2] - (s2 == r ? 1 : 0);
+        for (int t = 0; t < pw; ++t) dd *= xr[s2];
       }
-      dq[nd] = dmul<L>(Mi, dd);
+      dq[nd] = Mi * dd;
       dsp[nd++] = m.rsp[i][r];
     }
     for (int r = 0; r < npr; ++r) {
-      Dn<L> dd = dscale<L>(kb, m.pnud[i][r]);
-      for (int s = 0; s < npr; ++s) {
-        const int pw = m.pnu[i][s] - (s == r ? 1 : 0);
-        for (int t = 0; t < pw; ++t) dd = dmul<L>(dd, xp[s]);
+      double dd = kb * m.pnud[i][r];
+      for (int s2 = 0; s2 < npr; ++s2) {
+        const int pw = m.pnu[i][s2] - (s2 == r ? 1 : 0);
+        for (int t = 0; t < pw; ++t) dd *= xp[s2];
       }
-      dq[nd] = dscale<L>(dmul<L>(Mi, dd), -1.0);
+      dq[nd] = -Mi * dd;
       dsp[nd++] = m.psp[i][r];
     }
     for (int side = 0; side < 2; ++side) {
@@ -504,68 +442,135 @@ __device__ void chem_vjp_lanes(const double* uval, double Tval, const MechDev& m
         const int k = side ? m.psp[i][r] : m.rsp[i][r];
         if (k >= NSP) continue;
         const double nu = side ? m.pnud[i][r] : -m.rnud[i][r];
+        wd[k] = fma(nu, q, wd[k]);
         for (int d = 0; d < nd; ++d) {
           const int jj = dsp[d];
           if (jj < NSP) {
-            J[k][jj] = dsfma<L>(nu, dq[d], J[k][jj]);
+            A[k][jj] = fma(nu, dq[d], A[k][jj]);
           } else {
-            const Dn<L> v = dscale<L>(dq[d], nu);
-            for (int l = 0; l < NSP; ++l) J[k][l] = dsfma<L>(-m.mratio[l], v, J[k][l]);
+            const double v = dq[d] * nu;
+            for (int l = 0; l < NSP; ++l) A[k][l] = fma(-m.mratio[l], v, A[k][l]);
           }
         }
         if (m.tb[i]) {
-          const Dn<L> v = dscale<L>(net, nu);
-          for (int l = 0; l < NSP; ++l) J[k][l] = dsfma<L>(m.ceff[i][l], v, J[k][l]);
+          const double v = net * nu;
+          for (int l = 0; l < NSP; ++l) A[k][l] = fma(m.ceff[i][l], v, A[k][l]);
         }
       }
     }
   }
-  // (I - dt J) dx = dt wd, LU with partial pivoting on the values
-  Dn<L> b[NSP];
+  // A = I - dt J'', factored P A = L U in place (partial pivoting on values)
+  double x[NSP];
+  int perm[NSP];
+#pragma unroll
   for (int k = 0; k < NSP; ++k) {
-    b[k] = dscale<L>(wd[k], dt);
-    for (int l = 0; l < NSP; ++l) {
-      J[k][l] = dscale<L>(J[k][l], -dt);
-      if (k == l) J[k][l].v += 1.0;
-    }
+    x[k] = dt * wd[k];
+#pragma unroll
+    for (int l = 0; l < NSP; ++l) A[k][l] = fma(-dt, A[k][l], k == l ? 1.0 : 0.0);
   }
   for (int c = 0; c < NSP; ++c) {
     int piv = c;
-    double best = fabs(J[c][c].v);
+    double best = fabs(A[c][c]);
     for (int r = c + 1; r < NSP; ++r)
-      if (fabs(J[r][c].v) > best) { best = fabs(J[r][c].v); piv = r; }
+      if (fabs(A[r][c]) > best) { best = fabs(A[r][c]); piv = r; }
+    perm[c] = piv;
     if (piv != c) {
-      for (int k = 0; k < NSP; ++k) { Dn<L> t = J[c][k]; J[c][k] = J[piv][k]; J[piv][k] = t; }
-      Dn<L> t = b[c]; b[c] = b[piv]; b[piv] = t;
+      for (int k = 0; k < NSP; ++k) { const double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+      const double t = x[c]; x[c] = x[piv]; x[piv] = t;
     }
-    const Dn<L> ip = drcp<L>(J[c][c]);
+    const double ip = rcp(A[c][c]);
     for (int r = c + 1; r < NSP; ++r) {
-      const Dn<L> f = dmul<L>(J[r][c], ip);
-      for (int k = c + 1; k < NSP; ++k) J[r][k] = dsub<L>(J[r][k], dmul<L>(f, J[c][k]));
-      b[r] = dsub<L>(b[r], dmul<L>(f, b[c]));
+      const double f = A[r][c] * ip;
+      A[r][c] = f;  // L
+      for (int k = c + 1; k < NSP; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
+      x[r] = fma(-f, x[c], x[r]);
     }
   }
   for (int r = NSP - 1; r >= 0; --r) {
-    Dn<L> s = b[r];
-    for (int k = r + 1; k < NSP; ++k) s = dsub<L>(s, dmul<L>(J[r][k], b[k]));
-    b[r] = dmul<L>(s, drcp<L>(J[r][r]));
+    double s = x[r];
+    for (int k = r + 1; k < NSP; ++k) s = fma(-A[r][k], x[k], s);
+    x[r] = s * rcp(A[r][r]);
   }
-  // d(U^{n+1})/d(U*_lane) = identity + d(M_k dx_k) on the species rows
+  // mu = A^{-T} r: U^T z = r, L^T w = z, then undo the row swaps
+  double mu[NSP];
+  for (int c = 0; c < NSP; ++c) {
+    double s = m.M[c] * lam[4 + c];
+    for (int k = 0; k < c; ++k) s = fma(-A[k][c], mu[k], s);
+    mu[c] = s * rcp(A[c][c]);
+  }
+  for (int c = NSP - 1; c >= 0; --c) {
+    double s = mu[c];
+    for (int k = c + 1; k < NSP; ++k) s = fma(-A[k][c], mu[k], s);
+    mu[c] = s;
+  }
+  for (int c = NSP - 1; c >= 0; --c)
+    if (perm[c] != c) { const double t = mu[c]; mu[c] = mu[perm[c]]; mu[perm[c]] = t; }
+  double xe[NS];
+  double xN = 0.0;
 #pragma unroll
-  for (int l = 0; l < L; ++l) {
-    const int lane = lane0 + l;
-    if (lane >= NV) continue;
-    double s = lam[lane];
-    for (int k = 0; k < NSP; ++k) s = fma(lam[4 + k], m.M[k] * b[k].d[l], s);
-    out[lane] = s;
+  for (int l = 0; l < NSP; ++l) {
+    xe[l] = x[l];
+    xN = fma(-m.mratio[l], x[l], xN);
   }
+  xe[NSP] = xN;
+
+  // ---- reverse: gradient of psi in (T, X) ----
+  double gT = 0.0, gX[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) gX[k] = 0.0;
+  for (int i = 0; i < m.nr; ++i) {
+    const int nre = m.nre[i], npr = m.npr[i];
+    double mi = 0.0;
+    for (int r = 0; r < nre; ++r)
+      if (m.rsp[i][r] < NSP) mi = fma(-m.rnud[i][r], mu[m.rsp[i][r]], mi);
+    for (int r = 0; r < npr; ++r)
+      if (m.psp[i][r] < NSP) mi = fma(m.pnud[i][r], mu[m.psp[i][r]], mi);
+    const double w = dt * mi;
+    const double kf = kfa[i], kb = kba[i];
+    double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
+    monomial(X, m.rsp[i], m.rnu[i], nre, xe, F, gF, DF, hF);
+    monomial(X, m.psp[i], m.pnu[i], npr, xe, B, gB, DB, hB);
+    const double net = fma(kf, F, -kb * B);
+    const double Dnet = fma(kf, DF, -kb * DB);
+    double Mi = 1.0, DMi = 0.0;
+    if (m.tb[i]) {
+      Mi = Ctot;
+      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
+      for (int j = 0; j < NS; ++j) DMi = fma(1.0 + m.effm1[i][j], xe[j], DMi);
+    }
+    const double MD = Mi + DMi;
+    const double kfp = kf * dkfa[i], kbp = kb * dkba[i];
+    gT = fma(w, fma(MD, fma(kfp, F, -kbp * B), Mi * fma(kfp, DF, -kbp * DB)), gT);
+    for (int r = 0; r < nre; ++r) {
+      const int j = m.rsp[i][r];
+      gX[j] = fma(w * kf, fma(MD, gF[r], Mi * hF[r]), gX[j]);
+    }
+    for (int r = 0; r < npr; ++r) {
+      const int j = m.psp[i][r];
+      gX[j] = fma(-w * kb, fma(MD, gB[r], Mi * hB[r]), gX[j]);
+    }
+    if (m.tb[i]) {
+      const double v = w * (net + Dnet);
+      for (int j = 0; j < NS; ++j) gX[j] = fma(1.0 + m.effm1[i][j], v, gX[j]);
+    }
+  }
+  // chain to U*: X(U*) and the implicit dT/dU* of the Newton recovery
+  CellThermo<NS> ct;
+  cell_thermo<NS>(u, T, m, ct);
+  double dT[NV], dp[NV];
+  dT_dp_dU<NS>(u, T, m, ct, dT, dp);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = fma(gT, dT[q], lam[q]);
+  const double gN = gX[NSP] * m.invM[NSP];
+  out[0] += gN;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) out[4 + k] += fma(gX[k], m.invM[k], -gN);
 }
 
-constexpr int CHEM_L = 4;
-
 template <int NS>
-__global__ void k_adj_chem(StateView Sstar, GridDev g, const MechDev* __restrict__ mech, double dt,
-                           const double* __restrict__ lam, double* __restrict__ out, int lane0) {
+__global__ void __launch_bounds__(128) k_adj_chem_rev(StateView Sstar, GridDev g, const MechDev* __restrict__ mech,
+                                                      double dt, const double* __restrict__ lam,
+                                                      double* __restrict__ out) {
   constexpr int NV = NS + 3;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.n) return;
@@ -575,10 +580,10 @@ __global__ void k_adj_chem(StateView Sstar, GridDev g, const MechDev* __restrict
   for (int k = 0; k < NV; ++k) {
     u[k] = Sstar.plane(k, n)[q];
     l[k] = lam[(long long)k * n + q];
-    o[k] = 0.0;
   }
-  chem_vjp_lanes<NS, CHEM_L>(u, Sstar.plane(NV, n)[q], *mech, dt, l, lane0, o);
-  for (int k = lane0; k < lane0 + CHEM_L && k < NV; ++k) out[(long long)k * n + q] = o[k];
+  chem_vjp_rev<NS>(u, Sstar.plane(NV, n)[q], *mech, dt, l, o);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[(long long)k * n + q] = o[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -720,13 +725,10 @@ cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev,
 
 cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, const MechDev* mech, double dt,
                             const double* lam, double* out, cudaStream_t st) {
-  const int nv = ns + 3;
-  for (int lane0 = 0; lane0 < nv; lane0 += CHEM_L) {
-    switch (ns) {
-      case 3: k_adj_chem<3><<<nblk(g.n, 64), 64, 0, st>>>(Sstar, g, mech, dt, lam, out, lane0); break;
-      case 9: k_adj_chem<9><<<nblk(g.n, 64), 64, 0, st>>>(Sstar, g, mech, dt, lam, out, lane0); break;
-      default: return cudaErrorInvalidValue;
-    }
+  switch (ns) {
+    case 3: k_adj_chem_rev<3><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out); break;
+    case 9: k_adj_chem_rev<9><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
