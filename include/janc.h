@@ -70,12 +70,18 @@ typedef struct janc_grid_s* janc_grid_t;
 #define JANC_CHEM_OFF 0
 #define JANC_CHEM_LIE 1
 #define JANC_CHEM_STRANG 2
+/* No splitting: the production rates of the mechanism are a source term of
+ * the semi-discrete equation, advanced with the fluxes by the same TVD-RK3
+ * (the user source_terms path of Sec. 4.3, for a weakly stiff global
+ * reaction); advance_source_term is not run. */
+#define JANC_CHEM_EXPLICIT 3
 
 /* Grid description.
  * nx, ny >= 1 cells; dx, dy > 0 m; bc = {left, right, bottom, top};
  * chemistry = JANC_CHEM_* (above): JANC_CHEM_OFF runs the flux terms only,
- * the explicit variant of advance_one_step (Sec. 4.3). The server and the
- * adjoint take JANC_CHEM_OFF or JANC_CHEM_LIE only (JANC_E_UNSUPPORTED);
+ * the explicit variant of advance_one_step (Sec. 4.3). The server and AMR
+ * take JANC_CHEM_OFF or JANC_CHEM_LIE only, the adjoint also
+ * JANC_CHEM_EXPLICIT (otherwise JANC_E_UNSUPPORTED);
  * weno_eps = epsilon of the WENO5-JS weights (1e-6 if <= 0);
  * newton_tol / newton_maxit = stop when |dT| <= tol * T (1e-12 / 50 if <= 0). */
 typedef struct {

@@ -715,11 +715,36 @@ template <class S> int chemistry_step(const Mech& m, const Grid& g, Field<S>& F,
 
 // Splitting of the chemistry and flux operators within one step.
 enum : int {
-  CHEM_OFF = 0,     // flux terms only (the explicit variant without sources)
-  CHEM_LIE = 1,     // flux(dt) then chemistry(dt): advance_one_step as coded in Sec. 4.3
-  CHEM_STRANG = 2,  // chemistry(dt/2), flux(dt), chemistry(dt/2): the Strang
-                    // splitting named in the text of Sec. 4.3
+  CHEM_OFF = 0,       // flux terms only (the explicit variant without sources)
+  CHEM_LIE = 1,       // flux(dt) then chemistry(dt): advance_one_step as coded in Sec. 4.3
+  CHEM_STRANG = 2,    // chemistry(dt/2), flux(dt), chemistry(dt/2): the Strang
+                      // splitting named in the text of Sec. 4.3
+  CHEM_EXPLICIT = 3,  // no splitting: the production rates are a source term of
+                      // the semi-discrete equation, advanced by the same TVD-RK3
+                      // as the fluxes (the user source_terms path of Sec. 4.3)
 };
+
+// L += S(U): the mass production rates of the carried species (Eq. 4.7-4.9)
+// at each cell's T, added to the rows rho Y_1 .. rho Y_{ns-1}.
+template <class S> void add_sources(const Mech& m, const Field<S>& F, std::vector<S>& L) {
+  const int ns = m.ns;
+  #pragma omp parallel for schedule(static)
+  for (int j = 0; j < F.ny; ++j)
+    for (int i = 0; i < F.nx; ++i) {
+      S X[16], w[16];
+      S rest = F.u(0, i, j);
+      for (int k = 0; k < ns - 1; ++k) {
+        X[k] = F.u(4 + k, i, j) / m.M[k];
+        rest = rest - F.u(4 + k, i, j);
+      }
+      X[ns - 1] = rest / m.M[ns - 1];
+      production_rates(m, F.t(i, j), X, w);
+      for (int k = 0; k < ns - 1; ++k) {
+        S& l = L[((size_t)(4 + k) * F.ny + j) * F.nx + i];
+        l = l + w[k];
+      }
+    }
+}
 
 // One time step (advance_one_step of Sec. 4.3): TVD-RK3 of the flux terms
 // (Shu-Osher form) and the point-implicit chemistry (Eq. 4.12-4.13) in the
@@ -733,16 +758,20 @@ template <class S> int advance_one_step(const Mech& m, const Grid& g, Field<S>& 
   if (chem == CHEM_STRANG && reacting) st |= chemistry_step(m, g, F, 0.5 * dt);
   std::vector<S> L;
   Field<S> U1 = F, U2 = F;
+  const bool explicit_src = chem == CHEM_EXPLICIT && reacting;
   // stage 1: U1 = U^n + dt L(U^n)
   rhs(m, g, F, L);
+  if (explicit_src) add_sources(m, F, L);
   for (size_t q = 0; q < N; ++q) U1.U[q] = F.U[q] + dt * L[q];
   st |= update_T(m, g, U1, F);
   // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
   rhs(m, g, U1, L);
+  if (explicit_src) add_sources(m, U1, L);
   for (size_t q = 0; q < N; ++q) U2.U[q] = 0.75 * F.U[q] + 0.25 * (U1.U[q] + dt * L[q]);
   st |= update_T(m, g, U2, U1);
   // stage 3: U* = 1/3 U^n + 2/3 (U2 + dt L(U2))
   rhs(m, g, U2, L);
+  if (explicit_src) add_sources(m, U2, L);
   Field<S> Us = F;
   for (size_t q = 0; q < N; ++q) Us.U[q] = (1.0 / 3.0) * F.U[q] + (2.0 / 3.0) * (U2.U[q] + dt * L[q]);
   st |= update_T(m, g, Us, U2);

@@ -18,7 +18,10 @@ The paper's 9-species / 19-reaction mechanism and its gri30 NASA-7 data
   ignites (T rises by 400 K) within 5 us .. 200 us under the oracle's own
   point-implicit step (dt = 1e-8 s); otherwise the next seed is tried.
 
+Also writes the one-step global mechanism global_h2o2_g129 (write_global_g129).
+
 Run from the repository root:  python oracle/make_mechanism.py
+(python oracle/make_mechanism.py global writes only the global mechanism)
 """
 from __future__ import annotations
 
@@ -157,7 +160,43 @@ def ignition_delay(flat, T0=1500.0, p0=20 * inputs.ATM, dt=1e-8, t_max=5e-4, chu
     return None
 
 
+def write_global_g129(out_dir):
+    """One-step global H2-O2 mechanism on a calorically perfect gas with
+    gamma = 1.29 (the fixed-gamma, single-step setting of Sec. 6.2; its
+    parameters are not printed in the paper, so these are synthetic):
+    cp/R = gamma / (gamma - 1) for every species; formation enthalpy of H2O
+    scaled to -60 kJ/mol (an adiabatic rise of about 2000 K for the
+    stoichiometric mixture) and its standard entropy set to 240 J/(mol K) so
+    that the equilibrium lies on the product side up to about 4000 K;
+    2 H2 + O2 => 2 H2O, mass action of order 3, A = 1e5 (m^3/mol)^2/s,
+    b = 0, Ea = 120 kJ/mol (slow enough for an explicit RK3 source at
+    CFL 0.5 on 0.1 mm cells)."""
+    gamma = 1.29
+    a0 = gamma / (gamma - 1.0)
+    hf = {"H2": 0.0, "O2": 0.0, "H2O": -60.0e3}
+    s298 = {"H2": 130.7, "O2": 205.2, "H2O": 240.0}
+    species = ["H2", "O2", "H2O"]
+    nasa = []
+    for sp in species:
+        a5 = hf[sp] / RU - a0 * 298.15
+        a6 = s298[sp] / RU - a0 * np.log(298.15)
+        nasa.append([a0, 0.0, 0.0, 0.0, 0.0, a5, a6])
+    mech = {"name": "global_h2o2_g129", "species": species, "M": [molar_mass(sp) for sp in species],
+            "nasa7": nasa,
+            "reactions": [{"equation": "2 H2 + O2 <=> 2 H2O", "reactants": {"H2": 2, "O2": 1},
+                           "products": {"H2O": 2}, "A": 1.0e5, "b": 0.0, "Ea": 1.2e5, "third_body": False,
+                           "efficiencies": {}}],
+            "units": "SI: M kg/mol; A in (m^3/mol)^2/s; Ea J/mol; NASA-7 single range, dimensionless",
+            "provenance": "synthetic, written by oracle/make_mechanism.py (write_global_g129)",
+            "elements": {sp: ATOMS[sp] for sp in species}}
+    with open(os.path.join(out_dir, "global_h2o2_g129.json"), "w") as f:
+        json.dump(mech, f, indent=1)
+
+
 def main():
+    if sys.argv[1:] == ["global"]:
+        write_global_g129(os.path.join(ROOT, "paper_2504_13750_gb300", "mechanisms"))
+        return
     check_balance()
     out_dir = os.path.join(ROOT, "paper_2504_13750_gb300", "mechanisms")
     os.makedirs(out_dir, exist_ok=True)
@@ -185,6 +224,7 @@ def main():
              "provenance": "Sod shock tube gas of Sec. 5.1(1)"}
     with open(os.path.join(out_dir, "ideal_gamma14.json"), "w") as f:
         json.dump(ideal, f, indent=1)
+    write_global_g129(out_dir)
 
 
 if __name__ == "__main__":

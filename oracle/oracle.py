@@ -270,15 +270,15 @@ def cfl_dt(mech, grid, U, T, cfl):
     return lib().orc_cfl_dt(mh.ref, ctypes.byref(_grid(grid)), _ptr(_f64(U)), _ptr(_f64(T)), float(cfl))
 
 
-CHEM_OFF, CHEM_LIE, CHEM_STRANG = 0, 1, 2
+CHEM_OFF, CHEM_LIE, CHEM_STRANG, CHEM_EXPLICIT = 0, 1, 2, 3
 
 
 def _chem_mode(chem) -> int:
-    """False/True -> off/Lie; or one of CHEM_OFF, CHEM_LIE, CHEM_STRANG."""
+    """False/True -> off/Lie; or one of CHEM_OFF, CHEM_LIE, CHEM_STRANG, CHEM_EXPLICIT."""
     if isinstance(chem, bool):
         return CHEM_LIE if chem else CHEM_OFF
     mode = int(chem)
-    if mode not in (CHEM_OFF, CHEM_LIE, CHEM_STRANG):
+    if mode not in (CHEM_OFF, CHEM_LIE, CHEM_STRANG, CHEM_EXPLICIT):
         raise ValueError(f"chemistry mode {chem!r}")
     return mode
 

@@ -586,6 +586,102 @@ __global__ void __launch_bounds__(128) k_adj_chem_rev(StateView Sstar, GridDev g
   for (int k = 0; k < NV; ++k) out[(long long)k * n + q] = o[k];
 }
 
+// Explicit source S(U): rho Y_k rows receive M_k wdot_k(T(U), X(U)). The VJP
+// nu += (dS/dU)^T mu is the gradient of g = sum_i m_i q_i with
+// m_i = sum_k nu_ki M_k mu_{4+k}, in (T, X) per reaction, chained through
+// X(U) and the implicit dT/dU.
+template <int NS>
+__global__ void __launch_bounds__(128) k_src_vjp(StateView S, GridDev g, const MechDev* __restrict__ mech,
+                                                 const double* __restrict__ mu, double* __restrict__ nu) {
+  constexpr int NSP = NS - 1;
+  constexpr int NV = NS + 3;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= g.n) return;
+  const long long n = g.n;
+  const MechDev& m = *mech;
+  double u[NV], w[NSP];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) u[k] = S.plane(k, n)[q];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) w[k] = m.M[k] * mu[(long long)(4 + k) * n + q];
+  const double T = S.plane(NV, n)[q];
+  double X[NS];
+  double rest = u[0];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    X[k] = u[4 + k] * m.invM[k];
+    rest -= u[4 + k];
+  }
+  X[NSP] = rest * m.invM[NSP];
+  double Ctot = X[0];
+#pragma unroll
+  for (int k = 1; k < NS; ++k) Ctot += X[k];
+  const double lnT = log(T);
+  const double rT = rcp(T);
+  const double rT2 = rT * rT;
+  double eG[NS], reG[NS], dG[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double* c = m.gc[k];
+    eG[k] = exp_t(fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6]))));
+    reG[k] = rcp(eG[k]);
+    dG[k] = fma(c[0], rT, fma(-c[5], rT2, fma(T, fma(T, fma(T, 4.0 * c[4], 3.0 * c[3]), 2.0 * c[2]), c[1])));
+  }
+  const double cref = (P_REF / RU) * rT;
+  const double rcref = (RU / P_REF) * T;
+  double zero[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) zero[k] = 0.0;
+  double gT = 0.0, gX[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) gX[k] = 0.0;
+  for (int i = 0; i < m.nr; ++i) {
+    const int nre = m.nre[i], npr = m.npr[i];
+    double mi = 0.0;
+    for (int r = 0; r < nre; ++r)
+      if (m.rsp[i][r] < NSP) mi = fma(-m.rnud[i][r], w[m.rsp[i][r]], mi);
+    for (int r = 0; r < npr; ++r)
+      if (m.psp[i][r] < NSP) mi = fma(m.pnud[i][r], w[m.psp[i][r]], mi);
+    const double kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
+    const double dlkf = fma(m.b[i], rT, m.EaR[i] * rT2);
+    double kb = kf, dlkb = dlkf;
+    for (int r = 0; r < nre; ++r)
+      for (int qq = 0; qq < m.rnu[i][r]; ++qq) { kb *= eG[m.rsp[i][r]]; dlkb += dG[m.rsp[i][r]]; }
+    for (int r = 0; r < npr; ++r)
+      for (int qq = 0; qq < m.pnu[i][r]; ++qq) { kb *= reG[m.psp[i][r]]; dlkb -= dG[m.psp[i][r]]; }
+    const int dn = m.dnu[i];
+    for (int qq = 0; qq < dn; ++qq) kb *= rcref;
+    for (int qq = 0; qq < -dn; ++qq) kb *= cref;
+    dlkb = fma((double)dn, rT, dlkb);
+    double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
+    monomial(X, m.rsp[i], m.rnu[i], nre, zero, F, gF, DF, hF);
+    monomial(X, m.psp[i], m.pnu[i], npr, zero, B, gB, DB, hB);
+    double Mi = 1.0;
+    if (m.tb[i]) {
+      Mi = Ctot;
+      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
+    }
+    const double net = fma(kf, F, -kb * B);
+    gT = fma(mi * Mi, fma(kf * dlkf, F, -kb * dlkb * B), gT);
+    for (int r = 0; r < nre; ++r) gX[m.rsp[i][r]] = fma(mi * Mi * kf, gF[r], gX[m.rsp[i][r]]);
+    for (int r = 0; r < npr; ++r) gX[m.psp[i][r]] = fma(-mi * Mi * kb, gB[r], gX[m.psp[i][r]]);
+    if (m.tb[i])
+      for (int j = 0; j < NS; ++j) gX[j] = fma(1.0 + m.effm1[i][j], mi * net, gX[j]);
+  }
+  CellThermo<NS> ct;
+  cell_thermo<NS>(u, T, m, ct);
+  double dT[NV], dp[NV];
+  dT_dp_dU<NS>(u, T, m, ct, dT, dp);
+  const double gN = gX[NSP] * m.invM[NSP];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double d = gT * dT[k];
+    if (k == 0) d += gN;
+    if (k >= 4) d += fma(gX[k - 4], m.invM[k - 4], -gN);
+    nu[(long long)k * n + q] += d;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Small kernels: linear combinations, loss terms, primitive T derivative.
 // ---------------------------------------------------------------------------
@@ -728,6 +824,16 @@ cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, co
   switch (ns) {
     case 3: k_adj_chem_rev<3><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out); break;
     case 9: k_adj_chem_rev<9><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const double* mu,
+                              double* nu, cudaStream_t st) {
+  switch (ns) {
+    case 3: k_src_vjp<3><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, mu, nu); break;
+    case 9: k_src_vjp<9><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, mu, nu); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

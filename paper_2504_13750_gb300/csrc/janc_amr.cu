@@ -517,6 +517,7 @@ cudaError_t solve_layer_t(janc_amr_s* A, int i, double dt) {
     ctl.cfl = 0.0;
     ctl.hmin = 1.0;
     ctl.chem_frac = 1.0;
+    ctl.source = 0;
     e = launch_chem(NS, S0, layer_grid(A, i), gp.mech, ctl, a, a + 8, A->d_status, st);
   }
   return e;
@@ -690,7 +691,8 @@ int janc_amr_create(const janc_grid_desc* base, const janc_mechanism* m, const j
   if (a->levels < 0 || a->levels > 6) return afail(JANC_E_INVALID, "janc_amr_create: levels must be 0..6");
   if (a->n_buffer < 0 || a->regrid_every <= 0) return afail(JANC_E_INVALID, "janc_amr_create: bad buffer or period");
   if (base->nx % AH || base->ny % AH) return afail(JANC_E_INVALID, "janc_amr_create: nx, ny must be multiples of 8");
-  if (base->chemistry == JANC_CHEM_STRANG) return afail(JANC_E_UNSUPPORTED, "janc_amr_create: Lie order only");
+  if (base->chemistry == JANC_CHEM_STRANG || base->chemistry == JANC_CHEM_EXPLICIT)
+    return afail(JANC_E_UNSUPPORTED, "janc_amr_create: Lie order only");
   if (((long long)base->nx << a->levels) > 65535 || ((long long)base->ny << a->levels) > 65535 * AB)
     return afail(JANC_E_INVALID, "janc_amr_create: finest index space too large");
   janc_amr_s* A = new janc_amr_s();

@@ -81,8 +81,8 @@ int check_desc(const janc_grid_desc* d, const janc_mechanism* m) {
   if (!m->M || !m->nasa) return fail(JANC_E_INVALID, "null molar masses or NASA-7 table");
   if (m->nr > 0 && (!m->A || !m->b || !m->Ea || !m->nuf || !m->nub || !m->tb || !m->eff))
     return fail(JANC_E_INVALID, "null reaction table");
-  if (d->chemistry != JANC_CHEM_OFF && d->chemistry != JANC_CHEM_LIE && d->chemistry != JANC_CHEM_STRANG)
-    return fail(JANC_E_INVALID, "chemistry must be JANC_CHEM_OFF, JANC_CHEM_LIE or JANC_CHEM_STRANG");
+  if (d->chemistry < JANC_CHEM_OFF || d->chemistry > JANC_CHEM_EXPLICIT)
+    return fail(JANC_E_INVALID, "chemistry must be one of the JANC_CHEM_* modes");
   if (d->chemistry && (m->nr == 0 || m->ns < 3)) return fail(JANC_E_INVALID, "chemistry needs reactions and ns >= 3");
   return JANC_OK;
 }
@@ -393,6 +393,7 @@ int janc_step(janc_grid_t g, int n_steps, double dt, double cfl, double* t_out, 
   ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
   const bool strang = g->d.chemistry == JANC_CHEM_STRANG;
   ctl.chem_frac = strang ? 0.5 : 1.0;
+  ctl.source = g->d.chemistry == JANC_CHEM_EXPLICIT ? 1 : 0;
   double t_before = 0.0;
   if (t_out) {
     cudaError_t e = cudaMemcpyAsync(&t_before, g->clock2, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
@@ -400,7 +401,7 @@ int janc_step(janc_grid_t g, int n_steps, double dt, double cfl, double* t_out, 
     if (e != cudaSuccess) return fail_cuda(e, "janc_step clock read");
   }
   const StateView S0 = sv(g, 0), S1 = sv(g, 1), S2 = sv(g, 2);
-  const bool chem = g->d.chemistry != 0;
+  const bool chem = g->d.chemistry == JANC_CHEM_LIE || g->d.chemistry == JANC_CHEM_STRANG;
   int done = 0;
   while (done < n_steps) {
     const int nc = (n_steps - done) < CHUNK ? (n_steps - done) : CHUNK;
@@ -472,6 +473,7 @@ int janc_source_step(janc_grid_t g, int n_steps, double dt) {
   ctl.cfl = 0.0;
   ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
   ctl.chem_frac = 1.0;
+  ctl.source = 0;
   const StateView S0 = sv(g, 0);
   unsigned long long* a1 = g->alpha + 2;  // the new state's LF speeds, then slot 0
   for (int s = 0; s < n_steps; ++s) {
@@ -691,13 +693,15 @@ int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int
   auto segS = [&](int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
     return StateView{(double*)(seg + (size_t)(ckpt_every + 1 + 3 * m + which - 1) * L.state)};
   };
-  const bool chem = g->d.chemistry != 0;
+  const bool chem = g->d.chemistry == JANC_CHEM_LIE;
+  const bool src = g->d.chemistry == JANC_CHEM_EXPLICIT;
   const double w_loss = dt / g->gd.ny;
   StepCtl ctl;
   ctl.dt_fixed = dt;
   ctl.cfl = 0.0;
   ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
   ctl.chem_frac = 1.0;
+  ctl.source = src ? 1 : 0;
   int rc = JANC_OK;
   cudaError_t e = cudaMemsetAsync(small, 0, 256, st);
   // ---- forward with checkpoints and the loss ----
@@ -772,6 +776,7 @@ int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int
         if (e == cudaSuccess)
           e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
                              st);
+        if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, mu, nu, st);
         if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam2, 2.0 / 3.0, lamS, 1.0, nu, false, st);
         if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0 / 3.0, lamS, 0.0, nullptr, false, st);
         // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
@@ -779,12 +784,14 @@ int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int
         if (e == cudaSuccess)
           e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
                              st);
+        if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, mu, nu, st);
         if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam1, 0.25, lam2, 1.0, nu, false, st);
         if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 0.75, lam2, 0.0, nullptr, true, st);
         // stage 1: U1 = U^n + dt L(U^n)
         if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, dt, lam1, 0.0, nullptr, false, st);
         if (e == cudaSuccess)
           e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 8, g->gd, g->mech, st);
+        if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, mu, nu, st);
         if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0, lam1, 1.0, nu, true, st);
         std::swap(lamN, lam0);
       }

@@ -80,6 +80,7 @@ struct StepCtl {
   double cfl;
   double hmin;       // min(dx, dy)
   double chem_frac;  // share of the step's dt taken by one chemistry launch: 1, or 1/2 in the Strang order
+  int source;        // 1: the production rates are an explicit source of every RK stage
 };
 
 // One request of a batched (serving) launch: its grid constants and buffers.
@@ -208,6 +209,62 @@ __device__ __forceinline__ double sound_speed(const double* u, double t, const M
   const double Cp = Cv + W;
   const double p = RU * W * t;
   return sqrt(Cp * p * rrho * rcp(Cv));
+}
+
+// Molar production rates (Eq. 4.7-4.9) of the carried species k < ns - 1 at
+// (T, X(u)), for the explicit source-term form of the step.
+template <int NS>
+__device__ __forceinline__ void carried_rates(const double* u, double T, const MechDev& m, double* wd) {
+  constexpr int NSP = NS - 1;
+  double X[NS];
+  double rest = u[0];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    X[k] = u[4 + k] * m.invM[k];
+    rest -= u[4 + k];
+    wd[k] = 0.0;
+  }
+  X[NSP] = rest * m.invM[NSP];
+  double Ctot = X[0];
+#pragma unroll
+  for (int k = 1; k < NS; ++k) Ctot += X[k];
+  const double lnT = log(T);
+  const double rT = rcp(T);
+  double eG[NS], reG[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double* c = m.gc[k];
+    eG[k] = exp_t(fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6]))));
+    reG[k] = rcp(eG[k]);
+  }
+  const double cref = (P_REF / RU) * rT;
+  const double rcref = (RU / P_REF) * T;
+  for (int i = 0; i < m.nr; ++i) {
+    const int nre = m.nre[i], npr = m.npr[i];
+    const double kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
+    double kb = kf;
+    for (int r = 0; r < nre; ++r)
+      for (int q = 0; q < m.rnu[i][r]; ++q) kb *= eG[m.rsp[i][r]];
+    for (int r = 0; r < npr; ++r)
+      for (int q = 0; q < m.pnu[i][r]; ++q) kb *= reG[m.psp[i][r]];
+    for (int q = 0; q < m.dnu[i]; ++q) kb *= rcref;
+    for (int q = 0; q < -m.dnu[i]; ++q) kb *= cref;
+    double fwd = kf, bwd = kb;
+    for (int r = 0; r < nre; ++r)
+      for (int q = 0; q < m.rnu[i][r]; ++q) fwd *= X[m.rsp[i][r]];
+    for (int r = 0; r < npr; ++r)
+      for (int q = 0; q < m.pnu[i][r]; ++q) bwd *= X[m.psp[i][r]];
+    double Mi = 1.0;
+    if (m.tb[i]) {
+      Mi = Ctot;
+      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
+    }
+    const double q = Mi * (fwd - bwd);
+    for (int r = 0; r < nre; ++r)
+      if (m.rsp[i][r] < NSP) wd[m.rsp[i][r]] = fma(-m.rnud[i][r], q, wd[m.rsp[i][r]]);
+    for (int r = 0; r < npr; ++r)
+      if (m.psp[i][r] < NSP) wd[m.psp[i][r]] = fma(m.pnud[i][r], q, wd[m.psp[i][r]]);
+  }
 }
 
 // Ghost-cell source index along one axis (3 layers, text after Eq. 4.11).

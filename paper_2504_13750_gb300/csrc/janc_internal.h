@@ -39,6 +39,11 @@ cudaError_t launch_rk_update(int ns, int stage, const StateView& Sin, const Stat
                              const StepCtl& ctl, const unsigned long long* alpha_step, unsigned long long* alpha_out,
                              int* status, double* clock2, cudaStream_t st);
 
+// nu += (dS/dU)^T mu for the explicit source S(U) (production rates of the
+// carried species at the stored T) at state S (janc_adjoint.cu).
+cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const double* mu,
+                              double* nu, cudaStream_t st);
+
 // Point-implicit chemistry in place on S (janc_chem.cu).
 cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
                         const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,

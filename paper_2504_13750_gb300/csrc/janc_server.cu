@@ -179,6 +179,7 @@ void fill_batchreq(janc_server_s* s, Req* r) {
   b.ctl.dt_fixed = r->dt > 0.0 ? r->dt : 0.0;
   b.ctl.cfl = r->cfl > 0.0 ? r->cfl : 0.0;
   b.ctl.chem_frac = 1.0;
+  b.ctl.source = 0;
   b.ctl.hmin = g.dx < g.dy ? g.dx : g.dy;
   int tot_f;
   face_flux_tiles(g, &b.nbx, &b.ntx_x, &b.ntx_y, &tot_f);
@@ -296,7 +297,8 @@ extern "C" {
 int janc_server_create(const janc_mechanism* m, int chemistry, size_t pool_bytes, void* pool, int max_active,
                        void* cuda_stream, janc_server_t* out) {
   if (!m || !out || max_active <= 0) return sfail(JANC_E_INVALID, "janc_server_create: bad argument");
-  if (chemistry == JANC_CHEM_STRANG) return sfail(JANC_E_UNSUPPORTED, "janc_server_create: the server runs the Lie order");
+  if (chemistry == JANC_CHEM_STRANG || chemistry == JANC_CHEM_EXPLICIT)
+    return sfail(JANC_E_UNSUPPORTED, "janc_server_create: the server runs the Lie order");
   // validate the mechanism through the grid checks on a small probe descriptor
   janc_grid_desc probe;
   std::memset(&probe, 0, sizeof probe);
@@ -373,7 +375,8 @@ int janc_server_submit(janc_server_t s, const janc_grid_desc* d, const double* T
   if ((d->bc[0] == JANC_BC_PERIODIC) != (d->bc[1] == JANC_BC_PERIODIC) ||
       (d->bc[2] == JANC_BC_PERIODIC) != (d->bc[3] == JANC_BC_PERIODIC))
     return sfail(JANC_E_INVALID, "janc_server_submit: periodic boundaries must pair");
-  if (d->chemistry == JANC_CHEM_STRANG) return sfail(JANC_E_UNSUPPORTED, "janc_server_submit: the server runs the Lie order");
+  if (d->chemistry == JANC_CHEM_STRANG || d->chemistry == JANC_CHEM_EXPLICIT)
+    return sfail(JANC_E_UNSUPPORTED, "janc_server_submit: the server runs the Lie order");
   if ((d->chemistry != 0) != (s->chem != 0))
     return sfail(JANC_E_INVALID, "janc_server_submit: chemistry flag differs from the server's");
   Req* r = new Req();

@@ -27,7 +27,7 @@ __device__ __forceinline__ void finish_cell(const StateView& S, long long n, lon
 
 // One UPD_BX x UPD_BY block (bx, by) of the stage update; shared by the
 // single-grid and the batched kernels.
-template <int NS, int STAGE>
+template <int NS, int STAGE, bool SRC = false>
 __device__ __forceinline__ void rk_update_block(const StateView& Sin, const StateView& S0, const StateView& Sout,
                                                 const double* __restrict__ Fx, const double* __restrict__ Gy,
                                                 const GridDev& g, const MechDev* __restrict__ mech,
@@ -49,11 +49,21 @@ __device__ __forceinline__ void rk_update_block(const StateView& Sin, const Stat
     const long long idx = (long long)j * g.nx + i;
     const int nx1 = g.nx + 1;
     double u[NV];
+    double src[NV > 4 ? NV - 4 : 1];
+    if (SRC) {  // explicit source term: production rates at the stage input
+      double uin[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) uin[k] = Sin.plane(k, n)[idx];
+      carried_rates<NS>(uin, Sin.plane(NV, n)[idx], *mech, src);
+#pragma unroll
+      for (int k = 0; k < NS - 1; ++k) src[k] *= mech->M[k];
+    }
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const double dF = Fx[((long long)k * g.ny + j) * nx1 + i + 1] - Fx[((long long)k * g.ny + j) * nx1 + i];
       const double dG = Gy[((long long)k * (g.ny + 1) + j + 1) * g.nx + i] - Gy[((long long)k * (g.ny + 1) + j) * g.nx + i];
-      const double L = -fma(dF, g.rdx, dG * g.rdy);
+      double L = -fma(dF, g.rdx, dG * g.rdy);
+      if (SRC && k >= 4) L += src[k - 4];
       const double uin = Sin.plane(k, n)[idx];
       if (STAGE == 1) {
         u[k] = fma(dt, L, uin);
@@ -72,7 +82,7 @@ __device__ __forceinline__ void rk_update_block(const StateView& Sin, const Stat
   block_reduce_alpha_status(sx, sy, st, alpha_out, status);
 }
 
-template <int NS, int STAGE>
+template <int NS, int STAGE, bool SRC>
 __global__ void __launch_bounds__(UPD_BX* UPD_BY) k_rk_update(StateView Sin, StateView S0, StateView Sout,
                                                               const double* __restrict__ Fx,
                                                               const double* __restrict__ Gy, GridDev g,
@@ -80,8 +90,8 @@ __global__ void __launch_bounds__(UPD_BX* UPD_BY) k_rk_update(StateView Sin, Sta
                                                               const unsigned long long* __restrict__ alpha_step,
                                                               unsigned long long* alpha_out, int* status,
                                                               double* clock2) {
-  rk_update_block<NS, STAGE>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, alpha_step, alpha_out, status, clock2, blockIdx.x,
-                             blockIdx.y);
+  rk_update_block<NS, STAGE, SRC>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, alpha_step, alpha_out, status, clock2,
+                                  blockIdx.x, blockIdx.y);
 }
 
 // Batched stage update over the flattened (request, block) list. Stage s
@@ -162,12 +172,21 @@ static cudaError_t launch_rk_update_t(int stage, const StateView& Sin, const Sta
                                       const StepCtl& ctl, const unsigned long long* a_step, unsigned long long* a_out,
                                       int* status, double* clock2, cudaStream_t st) {
   dim3 blk(UPD_BX, UPD_BY), grd((g.nx + UPD_BX - 1) / UPD_BX, (g.ny + UPD_BY - 1) / UPD_BY);
-  if (stage == 1)
-    k_rk_update<NS, 1><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
-  else if (stage == 2)
-    k_rk_update<NS, 2><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
-  else
-    k_rk_update<NS, 3><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+  if (ctl.source && NS > 1) {
+    if (stage == 1)
+      k_rk_update<NS, 1, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+    else if (stage == 2)
+      k_rk_update<NS, 2, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+    else
+      k_rk_update<NS, 3, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+  } else {
+    if (stage == 1)
+      k_rk_update<NS, 1, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+    else if (stage == 2)
+      k_rk_update<NS, 2, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+    else
+      k_rk_update<NS, 3, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+  }
   return cudaGetLastError();
 }
 

@@ -153,7 +153,7 @@ def _where(*args):
     return ws.pop() if ws else JANC_HOST
 
 
-CHEM_OFF, CHEM_LIE, CHEM_STRANG = 0, 1, 2
+CHEM_OFF, CHEM_LIE, CHEM_STRANG, CHEM_EXPLICIT = 0, 1, 2, 3
 
 
 def chem_mode(chemistry) -> int:

@@ -79,6 +79,33 @@ def test_trajectory_dot_product_with_chemistry(J):
     g.close()
 
 
+def test_explicit_source_trajectory_dot_product(J):
+    """Adjoint of the explicit source-term form (JANC_CHEM_EXPLICIT, one-step
+    global mechanism): <seed, dU^N> from the oracle's trajectory tangent
+    equals <dL/dU^0, dU^0> from the GPU reverse sweep."""
+    glob = inputs.load_mechanism("global_h2o2_g129")
+    Y = inputs.premix_Y(glob, {"H2": 4.032, "O2": 31.998})
+    st = inputs.tube(glob, 24, 8, Lx=0.025 * 24 / 128, Y=Y, perturb_seed=4)
+    rng = np.random.default_rng(13)
+    st["T"] = st["T"] + rng.normal(0.0, 5.0, st["T"].shape)
+    st["u"] = rng.normal(0.0, 40.0, st["T"].shape)
+    U = orc.prim_to_cons(glob, st["T"], st["p"], st["u"], st["v"], st["Y"])
+    dt = 1e-8
+    g = J.Grid.from_grid_dict(glob, st["grid"], chemistry=J.CHEM_EXPLICIT)
+    g.set_state(U, st["T"])
+    scale = np.maximum(np.abs(U).reshape(U.shape[0], -1).max(axis=1), 1e-12)
+    seed = np.ascontiguousarray(rng.normal(size=U.shape) / scale[:, None, None])
+    gU0 = np.zeros_like(U)
+    J.janc_step_adjoint(g.handle, 12, dt, 5, J.LOSS_SEEDED, seed, gU0)
+    V = _dirs(U, 4, 14)
+    dUN, _, _, s = orc.trajectory_tangent(glob, st["grid"], U, st["T"], V, 12, dt, chem=orc.CHEM_EXPLICIT)
+    assert s == 0
+    for l in range(4):
+        a, b = float(np.sum(seed * dUN[l])), float(np.sum(gU0 * V[l]))
+        assert abs(a - b) <= 1e-8 * np.sum(np.abs(seed * dUN[l])), (l, a, b)
+    g.close()
+
+
 def test_endwall_loss_value_and_gradient(J):
     st, U = _state(24, 8, 9, vel=40.0)
     dt = 2e-8

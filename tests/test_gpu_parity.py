@@ -151,6 +151,32 @@ def test_strang_rejected_by_server_and_adjoint(J):
     g.close()
 
 
+GLOBAL = inputs.load_mechanism("global_h2o2_g129")
+
+
+@pytest.mark.parametrize("steps", [1, 60])
+def test_explicit_source_global_mechanism(J, steps):
+    """JANC_CHEM_EXPLICIT (production rates as an RK3 source, no split
+    chemistry) with the one-step global mechanism at gamma = 1.29: a 128 x 16
+    stoichiometric H2-O2 tube with the 2000 K / 20 atm igniter."""
+    Y = inputs.premix_Y(GLOBAL, {"H2": 4.032, "O2": 31.998})
+    st = inputs.tube(GLOBAL, 128, 16, Lx=0.025, Y=Y, perturb_seed=1)
+    U = _cons(GLOBAL, st)
+    g = _grid(J, GLOBAL, st, chem=J.CHEM_EXPLICIT)
+    g.set_state(U, st["T"])
+    t, _ = g.step(steps, cfl=0.5, want_time=True)
+    Ug, Tg = g.get_state()
+    Uo, To, s, to, _ = orc.step(GLOBAL, st["grid"], U, st["T"], steps, cfl=0.5, chem=orc.CHEM_EXPLICIT)
+    assert s == 0
+    tol = 1e-10 if steps == 1 else 1e-8
+    assert abs(t - to) / to < 1e-12
+    assert rel_err(Ug, Uo) < tol
+    assert rel_err(Tg[None], To[None]) < tol
+    if steps > 1:  # the igniter has formed water (nothing is clipped: WENO may undershoot near 0)
+        assert np.max(1.0 - (Ug[4] + Ug[5]) / Ug[0]) > 0.05
+    g.close()
+
+
 def test_sod_gpu(J):
     import ref_exact
 
