@@ -333,6 +333,26 @@ def run_amr(janc, stream, levels=3, warm=20, steps=40, every=10):
             "note": "wall clock with host syncs (regrid block lists, CFL read) inside the timed region"}
 
 
+def run_inverse(janc, iters=15):
+    """Inverse-problem leg (the synthetic form of Sec. 6.2): 1000 x 400
+    periodic channel, one-step global reaction as an explicit source, loss of
+    Eq. 6.6 after 100 fixed-dt steps; Adam iterations per second, each one a
+    forward of 100 steps plus janc_step_adjoint over them (checkpoint every
+    20) plus the two state set-ups of dU_0/dtheta."""
+    from paper_2504_13750_gb300 import inverse
+
+    t0 = time.perf_counter()
+    P = inverse.ChannelInverse(nx=1000, ny=400, n_steps=100, dev_steps=400, ckpt_every=20)
+    setup = time.perf_counter() - t0
+    P.loss_and_grad(0.8)  # warm-up
+    hist, wall = P.optimize(0.8, iters=iters, lr=0.01)
+    P.close()
+    return {"workload": "channel_1000x400_global_h2o2_g129_explicit_100steps_adam_lr0.01",
+            "iterations": iters, "iterations_per_s": iters / wall, "setup_s": setup,
+            "theta_start": hist[0][0], "theta_end": hist[-1][0], "loss_start": hist[0][1], "loss_end": hist[-1][1],
+            "note": "paper (A100, JAX): 1.20 iterations/s on its 1000 x 400 RDC case with 100 steps per iteration"}
+
+
 def run_ours(args):
     import torch
 
@@ -457,6 +477,8 @@ def run_ours(args):
         line["adjoint"] = run_adjoint(janc, stream)
     if rank == 0 and not args.no_amr:
         line["amr"] = run_amr(janc, stream)
+    if rank == 0 and not args.no_inverse:
+        line["inverse"] = run_inverse(janc)
     if not args.no_serving:
         line["serving"] = run_serving(janc, stream, args.serving_requests, tuple(args.serving_steps))
     if rank == 0:
@@ -475,6 +497,8 @@ def run_only(args):
     if args.only == "adjoint":
         n = args.leg_steps or 500
         out = run_adjoint(janc, stream, nsteps=n, ckpt=max(1, n // 10))
+    elif args.only == "inverse":
+        out = run_inverse(janc, iters=args.leg_steps or 15)
     else:
         out = run_amr(janc, stream, steps=args.leg_steps or 40)
     print(json.dumps(out), flush=True)
@@ -492,12 +516,13 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--no-inverse", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests in the serving leg (the full stream is 256 with --serving-steps 100 1000)")
     ap.add_argument("--serving-steps", type=int, nargs=2, default=(50, 150))
     ap.add_argument("--nx", type=int, default=NX, help="tube cells along x (default: the 4096 x 512 workload)")
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--only", choices=("adjoint", "amr"), default=None,
+    ap.add_argument("--only", choices=("adjoint", "amr", "inverse"), default=None,
                     help="run one side leg alone and print its JSON object (for profiling)")
     ap.add_argument("--leg-steps", type=int, default=None,
                     help="with --only: adjoint trajectory steps (checkpoint every steps/10) or timed AMR base steps")
