@@ -353,6 +353,24 @@ def run_inverse(janc, iters=15):
             "note": "paper (A100, JAX): 1.20 iterations/s on its 1000 x 400 RDC case with 100 steps per iteration"}
 
 
+def reduce_max(pg, x, device="cuda"):
+    """Max over ranks of a per-rank scalar (the slowest rank's time); x
+    itself when there is no process group."""
+    if pg is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units processed by all ranks (weak scaling: every rank runs its own
+    replica) per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def run_ours(args):
     import torch
 
@@ -400,12 +418,9 @@ def run_ours(args):
     stt = g.status()
     if stt["status"] != 0:
         raise RuntimeError(f"device status {stt['status']:#x} after the timed region")
-    if pg:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(pg, ms)
     cells = NX * NY
-    value = world * cells * args.steps / (ms * 1e-3)
+    value = whole_job_rate(world, cells * args.steps, ms * 1e-3)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     nv = g.nv
@@ -422,11 +437,8 @@ def run_ours(args):
             janc.janc_step(g.handle, 1, cfl=CFL)
             janc.janc_get_state(g.handle, Uh, Th)
         e2e_s = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT,
+        e2e_s = reduce_max(pg, e2e_s)
+        e2e = {"value": whole_job_rate(world, cells * e2e_steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(Uh.nbytes + Th.nbytes), "d2h_bytes_per_step": int(Uh.nbytes + Th.nbytes),
                "steps": e2e_steps}
 
