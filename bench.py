@@ -177,12 +177,14 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
-def serve_stream(janc, mech_c, reqs, states, arrivals, max_active, pool_bytes, stream):
+def serve_stream(janc, mech_c, reqs, states, arrivals, max_active, pool_bytes, stream, cell_budget=0, max_skip_s=0.0):
     """Replays the request stream in real time through one server: a request
     is submitted once its arrival time has passed. Returns per-request
     latencies (completion - arrival, s) and the makespan."""
     s = janc.janc_server_create(mech_c, chemistry=True, pool_bytes=pool_bytes, max_active=max_active,
                                 stream=stream.cuda_stream)
+    if cell_budget:
+        janc.janc_server_set_cell_budget(s, cell_budget, max_skip_s)
     try:
         n = len(reqs)
         ids = [None] * n
@@ -218,10 +220,16 @@ def serve_stream(janc, mech_c, reqs, states, arrivals, max_active, pool_bytes, s
         janc.janc_server_destroy(s)
 
 
+SERVE_BUDGET_CELLS = 600_000   # just above the largest request (2048 x 256)
+SERVE_MAX_SKIP_S = 1.0
+
+
 def run_serving(janc, stream, n_req, steps_range, seed=1):
     """Serving leg: solves of mixed size and mixture arriving as a Poisson
     stream at 1.5x the one-at-a-time capacity, served by the batched server
-    and by a one-slot server running the same kernels."""
+    (active set capped at 600k cells, later requests may pass a blocked one
+    for 1 s) and by a one-slot server running the same kernels. The closed-
+    system capacity of the uncapped batched server is reported beside."""
     from paper_2504_13750_gb300 import inputs
 
     mech = inputs.load_mechanism("h2air_synth")
@@ -231,9 +239,11 @@ def run_serving(janc, stream, n_req, steps_range, seed=1):
     cell_steps = [r["nx"] * r["ny"] * r["steps"] for r in reqs]
     pool = 16 << 30
     zero = [0.0] * n_req
+    budget = dict(cell_budget=SERVE_BUDGET_CELLS, max_skip_s=SERVE_MAX_SKIP_S)
     # closed system (everything queued at t = 0): the capacity of each mode
     _, span_seq = serve_stream(janc, mech_c, reqs, states, zero, 1, pool, stream)
-    _, span_bat = serve_stream(janc, mech_c, reqs, states, zero, 256, pool, stream)
+    _, span_bat = serve_stream(janc, mech_c, reqs, states, zero, 256, pool, stream, **budget)
+    _, span_ps = serve_stream(janc, mech_c, reqs, states, zero, 256, pool, stream)
     cap_seq = n_req / span_seq
     # open system: Poisson arrivals at 1.5x the one-at-a-time capacity
     rate = 1.5 * cap_seq
@@ -242,15 +252,17 @@ def run_serving(janc, stream, n_req, steps_range, seed=1):
     arrivals = list(arrivals - arrivals[0])
     out = {"requests": n_req, "steps_range": list(steps_range), "grids": [list(g) for g in inputs.SERVING_GRIDS],
            "cell_steps": int(sum(cell_steps)),
-           "capacity_solves_per_s": {"batched": n_req / span_bat, "one_at_a_time": cap_seq},
+           "capacity_solves_per_s": {"batched": n_req / span_bat, "one_at_a_time": cap_seq,
+                                     "batched_uncapped": n_req / span_ps},
            "capacity_cell_steps_per_s": {"batched": sum(cell_steps) / span_bat,
                                          "one_at_a_time": sum(cell_steps) / span_seq},
-           "offered_rate_per_s": rate, "offered_load_vs_one_at_a_time": 1.5}
-    for name, slots in (("batched", 256), ("one_at_a_time", 1)):
-        lat, span = serve_stream(janc, mech_c, reqs, states, arrivals, slots, pool, stream)
+           "offered_rate_per_s": rate, "offered_load_vs_one_at_a_time": 1.5,
+           "batched_policy": {"max_active": 256, "cell_budget": SERVE_BUDGET_CELLS, "max_skip_s": SERVE_MAX_SKIP_S}}
+    for name, slots, kw in (("batched", 256, budget), ("one_at_a_time", 1, {})):
+        lat, span = serve_stream(janc, mech_c, reqs, states, arrivals, slots, pool, stream, **kw)
         out[name] = {"solves_per_s": n_req / span, "cell_steps_per_s": sum(cell_steps) / span,
                      "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                     "makespan_s": span, "max_active": slots}
+                     "mean_latency_s": float(np.mean(lat)), "makespan_s": span, "max_active": slots}
     out["batched_vs_one_at_a_time_solves"] = out["batched"]["solves_per_s"] / out["one_at_a_time"]["solves_per_s"]
     out["batched_vs_one_at_a_time_capacity"] = span_seq / span_bat
     return out
@@ -511,6 +523,8 @@ def run_only(args):
         out = run_adjoint(janc, stream, nsteps=n, ckpt=max(1, n // 10))
     elif args.only == "inverse":
         out = run_inverse(janc, iters=args.leg_steps or 15)
+    elif args.only == "serving":
+        out = run_serving(janc, stream, args.serving_requests, tuple(args.serving_steps))
     else:
         out = run_amr(janc, stream, steps=args.leg_steps or 40)
     print(json.dumps(out), flush=True)
@@ -534,7 +548,7 @@ def main():
     ap.add_argument("--serving-steps", type=int, nargs=2, default=(50, 150))
     ap.add_argument("--nx", type=int, default=NX, help="tube cells along x (default: the 4096 x 512 workload)")
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--only", choices=("adjoint", "amr", "inverse"), default=None,
+    ap.add_argument("--only", choices=("adjoint", "amr", "inverse", "serving"), default=None,
                     help="run one side leg alone and print its JSON object (for profiling)")
     ap.add_argument("--leg-steps", type=int, default=None,
                     help="with --only: adjoint trajectory steps (checkpoint every steps/10) or timed AMR base steps")

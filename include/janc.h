@@ -292,6 +292,16 @@ typedef struct {
 int janc_server_create(const janc_mechanism* m, int chemistry, size_t pool_bytes, void* pool, int max_active,
                        void* cuda_stream, janc_server_t* out);
 
+/* Cap on the summed cells of the active set (0, the default: none). A
+ * queued request that would take the active set past the cap waits until the
+ * active set has room or is empty (a request larger than the cap runs alone).
+ * Later requests may pass it until it has waited max_skip_s seconds since its
+ * submission; after that nothing behind it is admitted, so the active set
+ * drains for it (max_skip_s = 0: strict arrival order under the cap). Bounds
+ * how many solves share the GPU at once, so that a solve runs near full speed
+ * instead of being time-shared with every admitted one. */
+int janc_server_set_cell_budget(janc_server_t s, long long cells, double max_skip_s);
+
 /* Device bytes a request of this grid occupies while active. */
 int janc_server_footprint(janc_server_t s, const janc_grid_desc* d, size_t* bytes);
 

@@ -120,6 +120,9 @@ struct janc_server_s {
   bool owns_pool = false;
   Pool pool;
   int max_active = 0;
+  long long cell_budget = 0;   // cap on the active set's cells (0: none)
+  double max_skip_s = 0.0;     // how long later requests may pass a budget-blocked one
+  long long active_cells = 0;
   cudaStream_t stream = nullptr, copy_stream = nullptr;
   std::vector<Req*> reqs;
   std::deque<int> queue;
@@ -202,6 +205,7 @@ int admit(janc_server_s* s, Req* r) {
   r->fresh = 1;
   r->t_admit = now_s();
   s->active.push_back(r->id);
+  s->active_cells += r->n;
   s->dirty = true;
   return JANC_OK;
 }
@@ -210,6 +214,14 @@ void try_admit(janc_server_s* s) {
   for (auto it = s->queue.begin(); it != s->queue.end();) {
     if ((int)s->active.size() >= s->max_active) break;
     Req* r = s->reqs[*it];
+    // the cell budget admits a request that would exceed it only into an empty
+    // active set; later requests may pass it until it has waited max_skip_s,
+    // then nothing behind it is admitted (the active set drains for it)
+    if (s->cell_budget > 0 && !s->active.empty() && s->active_cells + r->n > s->cell_budget) {
+      if (now_s() - r->t_submit >= s->max_skip_s) break;
+      ++it;
+      continue;
+    }
     size_t off;
     if (s->pool.alloc(r->footprint, &off)) {
       r->off = off;
@@ -287,12 +299,20 @@ int retire(janc_server_s* s, Req* r) {
   if (e == cudaSuccess) e = cudaEventRecord(r->ev_copy, s->copy_stream);
   if (e != cudaSuccess) return scuda(e, "retire copy");
   r->state = R_COPYING;
+  s->active_cells -= r->n;
   return JANC_OK;
 }
 
 }  // namespace
 
 extern "C" {
+
+int janc_server_set_cell_budget(janc_server_t s, long long cells, double max_skip_s) {
+  if (!s || cells < 0 || !(max_skip_s >= 0.0)) return sfail(JANC_E_INVALID, "janc_server_set_cell_budget: bad argument");
+  s->cell_budget = cells;
+  s->max_skip_s = max_skip_s;
+  return JANC_OK;
+}
 
 int janc_server_create(const janc_mechanism* m, int chemistry, size_t pool_bytes, void* pool, int max_active,
                        void* cuda_stream, janc_server_t* out) {

@@ -97,6 +97,7 @@ def lib():
             L.janc_server_run.argtypes = [p, i, p]
             L.janc_server_poll.argtypes = [p, i, p]
             L.janc_server_fetch.argtypes = [p, i, p, p]
+            L.janc_server_set_cell_budget.argtypes = [p, ctypes.c_longlong, d]
             L.janc_server_destroy.argtypes = [p]
             L.janc_server_destroy.restype = None
             L.janc_adjoint_workspace_bytes.argtypes = [p, i, i, ctypes.POINTER(ctypes.c_size_t)]
@@ -326,6 +327,10 @@ def janc_selfcheck_rcp(x) -> int:
     out = ctypes.c_longlong()
     _check(lib().janc_selfcheck_rcp(x.ctypes.data_as(ctypes.c_void_p), int(x.size), ctypes.byref(out)))
     return out.value
+
+
+def janc_server_set_cell_budget(s, cells, max_skip_s=0.0):
+    _check(lib().janc_server_set_cell_budget(s, int(cells), float(max_skip_s)))
 
 
 def janc_server_create(mech: Mechanism, chemistry=True, pool_bytes=1 << 30, pool_ptr=None, max_active=64,

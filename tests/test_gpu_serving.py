@@ -48,9 +48,11 @@ def _alone(J, st, steps):
     return U, T
 
 
-def _serve(J, reqs, pool_bytes=2 << 30, max_active=64, stagger=0, watch=None):
+def _serve(J, reqs, pool_bytes=2 << 30, max_active=64, stagger=0, watch=None, budget=None):
     mech = J.Mechanism(H2AIR)
     s = J.janc_server_create(mech, chemistry=True, pool_bytes=pool_bytes, max_active=max_active)
+    if budget is not None:
+        J.janc_server_set_cell_budget(s, *budget)
     ids = []
     pending = list(reqs)
     try:
@@ -65,7 +67,7 @@ def _serve(J, reqs, pool_bytes=2 << 30, max_active=64, stagger=0, watch=None):
             pending = pending[take:]
             info = J.janc_server_run(s, 1)
             if watch is not None:
-                watch(info)
+                watch(info, s, ids)
             if not pending and info["n_active"] == 0 and info["n_queued"] == 0 and info["n_copying"] == 0:
                 break
         out = []
@@ -111,7 +113,7 @@ def test_admission_respects_pool(J):
     pool = int(2.5 * big) + (1 << 20)
     peak = {"used": 0, "active": 0}
 
-    def watch(info):
+    def watch(info, *_):
         assert info["pool_used"] <= info["pool_bytes"]
         peak["used"] = max(peak["used"], info["pool_used"])
         peak["active"] = max(peak["active"], info["n_active"])
@@ -121,6 +123,26 @@ def test_admission_respects_pool(J):
     for (Ua, Ta), (Um, Tm) in zip(alone, served):
         assert np.array_equal(Ua, Um) and np.array_equal(Ta, Tm)
     assert peak["used"] > 0
+
+
+@pytest.mark.parametrize("max_skip_s", [0.0, 10.0])
+def test_cell_budget_bounds_the_active_set(J, max_skip_s):
+    """With a cell budget the active set never holds more cells than the cap
+    unless one request runs alone, and every result is still the alone one,
+    bit for bit."""
+    reqs = _requests()
+    cap = 9000
+
+    def watch(info, s, ids):
+        # ids[k] is the id of reqs[k] (submission order)
+        active = [k for k, rid in enumerate(ids) if J.janc_server_poll(s, rid)["state"] == J.REQ_ACTIVE]
+        tot = sum(reqs[k][0]["nx"] * reqs[k][0]["ny"] for k in active)
+        assert len(active) <= 1 or tot <= cap, (active, tot)
+
+    served = _serve(J, reqs, watch=watch, budget=(cap, max_skip_s))
+    alone = [_alone(J, st, req["steps"]) for req, st in reqs]
+    for (Ua, Ta), (Um, Tm) in zip(alone, served):
+        assert np.array_equal(Ua, Um) and np.array_equal(Ta, Tm)
 
 
 def test_served_request_matches_oracle(J):
