@@ -114,3 +114,37 @@ def test_amr_without_refinement_is_the_grid_step(J):
     assert J.janc_amr_layer_blocks(a.handle, 1) == 0
     a.close()
     g.close()
+
+
+def test_full_layer_is_a_decomposed_fine_grid(J):
+    """Domain decomposition is exact: with every layer-1 block present (a
+    threshold every cell exceeds), layer 1 is the 2x-finer grid cut into
+    16 x 16 blocks that exchange 3 ghost columns per side every RK stage.
+    From the same one-to-four start it must step like one undecomposed fine
+    grid with dt/2 (the single-GPU form of the "N subdomains = 1 domain"
+    parity), to rounding."""
+    st = inputs.tube(H2AIR, 64, 16, Lx=0.05 * 64 / 256, perturb_seed=3)
+    a = J.Amr(H2AIR, st["grid"], chemistry=True, levels=1, threshold=-1.0, n_buffer=0, regrid_every=1000)
+    a.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    U0, T0 = a.base()
+    gf = dict(st["grid"], nx=128, ny=32, dx=st["grid"]["dx"] / 2, dy=st["grid"]["dy"] / 2)
+    f = J.Grid.from_grid_dict(H2AIR, gf)
+    f.set_state(np.ascontiguousarray(np.repeat(np.repeat(U0, 2, 1), 2, 2)),
+                np.ascontiguousarray(np.repeat(np.repeat(T0, 2, 0), 2, 1)))
+    dt = 2e-8
+    for n in range(1, 5):
+        a.step(1, dt=dt)
+        f.step(2, dt=dt / 2)
+        pos, UL, TL = a.layer(1)
+        assert len(pos) == (128 // 16) * (32 // 16)
+        Ug = np.zeros((UL.shape[1], 32, 128))
+        Tg = np.zeros((32, 128))
+        for k, (bx, by) in enumerate(pos):
+            Ug[:, by * 16:(by + 1) * 16, bx * 16:(bx + 1) * 16] = UL[k]
+            Tg[by * 16:(by + 1) * 16, bx * 16:(bx + 1) * 16] = TL[k]
+        Uf, Tf = f.get_state()
+        assert rel_err(Ug, Uf) < 1e-12 * n, (n, rel_err(Ug, Uf))
+        assert np.max(np.abs(Tg - Tf) / Tf) < 1e-12 * n
+    assert a.status() == 0
+    a.close()
+    f.close()
