@@ -543,7 +543,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-inverse", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=32,
+    ap.add_argument("--serving-requests", type=int, default=64,
                     help="requests in the serving leg (the full stream is 256 with --serving-steps 100 1000)")
     ap.add_argument("--serving-steps", type=int, nargs=2, default=(50, 150))
     ap.add_argument("--nx", type=int, default=NX, help="tube cells along x (default: the 4096 x 512 workload)")
