@@ -106,6 +106,41 @@ def test_explicit_source_trajectory_dot_product(J):
     g.close()
 
 
+def test_smooth_case_gradient_vs_central_differences(J):
+    """Adjoint against central differences of the GPU forward loss to 1e-6
+    where finite differences can resolve it: a smooth premixed state (1150 K
+    with an 80 K bump, smooth p, u, v; no shock), 20 steps with chemistry,
+    the end-wall loss, a temperature direction uniform in y (WENO-JS's
+    absolute epsilon makes y-varying perturbations of nearly uniform rows
+    nonlinear at the 1e-3 K scale), Richardson over h = 0.2 and 0.1 K."""
+    nx, ny = 48, 12
+    X, Yg = np.meshgrid((np.arange(nx) + 0.5) / nx, (np.arange(ny) + 0.5) / ny)
+    T = 1150 + 80 * np.exp(-((X - 0.3) ** 2 + (Yg - 0.4) ** 2) / 0.02)
+    p = 2 * inputs.ATM * (1 + 0.05 * np.cos(2 * np.pi * X))
+    u = 5 * np.sin(2 * np.pi * Yg)
+    v = 3 * np.cos(2 * np.pi * X)
+    Y = np.ascontiguousarray(np.repeat(inputs.h2air_Y(H2AIR, 1.0)[:, None, None], ny, 1).repeat(nx, 2))
+    grid = inputs.grid_dict(nx, ny, 1e-4, 1e-4, [0, 0, 1, 1])
+    g = J.Grid.from_grid_dict(H2AIR, grid, chemistry=True)
+    n, dt = 20, 2e-8
+    d = np.cos(np.pi * X)
+
+    def loss(eps):
+        g.set_primitive(T + eps * d, p, u, v, Y)
+        return J.janc_step_adjoint(g.handle, n, dt, 5, J.LOSS_ENDWALL_P, None, None)
+
+    g.set_primitive(T, p, u, v, Y)
+    gU0 = np.zeros((g.nv, ny, nx))
+    J.janc_step_adjoint(g.handle, n, dt, 5, J.LOSS_ENDWALL_P, None, gU0)
+    h = 1e-3
+    dU = (orc.prim_to_cons(H2AIR, T + h * d, p, u, v, Y) - orc.prim_to_cons(H2AIR, T - h * d, p, u, v, Y)) / (2 * h)
+    ad = float(np.sum(gU0 * dU))
+    fd = [(loss(hh) - loss(-hh)) / (2 * hh) for hh in (0.2, 0.1)]
+    fd_r = (4 * fd[1] - fd[0]) / 3
+    assert abs(ad - fd_r) <= 1e-6 * abs(fd_r), (ad, fd_r, fd)
+    g.close()
+
+
 def test_endwall_loss_value_and_gradient(J):
     st, U = _state(24, 8, 9, vel=40.0)
     dt = 2e-8
