@@ -364,7 +364,8 @@ int janc_rhs_static(const janc_grid_desc* d, const janc_mechanism* m, const doub
  * Algorithm 3 (ghost blocks from the same-layer neighbours or the physical
  * boundary; cells within 3 of a side with no neighbour take the layer-(i-1)
  * values after every RK stage; chemistry over the layer's dt), then the
- * four-to-one mean from the deepest layer up. The base dt is fixed or the CFL
+ * four-to-one mean from the deepest layer up, onto the parent cells none of
+ * whose children lies in an external band. The base dt is fixed or the CFL
  * of layer 0 at the step's start; layer i uses dt / 2^i. Chemistry:
  * JANC_CHEM_OFF or JANC_CHEM_LIE. nx, ny of the base must be multiples of 8. */
 typedef struct janc_amr_s* janc_amr_t;
@@ -375,6 +376,9 @@ typedef struct {
   double threshold;   /* refinement criterion |grad T| > threshold, K/m */
   int n_buffer;       /* buffer cells around the masked cells (layer i-1 cells) */
   int regrid_every;   /* base steps between regrids (>= 1); step 0 builds the layers */
+  int synchronous;    /* 0: crossover advance (Fig. 2a); 1: synchronous advance (Fig. 2b): every
+                         layer takes the step's dt (the CFL dt of layer 0 / 2^levels when the CFL
+                         drives it), deepest first */
 } janc_amr_desc;
 
 /* Create an AMR hierarchy over the base grid `base` (device memory owned by
@@ -385,8 +389,9 @@ int janc_amr_create(const janc_grid_desc* base, const janc_mechanism* m, const j
  * refined layers are rebuilt at the next step. */
 int janc_amr_set_state_primitive(janc_amr_t a, const double* T, const double* p, const double* u, const double* v,
                                  const double* Y, int where);
-/* n base steps with a fixed dt (> 0) or the CFL number (> 0); t_out (may be
- * null) receives the simulated time advanced. */
+/* n steps with a fixed dt (> 0) or the CFL number (> 0); t_out (may be
+ * null) receives the simulated time advanced. A crossover step advances the
+ * base dt; a synchronous step advances dt (or the CFL dt of layer 0 / 2^levels). */
 int janc_amr_step(janc_amr_t a, int n_steps, double dt, double cfl, double* t_out);
 /* Blocks of layer `level` (1..levels). */
 int janc_amr_layer_blocks(janc_amr_t a, int level, int* nblk);
@@ -398,7 +403,8 @@ int janc_amr_get_layer(janc_amr_t a, int level, int* pos, double* U, double* T);
 int janc_amr_get_base(janc_amr_t a, double* U, double* T, int where);
 /* OR of the JANC_ST_* bits of every layer since creation. Synchronous. */
 int janc_amr_status(janc_amr_t a, int* status);
-/* Cell updates of the last base step: base cells + sum over layers of 2^i x cells. */
+/* Cell updates of the last step: base cells + sum over layers of 2^i x cells
+ * (crossover) or of the cells once (synchronous). */
 int janc_amr_cell_updates(janc_amr_t a, long long* per_step);
 void janc_amr_destroy(janc_amr_t a);
 

@@ -41,7 +41,12 @@ structure, in the paper's terms:
 * Crossover advance (Fig. 2a): layer i takes two steps of dt_i / 2 on layer
   i + 1 before each of its own steps of dt_i, deepest layer first
   (Algorithm 2); then interpolate_fine_to_coarse ("four to one" arithmetic
-  mean, layers ..., 2, 1 in turn) once per base step.
+  mean, layers ..., 2, 1 in turn) once per base step, onto the parent cells
+  whose children are all outside the external band (the band holds copies
+  of the parent, so averaging it back would freeze that region).
+* Synchronous advance (Fig. 2b): every layer takes one step of the deepest
+  layer's dt, deepest layer first, then the four-to-one means; a step then
+  advances dt_base / 2^levels.
 * The blocks are regenerated every regrid_every base steps (before the
   solve, as in Algorithm 2); a block that exists before and after keeps its
   data (find_and_update_unaltered_block), a new block is refined from its
@@ -98,7 +103,7 @@ class Layer:
 
 class AMROracle:
     def __init__(self, mech, grid, U0, T0, levels=2, threshold=1e6, n_buffer=2, B=16, regrid_every=10,
-                 chem=True, force_blocks=None):
+                 chem=True, force_blocks=None, synchronous=False):
         assert B % 2 == 0 and grid["nx"] % (B // 2) == 0 and grid["ny"] % (B // 2) == 0
         self.m = mech
         self.g0 = dict(grid)
@@ -110,6 +115,7 @@ class AMROracle:
         self.regrid_every = regrid_every
         self.chem = chem
         self.force_blocks = force_blocks      # optional {level: set of (bx, by)} overriding the criterion
+        self.synchronous = synchronous
         self.U0 = np.array(U0, dtype=np.float64)
         self.T0 = np.array(T0, dtype=np.float64)
         self.layers = [None] + [self._layer(i, [], np.zeros((0, self.nv, B, B)), np.zeros((0, B, B)))
@@ -338,18 +344,24 @@ class AMROracle:
         self.solve_layer(i, dt)
 
     def fine_to_coarse(self):
-        """interpolate_fine_to_coarse: four-to-one arithmetic mean, layers ..., 2, 1."""
+        """interpolate_fine_to_coarse: four-to-one arithmetic mean, layers ..., 2, 1,
+        onto the parent cells none of whose four children lies in the block's
+        external band (those children are copies of the parent, not values
+        the fine solver computed; the parent keeps its own value there)."""
         h = self.B // 2
         for i in range(self.levels, 0, -1):
             L = self.layers[i]
             for k, (bx, by) in enumerate(L.pos):
                 f = L.U[k]
+                band = self.external_band(L, k)
+                keep = band[0::2, 0::2] | band[0::2, 1::2] | band[1::2, 0::2] | band[1::2, 1::2]
                 mean = 0.25 * ((f[:, 0::2, 0::2] + f[:, 0::2, 1::2]) + (f[:, 1::2, 0::2] + f[:, 1::2, 1::2]))
                 if i - 1 == 0:
                     ys, xs = slice(by * h, (by + 1) * h), slice(bx * h, (bx + 1) * h)
                     Tw = self.T0[ys, xs]
                     Tn, st = orc.newton(self.m, dict(self.g0, nx=h, ny=h), mean, Tw)
                     assert st == 0, st
+                    mean[:, keep], Tn[keep] = self.U0[:, ys, xs][:, keep], Tw[keep]
                     self.U0[:, ys, xs], self.T0[ys, xs] = mean, Tn
                 else:
                     P = self.layers[i - 1]
@@ -359,23 +371,35 @@ class AMROracle:
                     Tw = P.T[kp][ys, xs]
                     Tn, st = orc.newton(self.m, dict(self.g0, nx=h, ny=h), mean, Tw)
                     assert st == 0, st
+                    mean[:, keep], Tn[keep] = P.U[kp][:, ys, xs][:, keep], Tw[keep]
                     P.U[kp][:, ys, xs], P.T[kp][ys, xs] = mean, Tn
 
     def step(self, dt=0.0, cfl=0.0):
-        """One base step (Algorithm 2). Returns the base dt."""
+        """One step (Algorithm 2). Crossover: a base step of dt (the CFL dt of
+        layer 0 when dt <= 0). Synchronous: every layer advances dt (the
+        CFL dt of layer 0 divided by 2^levels when dt <= 0). Returns the dt
+        advanced."""
         if self.nstep % self.regrid_every == 0:
             self.regrid()
         if dt <= 0.0:
             dt = orc.cfl_dt(self.m, self.g0, self.U0, self.T0, cfl)
-        self.advance(0, dt)
+            if self.synchronous:
+                dt /= 2 ** self.levels
+        if self.synchronous:
+            for i in range(self.levels, -1, -1):
+                if i == 0 or self.layers[i].pos:
+                    self.solve_layer(i, dt)
+        else:
+            self.advance(0, dt)
         self.fine_to_coarse()
         self.nstep += 1
         self.t += dt
         return dt
 
     def cell_updates_per_step(self):
-        """Cell updates of one base step: base cells plus 2^i x the cells of layer i."""
+        """Cell updates of one step: base cells plus the cells of layer i, times
+        2^i (crossover) or once (synchronous)."""
         n = self.g0["nx"] * self.g0["ny"]
         for i in range(1, self.levels + 1):
-            n += len(self.layers[i].pos) * self.B * self.B * 2 ** i
+            n += len(self.layers[i].pos) * self.B * self.B * (1 if self.synchronous else 2 ** i)
         return n

@@ -228,6 +228,8 @@ __global__ void __launch_bounds__(256) k_amr_alpha(StateView S, long long n, con
 }
 
 // ---- four-to-one mean onto the parent, then Newton T and aux planes ----
+// Parent cells with a child in the external band keep their own value: the
+// band holds copies of the parent, not values the fine solver computed.
 template <int NS>
 __global__ void __launch_bounds__(AH* AH) k_amr_f2c(StateView Sf, LayerDev L, ParentDev P,
                                                     const MechDev* __restrict__ mech, double newton_tol,
@@ -235,6 +237,10 @@ __global__ void __launch_bounds__(AH* AH) k_amr_f2c(StateView Sf, LayerDev L, Pa
   constexpr int NV = NS + 3;
   const int blk = blockIdx.x;
   const int a = threadIdx.x % AH, b = threadIdx.x / AH;
+  const int* nb = L.nbr + 4 * blk;
+  if (in_band(nb, 2 * a, 2 * b) || in_band(nb, 2 * a + 1, 2 * b) || in_band(nb, 2 * a, 2 * b + 1) ||
+      in_band(nb, 2 * a + 1, 2 * b + 1))
+    return;
   const int pk = L.pos[blk];
   const long long pi = parent_index(P, (pk & 0xffff) * AH + a, (pk >> 16) * AH + b);
   const long long f00 = (long long)blk * AB2 + (2 * b) * AB + 2 * a;
@@ -768,7 +774,17 @@ int janc_amr_step(janc_amr_t A, int n_steps, double dt, double cfl, double* t_ou
       const double hmin = A->d.dx < A->d.dy ? A->d.dx : A->d.dy;
       h = cfl * hmin / (ax > ay ? ax : ay);
     }
-    int rc = advance(A, 0, h);
+    int rc = JANC_OK;
+    if (A->a.synchronous) {  // Fig. 2b: every layer takes this dt, deepest first
+      if (!(dt > 0.0)) h = std::ldexp(h, -A->a.levels);
+      for (int i = A->a.levels; i >= 1 && rc == JANC_OK; --i) {
+        cudaError_t e = solve_layer(A, i, h);
+        if (e != cudaSuccess) rc = afail_cuda(e, "AMR layer solve");
+      }
+      if (rc == JANC_OK) rc = janc_step(A->g0, 1, h, 0.0, nullptr, nullptr);
+    } else {
+      rc = advance(A, 0, h);
+    }
     if (rc != JANC_OK) return rc;
     cudaError_t e = cudaSuccess;
     for (int i = A->a.levels; i >= 1 && e == cudaSuccess; --i)
@@ -778,7 +794,7 @@ int janc_amr_step(janc_amr_t A, int n_steps, double dt, double cfl, double* t_ou
     if (e == cudaSuccess) e = launch_alpha(A->ns, gp.S0, gp.gd.n, gp.mech, gp.alpha, A->d_status, st);
     if (e != cudaSuccess) return afail_cuda(e, "AMR fine-to-coarse");
     long long up = (long long)A->d.nx * A->d.ny;
-    for (int i = 1; i <= A->a.levels; ++i) up += ((long long)A->L[i].nblk * AB2) << i;
+    for (int i = 1; i <= A->a.levels; ++i) up += ((long long)A->L[i].nblk * AB2) << (A->a.synchronous ? 0 : i);
     A->updates_last = up;
     A->nstep += 1;
     A->t += h;

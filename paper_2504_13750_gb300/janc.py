@@ -458,7 +458,7 @@ class Grid:
 
 class AmrDesc(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("block", ctypes.c_int), ("threshold", ctypes.c_double),
-                ("n_buffer", ctypes.c_int), ("regrid_every", ctypes.c_int)]
+                ("n_buffer", ctypes.c_int), ("regrid_every", ctypes.c_int), ("synchronous", ctypes.c_int)]
 
 
 def janc_amr_create(desc, mech: Mechanism, amr: AmrDesc, stream=None):
@@ -522,7 +522,7 @@ class Amr:
     """Owner of one AMR hierarchy (janc_amr_*) on the current CUDA stream."""
 
     def __init__(self, mech: dict, grid: dict, chemistry=True, levels=2, threshold=1e6, n_buffer=2,
-                 regrid_every=10, stream=None):
+                 regrid_every=10, stream=None, synchronous=False):
         import torch
 
         self.mech = Mechanism(mech)
@@ -532,7 +532,7 @@ class Amr:
         self.desc = make_desc(grid["nx"], grid["ny"], grid["dx"], grid["dy"], grid["bc"], chemistry=chemistry,
                               weno_eps=grid.get("weno_eps", 1e-6), newton_tol=grid.get("newton_tol", 1e-12),
                               newton_maxit=grid.get("newton_maxit", 50))
-        self.amr = AmrDesc(int(levels), 16, float(threshold), int(n_buffer), int(regrid_every))
+        self.amr = AmrDesc(int(levels), 16, float(threshold), int(n_buffer), int(regrid_every), int(bool(synchronous)))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = janc_amr_create(self.desc, self.mech, self.amr, self.stream.cuda_stream)
 

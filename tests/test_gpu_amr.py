@@ -47,13 +47,14 @@ def _margin_ok(o: AMROracle):
     return True
 
 
-def _compare(J, mech, st, chem, levels, thr, nbuf, every, nsteps, cfl=0.5, dt=0.0, tol_step=1e-10):
+def _compare(J, mech, st, chem, levels, thr, nbuf, every, nsteps, cfl=0.5, dt=0.0, tol_step=1e-10, sync=False):
     if dt > 0.0:
         cfl = 0.0
     U = orc.prim_to_cons(mech, st["T"], st["p"], st["u"], st["v"], st["Y"])
     o = AMROracle(mech, st["grid"], U, st["T"], levels=levels, threshold=thr, n_buffer=nbuf, regrid_every=every,
-                  chem=chem)
-    a = J.Amr(mech, st["grid"], chemistry=chem, levels=levels, threshold=thr, n_buffer=nbuf, regrid_every=every)
+                  chem=chem, synchronous=sync)
+    a = J.Amr(mech, st["grid"], chemistry=chem, levels=levels, threshold=thr, n_buffer=nbuf, regrid_every=every,
+              synchronous=sync)
     a.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
     for n in range(nsteps):
         if n % every == 0:
@@ -76,10 +77,12 @@ def _compare(J, mech, st, chem, levels, thr, nbuf, every, nsteps, cfl=0.5, dt=0.
     return a, o
 
 
-def test_amr_reacting_tube_with_walls(J):
+@pytest.mark.parametrize("sync", [False, True])
+def test_amr_reacting_tube_with_walls(J, sync):
+    """Crossover (Fig. 2a) and synchronous (Fig. 2b) advance."""
     st = inputs.tube(H2AIR, 64, 16, Lx=0.05 * 64 / 256, perturb_seed=3)
     dx = st["grid"]["dx"]
-    a, o = _compare(J, H2AIR, st, True, levels=2, thr=100.0 / dx, nbuf=2, every=2, nsteps=5)
+    a, o = _compare(J, H2AIR, st, True, levels=2, thr=100.0 / dx, nbuf=2, every=2, nsteps=5, sync=sync)
     assert o.layers[1].pos and o.layers[2].pos
     a.close()
 

@@ -42,6 +42,70 @@ def test_crossover_order_of_algorithm_2():
     assert a.trace == [(2, dt / 4), (2, dt / 4), (1, dt / 2), (2, dt / 4), (2, dt / 4), (1, dt / 2), (0, dt)]
 
 
+def test_synchronous_order_of_algorithm_2():
+    """Fig. 2b: every layer takes the same dt, deepest first, once per step."""
+    st, U = _tube(32, 16)
+    force = {1: {(0, 0), (1, 0)}, 2: {(0, 0), (1, 1)}}
+    a = AMROracle(H2AIR, st["grid"], U, st["T"], levels=2, force_blocks=force, chem=False, synchronous=True)
+    dt = 1e-8
+    a.step(dt=dt)
+    assert a.trace == [(2, dt), (1, dt), (0, dt)]
+    assert a.cell_updates_per_step() == 32 * 16 + (2 + 2) * 256
+
+
+def test_synchronous_and_crossover_agree_to_high_order():
+    """Both strategies integrate the same equations with third-order RK3
+    steps. On a smooth acoustic wave without chemistry, after the same
+    simulated time, their base layers differ by far less than the change over
+    that time. (With split chemistry the base layer's own dt enters the
+    first-order splitting error, so the two differ at O(dt) there.)"""
+    st, U = _tube(32, 16)
+    x = np.arange(32) / 32
+    st["T"] = 1150.0 + 50.0 * np.sin(2 * np.pi * x)[None, :] * np.ones((16, 1))
+    st["p"] = inputs.ATM * (1 + 0.05 * np.cos(2 * np.pi * x))[None, :] * np.ones((16, 1))
+    U = orc.prim_to_cons(H2AIR, st["T"], st["p"], st["u"], st["v"], st["Y"])
+    force = {1: {(2, 0), (3, 0), (2, 1), (3, 1)}}
+    dt = 2e-8
+    c = AMROracle(H2AIR, st["grid"], U, st["T"], levels=1, force_blocks=force, regrid_every=100, chem=False)
+    y = AMROracle(H2AIR, st["grid"], U, st["T"], levels=1, force_blocks=force, regrid_every=100, chem=False,
+                  synchronous=True)
+    for _ in range(4):
+        c.step(dt=dt)
+    for _ in range(8):
+        y.step(dt=dt / 2)
+    moved = 0
+    for k in range(4):
+        change = np.max(np.abs(c.U0[k] - U[k]))
+        if change > 0:
+            moved += 1
+            assert np.max(np.abs(c.U0[k] - y.U0[k])) < 0.02 * change, k
+    assert moved == 3
+
+
+def test_fine_to_coarse_skips_the_external_band():
+    """The four-to-one mean writes the parent cells whose four children the
+    fine solver computed; parent cells with a child in the external band
+    (a copy of the parent) keep their own value, so that region evolves on
+    the parent layer instead of freezing."""
+    st, U = _tube(32, 16)
+    force = {1: {(2, 0)}}                      # one block: every side external or physical
+    a = AMROracle(H2AIR, st["grid"], U, st["T"], levels=1, force_blocks=force, chem=False)
+    a.regrid()
+    L = a.layers[1]
+    rng = np.random.default_rng(3)
+    L.U = L.U * (1 + 1e-3 * rng.standard_normal(L.U.shape))
+    U_before = a.U0.copy()
+    a.fine_to_coarse()
+    band = a.external_band(L, 0)
+    keep = band[0::2, 0::2] | band[0::2, 1::2] | band[1::2, 0::2] | band[1::2, 1::2]
+    f = L.U[0]
+    mean = 0.25 * ((f[:, 0::2, 0::2] + f[:, 0::2, 1::2]) + (f[:, 1::2, 0::2] + f[:, 1::2, 1::2]))
+    region = a.U0[:, 0:8, 16:24]
+    assert keep.any() and not keep.all()
+    assert np.array_equal(region[:, keep], U_before[:, 0:8, 16:24][:, keep])
+    assert np.array_equal(region[:, ~keep], mean[:, ~keep])
+
+
 def test_refine_then_coarsen_returns_the_parent():
     st, U = _tube(32, 16)
     force = {1: {(1, 0), (2, 1), (3, 1)}, 2: {(2, 1), (5, 2)}}
