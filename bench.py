@@ -124,9 +124,11 @@ def weno_flops():
 
 
 # ----------------------------------------------------------------------------
-def cpu_baseline_oracle(mech, st, steps=2):
+def cpu_baseline_oracle(mech, st, steps=5):
     """The oracle as it stands on the host cores: `steps` full steps of the
-    4096 x 512 tube. Returns (cell-steps/s, cores, sample text)."""
+    4096 x 512 tube (about 10 s on 16 cores), plus one step of a 4096 x 32
+    slab on one thread. Returns (cell-steps/s, cores, sample text, single-
+    thread cell-steps/s)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as orc
 
@@ -136,7 +138,15 @@ def cpu_baseline_oracle(mech, st, steps=2):
     t0 = time.perf_counter()
     orc.step(mech, st["grid"], U, st["T"], steps, cfl=CFL)
     dt = time.perf_counter() - t0
-    return NX * NY * steps / dt, cores, f"{steps} full steps of the {NX}x{NY} tube ({dt:.1f} s)"
+    rows = 32
+    g1 = dict(st["grid"], ny=rows)
+    orc.set_threads(1)
+    t1 = time.perf_counter()
+    orc.step(mech, g1, np.ascontiguousarray(U[:, :rows]), np.ascontiguousarray(st["T"][:rows]), 1, cfl=CFL)
+    d1 = time.perf_counter() - t1
+    orc.set_threads(0)
+    return (NX * NY * steps / dt, cores, f"{steps} full steps of the {NX}x{NY} tube ({dt:.1f} s)",
+            NX * rows / d1)
 
 
 def run_reference(args):
@@ -419,8 +429,9 @@ def run_ours(args):
     # CPU baseline first (rank 0, N = 1 only), before the GPU is busy
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_baseline_oracle(mech, st)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        v, cores, sample, v1 = cpu_baseline_oracle(mech, st)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": v1, "unit": UNIT, "sample": f"1 step of a {NX}x32 slab on 1 thread"}}
 
     stream = torch.cuda.Stream()
     g = janc.Grid(mech, NX, NY, st["grid"]["dx"], st["grid"]["dy"], st["grid"]["bc"], chemistry=True,
