@@ -79,3 +79,37 @@ def test_oracle_and_product_share_no_code():
         if f.endswith((".py", ".cpp", ".hpp")):
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "csrc" not in text and "janc_device" not in text and "import janc" not in text, f
+
+
+def test_new_entry_points_validate_without_gpu(libjanc):
+    """Argument checks of the AMR, server-budget, source-step and chemistry
+    modes return before any CUDA call."""
+    from paper_2504_13750_gb300 import janc
+
+    mech = janc.Mechanism(inputs.load_mechanism("h2air_synth"))
+    d = janc.make_desc(64, 16, 1e-4, 1e-4, [0, 0, 0, 0])
+    amr = janc.AmrDesc(2, 16, 1e6, 2, 10, 0)
+    for bad, rc in ((janc.AmrDesc(2, 32, 1e6, 2, 10, 0), -2),     # block must be 16
+                    (janc.AmrDesc(9, 16, 1e6, 2, 10, 0), -1),     # levels 0..6
+                    (janc.AmrDesc(2, 16, 1e6, -1, 10, 0), -1),    # buffer >= 0
+                    (janc.AmrDesc(2, 16, 1e6, 2, 0, 0), -1)):     # regrid period >= 1
+        with pytest.raises(janc.JancError) as e:
+            janc.janc_amr_create(d, mech, bad)
+        assert e.value.rc == rc
+    odd = janc.make_desc(60, 16, 1e-4, 1e-4, [0, 0, 0, 0])         # not a multiple of 8
+    with pytest.raises(janc.JancError) as e:
+        janc.janc_amr_create(odd, mech, amr)
+    assert e.value.rc == -1
+    for mode in (janc.CHEM_STRANG, janc.CHEM_EXPLICIT):           # AMR runs the Lie order
+        with pytest.raises(janc.JancError) as e:
+            janc.janc_amr_create(janc.make_desc(64, 16, 1e-4, 1e-4, [0, 0, 0, 0], chemistry=mode), mech, amr)
+        assert e.value.rc == -2
+    with pytest.raises(janc.JancError) as e:                         # chemistry mode out of range
+        janc.janc_workspace_bytes(janc.make_desc(64, 16, 1e-4, 1e-4, [0, 0, 0, 0], chemistry=7), mech)
+    assert e.value.rc == -1
+    assert janc.janc_workspace_bytes(janc.make_desc(64, 16, 1e-4, 1e-4, [0, 0, 0, 0], chemistry=janc.CHEM_EXPLICIT),
+                                     mech) > 0
+    with pytest.raises(janc.JancError):                              # null server
+        janc.janc_server_set_cell_budget(None, 1000)
+    with pytest.raises(janc.JancError):                              # null grid
+        janc.janc_source_step(None, 1, 1e-8)
