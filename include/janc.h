@@ -234,6 +234,23 @@ int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, siz
 int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int loss_kind, const double* seed,
                       double* dL_dU0, double* loss_out, void* workspace, size_t workspace_bytes, int where);
 
+/* The two halves of janc_step_adjoint, for losses that need U^N first (the
+ * cotangent dL/dU^N of a nonlinear loss, e.g. an autograd graph on U^N).
+ * janc_adjoint_forward runs n_steps fixed-dt steps from the grid's state with
+ * checkpoints in `workspace` (janc_adjoint_workspace_bytes; null: an internal
+ * allocation) and leaves U^N in the grid. With JANC_LOSS_ENDWALL_P it returns
+ * that loss in *loss_out (may be null); with JANC_LOSS_SEEDED nothing is
+ * accumulated. A later forward on the same grid replaces the pending one. */
+int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, int loss_kind, double* loss_out,
+                         void* workspace, size_t workspace_bytes);
+/* janc_adjoint_reverse: dL/dU^0 of the pending forward, for the cotangent
+ * seed = dL/dU^N ([nv][ny][nx]; null: zero) plus the end-wall loss's own
+ * cotangents when the forward used JANC_LOSS_ENDWALL_P. The workspace must be
+ * the forward's and untouched; the grid's own state may have changed since.
+ * Synchronous; ends the pending forward (and frees an internal workspace).
+ * JANC_E_INVALID without a pending forward. */
+int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int where);
+
 /* Vector-Jacobian product of the right-hand side L(U) (Eq. 4.10-4.11 with
  * WENO5, the ghost layers and the global LF speeds) at the grid's current
  * state: nu = (dL/dU)^T mu, both [nv][ny][nx], host or device. workspace:

@@ -1,4 +1,11 @@
-"""torch.autograd.Function around the discrete adjoint of the C ABI.
+"""torch.autograd.Function wrappers around the discrete adjoint of the C ABI.
+
+``rollout(grid, U0, n_steps, dt, ckpt_every)`` maps the initial conserved
+state U^0 (a device tensor [nv, ny, nx]) to U^N after n fixed-dt steps. Its
+forward runs janc_adjoint_forward (checkpoints kept on the device); its
+backward receives dL/dU^N from whatever loss follows and runs
+janc_adjoint_reverse, so any torch expression of U^N is differentiable with
+respect to U^0. One rollout may be pending per grid at a time.
 
 ``trajectory_loss(grid, T0, p, u, v, Y, n_steps, dt, ckpt_every)`` loads the
 initial state from primitive fields (device tensors) with the temperature
@@ -42,3 +49,26 @@ class JancTrajectory(torch.autograd.Function):
 
 def trajectory_loss(grid, T0, p, u, v, Y, n_steps, dt, ckpt_every=50):
     return JancTrajectory.apply(T0, grid, p, u, v, Y, n_steps, dt, ckpt_every)
+
+
+class JancRollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U0, grid, n_steps, dt, ckpt_every):
+        if not (U0.is_cuda and U0.dtype == torch.float64 and U0.is_contiguous()):
+            raise ValueError("U0 must be a contiguous float64 CUDA tensor")
+        janc.janc_set_state(grid.handle, U0.detach())
+        janc.janc_adjoint_forward(grid.handle, n_steps, dt, ckpt_every, janc.LOSS_SEEDED)
+        UN = torch.empty_like(U0)
+        janc.janc_get_state(grid.handle, UN, None)
+        ctx.grid = grid
+        return UN
+
+    @staticmethod
+    def backward(ctx, gUN):
+        gU0 = torch.empty_like(gUN)
+        janc.janc_adjoint_reverse(ctx.grid.handle, gUN.contiguous(), gU0)
+        return gU0, None, None, None, None
+
+
+def rollout(grid, U0, n_steps, dt, ckpt_every=50):
+    return JancRollout.apply(U0, grid, n_steps, dt, ckpt_every)

@@ -177,6 +177,14 @@ struct janc_grid_s {
   int* status;
   MechDev* mech;
   int steps_done;
+  // trajectory of the last janc_adjoint_forward, for janc_adjoint_reverse
+  struct AdjPending {
+    bool valid = false;
+    int n_steps = 0, ckpt_every = 1, loss_kind = 0;
+    double dt = 0.0;
+    char* ws = nullptr;
+    bool own = false;
+  } adj;
   // per-kernel event timing (janc_profile)
   bool prof_on = false;
   struct Mark { cudaEvent_t a, b; int cls; };
@@ -316,6 +324,7 @@ void janc_destroy_grid(janc_grid_t g) {
   for (auto& m : g->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : g->pool) cudaEventDestroy(e);
   if (g->owns_ws) cudaFree(g->ws);
+  if (g->adj.own && g->adj.ws) cudaFree(g->adj.ws);  // a forward never reversed
   delete g;
 }
 
@@ -657,54 +666,76 @@ int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, s
   return rc;
 }
 
-int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int loss_kind, const double* seed,
-                      double* dL_dU0, double* loss_out, void* workspace, size_t workspace_bytes, int where) {
-  if (!g || n_steps < 0 || !(dt > 0.0) || ckpt_every <= 0) return fail(JANC_E_INVALID, "bad argument");
-  if (loss_kind != JANC_LOSS_ENDWALL_P && loss_kind != JANC_LOSS_SEEDED) return fail(JANC_E_INVALID, "loss kind");
-  if (loss_kind == JANC_LOSS_SEEDED && !seed) return fail(JANC_E_INVALID, "seeded loss needs a seed");
-  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
-  if (g->d.chemistry == JANC_CHEM_STRANG) return fail(JANC_E_UNSUPPORTED, "the adjoint reverses the Lie order only");
-  const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
-  char* ws = (char*)workspace;
-  bool own = false;
-  if (!ws) {
-    if (cudaMalloc(&ws, L.total) != cudaSuccess) return fail(JANC_E_NOMEM, "janc_step_adjoint: cudaMalloc failed");
-    own = true;
-  } else if (workspace_bytes < L.total || ((uintptr_t)ws & 255u)) {
-    return fail(JANC_E_NOMEM, "janc_step_adjoint: workspace too small or misaligned");
-  }
-  cudaStream_t st = g->stream;
-  const size_t n = (size_t)g->n;
-  const int nv = g->nv;
-  const size_t nvn = (size_t)nv * n;
-  const size_t lamb = align256(sizeof(double) * nvn);
-  char* p = ws;
-  char* ckpt = p; p += L.ckpt;
-  char* seg = p; p += L.seg;
-  unsigned long long* alog = (unsigned long long*)p; p += L.alog;
+}  // extern "C"
+
+namespace {
+
+// Pointers into an adjoint workspace (see adj_layout).
+struct AdjPtrs {
+  char* ckpt;
+  char* seg;
+  unsigned long long* alog;
   double* lam[7];
-  for (int k = 0; k < 7; ++k) { lam[k] = (double*)p; p += lamb; }
-  double* cfx = (double*)p; p += L.cfx;
-  double* cfy = (double*)p; p += L.cfy;
-  double* small = (double*)p;  // [0] loss, [8..15] vjp scratch
-  auto ckpt_state = [&](int c) { return StateView{(double*)(ckpt + (size_t)c * (L.state + 256))}; };
-  auto ckpt_alpha = [&](int c) { return (unsigned long long*)(ckpt + (size_t)c * (L.state + 256) + L.state); };
-  auto segS0 = [&](int m) { return StateView{(double*)(seg + (size_t)m * L.state)}; };
-  auto segS = [&](int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
-    return StateView{(double*)(seg + (size_t)(ckpt_every + 1 + 3 * m + which - 1) * L.state)};
-  };
-  const bool chem = g->d.chemistry == JANC_CHEM_LIE;
-  const bool src = g->d.chemistry == JANC_CHEM_EXPLICIT;
-  const double w_loss = dt / g->gd.ny;
+  double* cfx;
+  double* cfy;
+  double* small;  // [0] loss, [8..15] vjp scratch
+};
+
+AdjPtrs adj_ptrs(const janc_grid_s* g, const AdjLayout& L, char* ws) {
+  AdjPtrs q;
+  const size_t lamb = align256(sizeof(double) * (size_t)g->nv * (size_t)g->n);
+  char* p = ws;
+  q.ckpt = p; p += L.ckpt;
+  q.seg = p; p += L.seg;
+  q.alog = (unsigned long long*)p; p += L.alog;
+  for (int k = 0; k < 7; ++k) { q.lam[k] = (double*)p; p += lamb; }
+  q.cfx = (double*)p; p += L.cfx;
+  q.cfy = (double*)p; p += L.cfy;
+  q.small = (double*)p;
+  return q;
+}
+
+StepCtl adj_ctl(const janc_grid_s* g, double dt) {
   StepCtl ctl;
   ctl.dt_fixed = dt;
   ctl.cfl = 0.0;
   ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
   ctl.chem_frac = 1.0;
-  ctl.source = src ? 1 : 0;
+  ctl.source = g->d.chemistry == JANC_CHEM_EXPLICIT ? 1 : 0;
+  return ctl;
+}
+
+void adj_release(janc_grid_s* g) {
+  if (g->adj.own && g->adj.ws) cudaFree(g->adj.ws);
+  g->adj = janc_grid_s::AdjPending();
+}
+
+}  // namespace
+
+extern "C" {
+
+int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, int loss_kind, double* loss_out,
+                         void* workspace, size_t workspace_bytes) {
+  if (!g || n_steps < 0 || !(dt > 0.0) || ckpt_every <= 0) return fail(JANC_E_INVALID, "bad argument");
+  if (loss_kind != JANC_LOSS_ENDWALL_P && loss_kind != JANC_LOSS_SEEDED) return fail(JANC_E_INVALID, "loss kind");
+  if (g->d.chemistry == JANC_CHEM_STRANG) return fail(JANC_E_UNSUPPORTED, "the adjoint reverses the Lie order only");
+  adj_release(g);
+  const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
+  char* ws = (char*)workspace;
+  bool own = false;
+  if (!ws) {
+    if (cudaMalloc(&ws, L.total) != cudaSuccess) return fail(JANC_E_NOMEM, "janc_adjoint_forward: cudaMalloc failed");
+    own = true;
+  } else if (workspace_bytes < L.total || ((uintptr_t)ws & 255u)) {
+    return fail(JANC_E_NOMEM, "janc_adjoint_forward: workspace too small or misaligned");
+  }
+  cudaStream_t st = g->stream;
+  const AdjPtrs q = adj_ptrs(g, L, ws);
+  auto ckpt_state = [&](int c) { return StateView{(double*)(q.ckpt + (size_t)c * (L.state + 256))}; };
+  auto ckpt_alpha = [&](int c) { return (unsigned long long*)(q.ckpt + (size_t)c * (L.state + 256) + L.state); };
+  const double w_loss = dt / g->gd.ny;
   int rc = JANC_OK;
-  cudaError_t e = cudaMemsetAsync(small, 0, 256, st);
-  // ---- forward with checkpoints and the loss ----
+  cudaError_t e = cudaMemsetAsync(q.small, 0, 256, st);
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
     if (s % ckpt_every == 0) {
       const int c = s / ckpt_every;
@@ -715,96 +746,164 @@ int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int
     if (e != cudaSuccess) break;
     rc = janc_step(g, 1, dt, 0.0, nullptr, nullptr);
     if (rc) break;
-    if (loss_kind == JANC_LOSS_ENDWALL_P) e = launch_loss_endwall(g->ns, sv(g, 0), g->gd, w_loss, small, st);
+    if (loss_kind == JANC_LOSS_ENDWALL_P) e = launch_loss_endwall(g->ns, sv(g, 0), g->gd, w_loss, q.small, st);
   }
-  if (!rc && e == cudaSuccess && loss_kind == JANC_LOSS_SEEDED) {
-    double* dseed = lam[6];
-    e = cudaMemcpyAsync(dseed, seed, sizeof(double) * nvn,
-                        where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = launch_dot((long long)nvn, dseed, g->S[0], small, st);
-  }
-  // ---- reverse sweep over segments, recomputing each from its checkpoint ----
-  if (!rc && e == cudaSuccess && dL_dU0) {
-    double* lamN = lam[0];  // cotangent of U^{m+1}
-    double* lamS = lam[1];  // of U*
-    double* lam2 = lam[2];
-    double* lam1 = lam[3];
-    double* lam0 = lam[4];
-    double* mu = lam[5];
-    double* nu = lam[6];
-    if (loss_kind == JANC_LOSS_SEEDED) e = cudaMemcpyAsync(lamN, lam[6], sizeof(double) * nvn, cudaMemcpyDeviceToDevice, st);
-    else e = cudaMemsetAsync(lamN, 0, sizeof(double) * nvn, st);
-    for (int c = L.ncp - 1; c >= 0 && e == cudaSuccess && n_steps > 0; --c) {
-      const int m0 = c * ckpt_every;
-      const int len = (n_steps - m0) < ckpt_every ? (n_steps - m0) : ckpt_every;
-      // recompute the segment, keeping every stage state and its alpha
-      e = cudaMemcpyAsync(segS0(0).base, ckpt_state(c).base, L.state, cudaMemcpyDeviceToDevice, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(alog, 0, L.alog, st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(alog, ckpt_alpha(c), 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
-      for (int m = 0; m < len && e == cudaSuccess; ++m) {
-        unsigned long long* a = alog + 10 * m;
-        if (m > 0) e = cudaMemcpyAsync(a, alog + 10 * (m - 1) + 8, 16, cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) e = launch_face_flux(nv, segS0(m), a, g->Fx, g->Gy, g->gd, st);
-        if (e == cudaSuccess)
-          e = launch_rk_update(g->ns, 1, segS0(m), segS0(m), segS(m, 1), g->Fx, g->Gy, g->gd, g->mech, ctl, a, a + 2,
-                               g->status, nullptr, st);
-        if (e == cudaSuccess) e = launch_face_flux(nv, segS(m, 1), a + 2, g->Fx, g->Gy, g->gd, st);
-        if (e == cudaSuccess)
-          e = launch_rk_update(g->ns, 2, segS(m, 1), segS0(m), segS(m, 2), g->Fx, g->Gy, g->gd, g->mech, ctl, a,
-                               a + 4, g->status, nullptr, st);
-        if (e == cudaSuccess) e = launch_face_flux(nv, segS(m, 2), a + 4, g->Fx, g->Gy, g->gd, st);
-        if (e == cudaSuccess)
-          e = launch_rk_update(g->ns, 3, segS(m, 2), segS0(m), segS(m, 3), g->Fx, g->Gy, g->gd, g->mech, ctl, a,
-                               chem ? a + 6 : a + 8, g->status, nullptr, st);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(segS0(m + 1).base, segS(m, 3).base, L.state, cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess && chem)
-          e = launch_chem(g->ns, segS0(m + 1), g->gd, g->mech, ctl, a, a + 8, g->status, st);
-      }
-      // reverse through the segment
-      for (int m = len - 1; m >= 0 && e == cudaSuccess; --m) {
-        const unsigned long long* a = alog + 10 * m;
-        if (loss_kind == JANC_LOSS_ENDWALL_P)
-          e = launch_seed_endwall(g->ns, segS0(m + 1), g->gd, g->mech, w_loss, lamN, st);
-        if (e == cudaSuccess) {
-          if (chem) e = launch_chem_vjp(g->ns, segS(m, 3), g->gd, g->mech, dt, lamN, lamS, st);
-          else e = cudaMemcpyAsync(lamS, lamN, sizeof(double) * nvn, cudaMemcpyDeviceToDevice, st);
-        }
-        // stage 3: U* = U^n/3 + 2/3 (U2 + dt L(U2))
-        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 2.0 / 3.0 * dt, lamS, 0.0, nullptr, false, st);
-        if (e == cudaSuccess)
-          e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
-                             st);
-        if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, mu, nu, st);
-        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam2, 2.0 / 3.0, lamS, 1.0, nu, false, st);
-        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0 / 3.0, lamS, 0.0, nullptr, false, st);
-        // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
-        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 0.25 * dt, lam2, 0.0, nullptr, false, st);
-        if (e == cudaSuccess)
-          e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
-                             st);
-        if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, mu, nu, st);
-        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam1, 0.25, lam2, 1.0, nu, false, st);
-        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 0.75, lam2, 0.0, nullptr, true, st);
-        // stage 1: U1 = U^n + dt L(U^n)
-        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, dt, lam1, 0.0, nullptr, false, st);
-        if (e == cudaSuccess)
-          e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 8, g->gd, g->mech, st);
-        if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, mu, nu, st);
-        if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0, lam1, 1.0, nu, true, st);
-        std::swap(lamN, lam0);
-      }
-    }
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(dL_dU0, lamN, sizeof(double) * nvn,
-                          where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
-  }
-  if (!rc && e == cudaSuccess && loss_out) e = cudaMemcpyAsync(loss_out, small, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (!rc && e == cudaSuccess && loss_out) e = cudaMemcpyAsync(loss_out, q.small, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (!rc && e != cudaSuccess) rc = fail_cuda(e, "janc_step_adjoint");
-  if (own) cudaFree(ws);
-  return rc;
+  if (!rc && e != cudaSuccess) rc = fail_cuda(e, "janc_adjoint_forward");
+  if (rc) {
+    if (own) cudaFree(ws);
+    return rc;
+  }
+  g->adj.valid = true;
+  g->adj.n_steps = n_steps;
+  g->adj.ckpt_every = ckpt_every;
+  g->adj.loss_kind = loss_kind;
+  g->adj.dt = dt;
+  g->adj.ws = ws;
+  g->adj.own = own;
+  return JANC_OK;
+}
+
+int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int where) {
+  if (!g || !dL_dU0) return fail(JANC_E_INVALID, "null argument");
+  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
+  if (!g->adj.valid) return fail(JANC_E_INVALID, "janc_adjoint_reverse: no pending janc_adjoint_forward");
+  const int n_steps = g->adj.n_steps, ckpt_every = g->adj.ckpt_every, loss_kind = g->adj.loss_kind;
+  const double dt = g->adj.dt;
+  const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
+  const AdjPtrs q = adj_ptrs(g, L, g->adj.ws);
+  cudaStream_t st = g->stream;
+  const size_t n = (size_t)g->n;
+  const int nv = g->nv;
+  const size_t nvn = (size_t)nv * n;
+  auto ckpt_state = [&](int c) { return StateView{(double*)(q.ckpt + (size_t)c * (L.state + 256))}; };
+  auto ckpt_alpha = [&](int c) { return (unsigned long long*)(q.ckpt + (size_t)c * (L.state + 256) + L.state); };
+  auto segS0 = [&](int m) { return StateView{(double*)(q.seg + (size_t)m * L.state)}; };
+  auto segS = [&](int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
+    return StateView{(double*)(q.seg + (size_t)(ckpt_every + 1 + 3 * m + which - 1) * L.state)};
+  };
+  const bool chem = g->d.chemistry == JANC_CHEM_LIE;
+  const bool src = g->d.chemistry == JANC_CHEM_EXPLICIT;
+  const double w_loss = dt / g->gd.ny;
+  const StepCtl ctl = adj_ctl(g, dt);
+  unsigned long long* alog = q.alog;
+  double* cfx = q.cfx;
+  double* cfy = q.cfy;
+  double* small = q.small;
+  double* lamN = q.lam[0];  // cotangent of U^{m+1}
+  double* lamS = q.lam[1];  // of U*
+  double* lam2 = q.lam[2];
+  double* lam1 = q.lam[3];
+  double* lam0 = q.lam[4];
+  double* mu = q.lam[5];
+  double* nu = q.lam[6];
+  cudaError_t e = cudaSuccess;
+  if (seed) e = cudaMemcpyAsync(lamN, seed, sizeof(double) * nvn,
+                                where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+  else e = cudaMemsetAsync(lamN, 0, sizeof(double) * nvn, st);
+  for (int c = L.ncp - 1; c >= 0 && e == cudaSuccess && n_steps > 0; --c) {
+    const int m0 = c * ckpt_every;
+    const int len = (n_steps - m0) < ckpt_every ? (n_steps - m0) : ckpt_every;
+    // recompute the segment, keeping every stage state and its alpha
+    e = cudaMemcpyAsync(segS0(0).base, ckpt_state(c).base, L.state, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(alog, 0, L.alog, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(alog, ckpt_alpha(c), 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+    for (int m = 0; m < len && e == cudaSuccess; ++m) {
+      unsigned long long* a = alog + 10 * m;
+      if (m > 0) e = cudaMemcpyAsync(a, alog + 10 * (m - 1) + 8, 16, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = launch_face_flux(nv, segS0(m), a, g->Fx, g->Gy, g->gd, st);
+      if (e == cudaSuccess)
+        e = launch_rk_update(g->ns, 1, segS0(m), segS0(m), segS(m, 1), g->Fx, g->Gy, g->gd, g->mech, ctl, a, a + 2,
+                             g->status, nullptr, st);
+      if (e == cudaSuccess) e = launch_face_flux(nv, segS(m, 1), a + 2, g->Fx, g->Gy, g->gd, st);
+      if (e == cudaSuccess)
+        e = launch_rk_update(g->ns, 2, segS(m, 1), segS0(m), segS(m, 2), g->Fx, g->Gy, g->gd, g->mech, ctl, a,
+                             a + 4, g->status, nullptr, st);
+      if (e == cudaSuccess) e = launch_face_flux(nv, segS(m, 2), a + 4, g->Fx, g->Gy, g->gd, st);
+      if (e == cudaSuccess)
+        e = launch_rk_update(g->ns, 3, segS(m, 2), segS0(m), segS(m, 3), g->Fx, g->Gy, g->gd, g->mech, ctl, a,
+                             chem ? a + 6 : a + 8, g->status, nullptr, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(segS0(m + 1).base, segS(m, 3).base, L.state, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess && chem)
+        e = launch_chem(g->ns, segS0(m + 1), g->gd, g->mech, ctl, a, a + 8, g->status, st);
+    }
+    // reverse through the segment
+    for (int m = len - 1; m >= 0 && e == cudaSuccess; --m) {
+      const unsigned long long* a = alog + 10 * m;
+      if (loss_kind == JANC_LOSS_ENDWALL_P)
+        e = launch_seed_endwall(g->ns, segS0(m + 1), g->gd, g->mech, w_loss, lamN, st);
+      if (e == cudaSuccess) {
+        if (chem) e = launch_chem_vjp(g->ns, segS(m, 3), g->gd, g->mech, dt, lamN, lamS, st);
+        else e = cudaMemcpyAsync(lamS, lamN, sizeof(double) * nvn, cudaMemcpyDeviceToDevice, st);
+      }
+      // stage 3: U* = U^n/3 + 2/3 (U2 + dt L(U2))
+      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 2.0 / 3.0 * dt, lamS, 0.0, nullptr, false, st);
+      if (e == cudaSuccess)
+        e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
+                           st);
+      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, mu, nu, st);
+      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam2, 2.0 / 3.0, lamS, 1.0, nu, false, st);
+      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0 / 3.0, lamS, 0.0, nullptr, false, st);
+      // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
+      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 0.25 * dt, lam2, 0.0, nullptr, false, st);
+      if (e == cudaSuccess)
+        e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
+                           st);
+      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, mu, nu, st);
+      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam1, 0.25, lam2, 1.0, nu, false, st);
+      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 0.75, lam2, 0.0, nullptr, true, st);
+      // stage 1: U1 = U^n + dt L(U^n)
+      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, dt, lam1, 0.0, nullptr, false, st);
+      if (e == cudaSuccess)
+        e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 8, g->gd, g->mech, st);
+      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, mu, nu, st);
+      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0, lam1, 1.0, nu, true, st);
+      std::swap(lamN, lam0);
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dL_dU0, lamN, sizeof(double) * nvn,
+                        where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  adj_release(g);
+  if (e != cudaSuccess) return fail_cuda(e, "janc_adjoint_reverse");
+  return JANC_OK;
+}
+
+int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int loss_kind, const double* seed,
+                      double* dL_dU0, double* loss_out, void* workspace, size_t workspace_bytes, int where) {
+  if (!g || n_steps < 0 || !(dt > 0.0) || ckpt_every <= 0) return fail(JANC_E_INVALID, "bad argument");
+  if (loss_kind != JANC_LOSS_ENDWALL_P && loss_kind != JANC_LOSS_SEEDED) return fail(JANC_E_INVALID, "loss kind");
+  if (loss_kind == JANC_LOSS_SEEDED && !seed) return fail(JANC_E_INVALID, "seeded loss needs a seed");
+  if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
+  double loss = 0.0;
+  int rc = janc_adjoint_forward(g, n_steps, dt, ckpt_every, loss_kind, &loss, workspace, workspace_bytes);
+  if (rc) return rc;
+  if (loss_kind == JANC_LOSS_SEEDED) {  // loss = <seed, U^N>
+    const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
+    const AdjPtrs q = adj_ptrs(g, L, g->adj.ws);
+    const size_t nvn = (size_t)g->nv * (size_t)g->n;
+    double* dseed = q.lam[6];
+    cudaError_t e = cudaMemcpyAsync(dseed, seed, sizeof(double) * nvn,
+                                    where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(q.small, 0, sizeof(double), g->stream);
+    if (e == cudaSuccess) e = launch_dot((long long)nvn, dseed, g->S[0], q.small, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&loss, q.small, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+      adj_release(g);
+      return fail_cuda(e, "janc_step_adjoint");
+    }
+  }
+  if (loss_out) *loss_out = loss;
+  if (!dL_dU0) {
+    adj_release(g);
+    return JANC_OK;
+  }
+  return janc_adjoint_reverse(g, loss_kind == JANC_LOSS_SEEDED ? seed : nullptr, dL_dU0, where);
 }
 
 int janc_primitive_T_vjp(janc_grid_t g, const double* T, const double* p, const double* u, const double* v,

@@ -12,8 +12,9 @@ snapshot the fresh-gas cells (water mass fraction below 1e-3) take the
 mixture of equivalence ratio theta at the same T, p and velocity, which gives
 U_0(theta). The loss compares U_n(theta) after n fixed-dt steps with
 U_n(1.0):  L = ||U_n(theta) - U_n(1)|| / ||U_n(1)||. Its gradient is
-<dL/dU_0, dU_0/dtheta>, dL/dU_0 from janc_step_adjoint with the seed
-dL/dU_n, dU_0/dtheta by a central difference of the (smooth) state set-up.
+<dL/dU_0, dU_0/dtheta>: dL/dU_0 from janc_adjoint_forward (which leaves U_n
+for the loss) and janc_adjoint_reverse with the cotangent dL/dU_n, dU_0/dtheta
+by a central difference of the (smooth) state set-up.
 
 Everything runs through the C ABI (janc_*); torch holds device buffers and
 runs the optimiser.
@@ -103,17 +104,20 @@ class ChannelInverse:
         return self.state()
 
     def loss_and_grad(self, theta):
+        """L(theta) and dL/dtheta: one checkpointed forward (janc_adjoint_forward),
+        the loss and its cotangent dL/dU_n from U_n, one reverse sweep
+        (janc_adjoint_reverse), then the contraction with dU_0/dtheta."""
         torch = self.torch
         self.set_theta(theta)
-        Un = self._forward()
+        janc.janc_adjoint_forward(self.g.handle, self.n_steps, self.dt, self.ckpt, janc.LOSS_SEEDED, self.wp,
+                                  self.nbytes)
+        Un = self.state()
         diff = Un - self.target
         dn = float(torch.linalg.vector_norm(diff))
         L = dn / self.tnorm
         seed = (diff / (dn * self.tnorm)).contiguous() if dn > 0 else torch.zeros_like(diff)
-        self.set_theta(theta)
         gU0 = torch.empty_like(Un)
-        janc.janc_step_adjoint(self.g.handle, self.n_steps, self.dt, self.ckpt, janc.LOSS_SEEDED, seed, gU0,
-                               self.wp, self.nbytes)
+        janc.janc_adjoint_reverse(self.g.handle, seed, gU0)
         h = 1e-4
         self.set_theta(theta + h)
         Up = self.state()

@@ -102,6 +102,8 @@ def lib():
             L.janc_server_destroy.restype = None
             L.janc_adjoint_workspace_bytes.argtypes = [p, i, i, ctypes.POINTER(ctypes.c_size_t)]
             L.janc_step_adjoint.argtypes = [p, i, d, i, i, p, p, p, p, ctypes.c_size_t, i]
+            L.janc_adjoint_forward.argtypes = [p, i, d, i, i, p, p, ctypes.c_size_t]
+            L.janc_adjoint_reverse.argtypes = [p, p, p, i]
             L.janc_rhs_vjp.argtypes = [p, p, p, p, ctypes.c_size_t, i]
             L.janc_primitive_T_vjp.argtypes = [p, p, p, p, p, p, p, p]
             L.janc_profile.argtypes = [p, i]
@@ -267,6 +269,21 @@ def janc_adjoint_workspace_bytes(g, n_steps, ckpt_every) -> int:
     out = ctypes.c_size_t()
     _check(lib().janc_adjoint_workspace_bytes(g, int(n_steps), int(ckpt_every), ctypes.byref(out)))
     return out.value
+
+
+def janc_adjoint_forward(g, n_steps, dt, ckpt_every, loss_kind=LOSS_SEEDED, workspace_ptr=None, workspace_bytes=0):
+    """Checkpointed forward of n_steps; U^N stays in the grid. Returns the
+    end-wall loss for LOSS_ENDWALL_P, else 0."""
+    loss = ctypes.c_double()
+    _check(lib().janc_adjoint_forward(g, int(n_steps), float(dt), int(ckpt_every), int(loss_kind), ctypes.byref(loss),
+                                      ctypes.c_void_p(workspace_ptr) if workspace_ptr else None, int(workspace_bytes)))
+    return loss.value
+
+
+def janc_adjoint_reverse(g, seed, dL_dU0):
+    """dL/dU^0 into dL_dU0 for the cotangent seed = dL/dU^N (None: zero)."""
+    a, b = _arg(seed), _arg(dL_dU0, True)
+    _check(lib().janc_adjoint_reverse(g, a[0], b[0], _where(a, b)))
 
 
 def janc_step_adjoint(g, n_steps, dt, ckpt_every, loss_kind=LOSS_ENDWALL_P, seed=None, dL_dU0=None,

@@ -141,6 +141,44 @@ def test_smooth_case_gradient_vs_central_differences(J):
     g.close()
 
 
+def test_rollout_autograd_and_split_adjoint(J):
+    """autograd.rollout (janc_adjoint_forward + janc_adjoint_reverse behind a
+    torch.autograd.Function): the gradient of a nonlinear torch loss of U^N
+    equals janc_step_adjoint with the seed dL/dU^N, and its projections equal
+    the oracle's trajectory tangent."""
+    import torch
+
+    from paper_2504_13750_gb300.autograd import rollout
+
+    st, U = _state(16, 8, 21, vel=40.0)
+    dt, n = 1e-8, 9
+    g = J.Grid.from_grid_dict(H2AIR, st["grid"])
+    U0 = torch.from_numpy(np.ascontiguousarray(U)).cuda().requires_grad_(True)
+    UN = rollout(g, U0, n, dt, 4)
+    w = torch.from_numpy(np.random.default_rng(22).normal(size=U.shape)).cuda()
+    scale = UN.detach().abs().amax(dim=(1, 2), keepdim=True).clamp_min(1e-12)
+    L = torch.sum(w * (UN / scale) ** 2)
+    L.backward()
+    gU0 = U0.grad.cpu().numpy()
+    # the same cotangent through janc_step_adjoint
+    seed = (2 * w * UN.detach() / scale ** 2).contiguous()
+    g2 = np.zeros_like(U)
+    g.set_state(U)
+    J.janc_step_adjoint(g.handle, n, dt, 4, J.LOSS_SEEDED, seed.cpu().numpy(), g2)
+    # (autograd forms 2 w (U/s) (1/s), the seed above 2 w U / s^2: last-bit differences)
+    assert np.max(np.abs(gU0 - g2)) <= 1e-12 * np.max(np.abs(g2))
+    V = _dirs(U, 3, 23)
+    dUN, _, _, s = orc.trajectory_tangent(H2AIR, st["grid"], U, st["T"], V, n, dt, chem=True)
+    assert s == 0
+    sd = seed.cpu().numpy()
+    for l in range(3):
+        a, b = float(np.sum(sd * dUN[l])), float(np.sum(gU0 * V[l]))
+        assert abs(a - b) <= 1e-8 * np.sum(np.abs(sd * dUN[l])), (l, a, b)
+    with pytest.raises(J.JancError):       # the reverse consumed the pending forward
+        J.janc_adjoint_reverse(g.handle, None, np.zeros_like(U))
+    g.close()
+
+
 def test_endwall_loss_value_and_gradient(J):
     st, U = _state(24, 8, 9, vel=40.0)
     dt = 2e-8
