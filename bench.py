@@ -144,7 +144,7 @@ def cpu_baseline_oracle(mech, st, steps=5):
     t1 = time.perf_counter()
     orc.step(mech, g1, np.ascontiguousarray(U[:, :rows]), np.ascontiguousarray(st["T"][:rows]), 1, cfl=CFL)
     d1 = time.perf_counter() - t1
-    orc.set_threads(0)
+    orc.set_threads(cores)
     return (NX * NY * steps / dt, cores, f"{steps} full steps of the {NX}x{NY} tube ({dt:.1f} s)",
             NX * rows / d1)
 
@@ -411,6 +411,42 @@ def whole_job_rate(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
+def run_config1(janc, stream, with_cpu=True):
+    """The 256 x 32 tube of config 1, all 200 steps at CFL 0.5: on the GPU
+    (one janc_step call, CUDA events) and, on rank 0, through the oracle on
+    the host cores (the whole run)."""
+    import torch
+    from paper_2504_13750_gb300 import inputs
+
+    mech = inputs.load_mechanism("h2air_synth")
+    st = inputs.tube(mech, 256, 32)
+    g = janc.Grid(mech, 256, 32, st["grid"]["dx"], st["grid"]["dy"], st["grid"]["bc"], chemistry=True, stream=stream)
+    Y = np.ascontiguousarray(st["Y"])
+    g.set_primitive(st["T"], st["p"], st["u"], st["v"], Y)
+    g.step(5, cfl=CFL)
+    g.set_primitive(st["T"], st["p"], st["u"], st["v"], Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(200, cfl=CFL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gpu_s = e0.elapsed_time(e1) * 1e-3
+    g.close()
+    out = {"workload": "h2air_detonation_tube_256x32_200steps_cfl0.5", "gpu_cell_steps_per_s": 256 * 32 * 200 / gpu_s}
+    if with_cpu:
+        sys.path.insert(0, os.path.join(ROOT, "oracle"))
+        import oracle as orc
+
+        cores = orc.set_threads(0)
+        U = orc.prim_to_cons(mech, st["T"], st["p"], st["u"], st["v"], st["Y"])
+        t0 = time.perf_counter()
+        orc.step(mech, st["grid"], U, st["T"], 200, cfl=CFL)
+        cpu_s = time.perf_counter() - t0
+        out.update({"cpu_cell_steps_per_s": 256 * 32 * 200 / cpu_s, "cpu_cores": cores, "cpu_s": cpu_s})
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -528,6 +564,8 @@ def run_ours(args):
     g.close()
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(janc, stream)
+    if rank == 0:
+        line["config1"] = run_config1(janc, stream, with_cpu=world == 1 and not args.no_cpu_baseline)
     if rank == 0 and not args.no_amr:
         line["amr"] = run_amr(janc, stream)
     if rank == 0 and not args.no_inverse:

@@ -62,7 +62,15 @@ def gpu_sweep(J):
 
 def test_sweep_matches_the_oracle(J, gpu_sweep):
     t, Ts, U_first = gpu_sweep
+    threads = orc.set_threads(0)   # the current count (0 only queries)
     orc.set_threads(1)
+    try:
+        _sweep_vs_oracle(t, Ts, U_first)
+    finally:
+        orc.set_threads(threads)
+
+
+def _sweep_vs_oracle(t, Ts, U_first):
     for c, T0 in enumerate(TEMPS):
         st = inputs.ignition_cell(H2AIR, T0=T0, p0=P0)
         U = orc.prim_to_cons(H2AIR, st["T"], st["p"], st["u"], st["v"], st["Y"])
