@@ -177,6 +177,34 @@ def test_explicit_source_global_mechanism(J, steps):
     g.close()
 
 
+@pytest.mark.parametrize("nx,ny", [(8, 8), (4096, 512)])
+def test_uniform_periodic_state_stays_uniform(J, nx, ny):
+    """Freestream at any size, bit for bit: a uniform reacting state moving
+    diagonally with periodic boundaries (WENO reproduces constant data
+    exactly, the LF speeds are a max over identical cells, every cell reacts
+    alike) stays uniform, and its cells equal those of an 8 x 8 grid."""
+    Y = inputs.h2air_Y(H2AIR, 1.0)
+
+    def run(nx, ny):
+        g = J.Grid(H2AIR, nx, ny, 1e-4, 1e-4, [2, 2, 2, 2], chemistry=True)
+        one = np.ones((ny, nx))
+        g.set_primitive(1250.0 * one, 2 * inputs.ATM * one, 50.0 * one, -30.0 * one,
+                        np.ascontiguousarray(Y[:, None, None] * one))
+        g.step(3, dt=2e-8)
+        U, T = g.get_state()
+        g.close()
+        return U, T
+
+    U, T = run(nx, ny)
+    assert np.all(U == U[:, :1, :1]) and np.all(T == T[0, 0])
+    Us, Ts = run(8, 8)
+    assert np.array_equal(U[:, 0, 0], Us[:, 0, 0]) and T[0, 0] == Ts[0, 0]
+    assert U[4:, 0, 0].sum() < U[0, 0, 0]           # still a mixture; chemistry has run
+    st = inputs.ignition_cell(H2AIR, T0=1250.0, p0=2 * inputs.ATM)
+    U1 = orc.prim_to_cons(H2AIR, st["T"], st["p"], st["u"], st["v"], st["Y"])
+    assert not np.allclose(U[4:, 0, 0], U1[4:, 0, 0], rtol=1e-12, atol=0)  # it reacted
+
+
 def test_sod_gpu(J):
     import ref_exact
 
