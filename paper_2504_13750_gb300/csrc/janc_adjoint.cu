@@ -165,14 +165,27 @@ __device__ __forceinline__ void gather_dir(const StateView& S, const double* __r
   }
 }
 
+// Lexicographic arg-max step: the larger speed (non-negative doubles as
+// bits), on equal speeds the lower linear index.
+__device__ __forceinline__ void argmax_merge(unsigned long long& m, int& i, unsigned long long m2, int i2) {
+  if (m2 > m || (m2 == m && i2 < i)) { m = m2; i = i2; }
+}
+
+// Cell pass of the RHS VJP (256 threads per block). Besides the gathered
+// cotangents it leaves, per block, the block sums of the alpha cotangents
+// (atomically added) and the arg-max of |u|+c and |v|+c over its cells in
+// part_mx / part_id [2 * block + direction].
 template <int NS>
 __global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, const double* __restrict__ CFx,
                             const double* __restrict__ CFy, double* __restrict__ nu, double* adj_alpha, GridDev g,
-                            const MechDev* __restrict__ mech) {
+                            const MechDev* __restrict__ mech, unsigned long long* __restrict__ part_mx,
+                            int* __restrict__ part_id) {
   constexpr int NV = NS + 3;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   double ax = 0.0, ay = 0.0;
+  unsigned long long sx = 0, sy = 0;
+  int cid = 0x7fffffff;
   if (i < g.nx && j < g.ny) {
     const long long n = g.n;
     const long long idx = (long long)j * g.nx + i;
@@ -197,56 +210,77 @@ __global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, cons
     aU[2] += a_v * rrho;
 #pragma unroll
     for (int k = 0; k < NV; ++k) nu[(long long)k * n + idx] = fma(dp[k], a_p, aU[k]);
+    // the LF speeds of this cell, as the forward's alpha max formed them
+    const double c = sound_speed<NS>(u, T, *mech);
+    const double rr = rcp(u[0]);
+    sx = dbits(dabs(u[1] * rr) + c);
+    sy = dbits(dabs(u[2] * rr) + c);
+    cid = (int)idx;
   }
-  // block sums of the alpha cotangents
+  // block sums of the alpha cotangents and block arg-max of the speeds
   __shared__ double rx[256], ry[256];
+  __shared__ unsigned long long mx[2][256];
+  __shared__ int id[2][256];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   rx[tid] = ax;
   ry[tid] = ay;
+  mx[0][tid] = sx;
+  mx[1][tid] = sy;
+  id[0][tid] = cid;
+  id[1][tid] = cid;
   __syncthreads();
   for (int s = blockDim.x * blockDim.y / 2; s > 0; s >>= 1) {
-    if (tid < s) { rx[tid] += rx[tid + s]; ry[tid] += ry[tid + s]; }
+    if (tid < s) {
+      rx[tid] += rx[tid + s];
+      ry[tid] += ry[tid + s];
+#pragma unroll
+      for (int d = 0; d < 2; ++d) argmax_merge(mx[d][tid], id[d][tid], mx[d][tid + s], id[d][tid + s]);
+    }
     __syncthreads();
   }
   if (tid == 0) {
     atomicAdd(adj_alpha, rx[0]);
     atomicAdd(adj_alpha + 1, ry[0]);
-  }
-}
-
-// Arg-max of |u|+c (d = 0) and |v|+c (d = 1) over the cells; ties go to the
-// lowest linear index. pass 0: max bits; pass 1: lowest index with the max.
-template <int NS>
-__global__ void k_speed_argmax(StateView S, GridDev g, const MechDev* __restrict__ mech, unsigned long long* mx,
-                               int* idx_out, int pass) {
-  constexpr int NV = NS + 3;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= g.n) return;
-  const long long n = g.n;
-  double u[NV];
+    const int b = blockIdx.x + gridDim.x * blockIdx.y;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) u[k] = S.plane(k, n)[q];
-  const double c = sound_speed<NS>(u, S.plane(NV, n)[q], *mech);
-  const double rr = rcp(u[0]);
-  const unsigned long long sx = dbits(dabs(u[1] * rr) + c), sy = dbits(dabs(u[2] * rr) + c);
-  if (pass == 0) {
-    atomicMax(mx, sx);
-    atomicMax(mx + 1, sy);
-  } else {
-    if (sx == mx[0]) atomicMin(idx_out, (int)q);
-    if (sy == mx[1]) atomicMin(idx_out + 1, (int)q);
+    for (int d = 0; d < 2; ++d) {
+      part_mx[2 * b + d] = mx[d][0];
+      part_id[2 * b + d] = id[d][0];
+    }
   }
 }
 
-// The alpha cotangents flow to the arg-max cells: d(|u_d| + c)/dU.
+// The alpha cotangents flow to the arg-max cells: d(|u_d| + c)/dU. One block
+// of 256 threads: the arg-max over the nb block partials of k_adj_cells
+// (ties: lowest linear index), then thread 0 applies the two cotangents.
 template <int NS>
-__global__ void k_adj_alpha(StateView S, GridDev g, const MechDev* __restrict__ mech, const int* idx,
+__global__ void k_adj_alpha(StateView S, GridDev g, const MechDev* __restrict__ mech,
+                            const unsigned long long* __restrict__ part_mx, const int* __restrict__ part_id, int nb,
                             const double* adj_alpha, double* nu) {
   constexpr int NV = NS + 3;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ unsigned long long mx[2][256];
+  __shared__ int id[2][256];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    unsigned long long m = 0;
+    int i = 0x7fffffff;
+    for (int b = tid; b < nb; b += blockDim.x) argmax_merge(m, i, part_mx[2 * b + d], part_id[2 * b + d]);
+    mx[d][tid] = m;
+    id[d][tid] = i;
+  }
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+#pragma unroll
+      for (int d = 0; d < 2; ++d) argmax_merge(mx[d][tid], id[d][tid], mx[d][tid + s], id[d][tid + s]);
+    }
+    __syncthreads();
+  }
+  if (tid != 0) return;
   const long long n = g.n;
   for (int d = 0; d < 2; ++d) {
-    const int cidx = idx[d];
+    const int cidx = id[d][0];
     if (cidx < 0 || cidx >= g.n) continue;
     const double a = adj_alpha[d];
     double u[NV];
@@ -786,25 +820,29 @@ __global__ void k_prim_T_vjp(const double* __restrict__ T, const double* __restr
 // ---------------------------------------------------------------------------
 static unsigned nblk(long long count, int thr) { return (unsigned)((count + thr - 1) / thr); }
 
+// Cell-pass blocks of 32 x 8 cells.
+static int adj_cell_blocks(const GridDev& g) { return ((g.nx + 31) / 32) * ((g.ny + 7) / 8); }
+
+size_t rhs_vjp_scratch_bytes(const GridDev& g) {
+  return 256 + (((size_t)adj_cell_blocks(g) * 2 * (sizeof(unsigned long long) + sizeof(int)) + 255) & ~(size_t)255);
+}
+
 template <int NS>
 static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const double* mu, double* nu, double* CFx,
-                             double* CFy, double* scratch /* 2 doubles + 2 u64 + 2 int */, const GridDev& g,
-                             const MechDev* mech, cudaStream_t st) {
+                             double* CFy, double* scratch, const GridDev& g, const MechDev* mech, cudaStream_t st) {
   constexpr int NV = NS + 3;
+  const int nb = adj_cell_blocks(g);
   double* adj_alpha = scratch;
-  unsigned long long* mx = (unsigned long long*)(scratch + 2);
-  int* idx = (int*)(scratch + 4);
-  cudaError_t e = cudaMemsetAsync(scratch, 0, 4 * sizeof(double), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(idx, 0x7f, 2 * sizeof(int), st);
+  unsigned long long* part_mx = (unsigned long long*)((char*)scratch + 256);
+  int* part_id = (int*)(part_mx + 2 * nb);
+  cudaError_t e = cudaMemsetAsync(adj_alpha, 0, 2 * sizeof(double), st);
   if (e != cudaSuccess) return e;
   const long long fx = (long long)NV * g.ny * (g.nx + 1), fy = (long long)NV * (g.ny + 1) * g.nx;
   k_adj_faces<NV><<<nblk(fx, 128), 128, 0, st>>>(S, alpha2_dev, mu, CFx, g, 1);
   k_adj_faces<NV><<<nblk(fy, 128), 128, 0, st>>>(S, alpha2_dev, mu, CFy, g, 0);
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-  k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, nu, adj_alpha, g, mech);
-  k_speed_argmax<NS><<<nblk(g.n, 256), 256, 0, st>>>(S, g, mech, mx, idx, 0);
-  k_speed_argmax<NS><<<nblk(g.n, 256), 256, 0, st>>>(S, g, mech, mx, idx, 1);
-  k_adj_alpha<NS><<<1, 32, 0, st>>>(S, g, mech, idx, adj_alpha, nu);
+  k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, nu, adj_alpha, g, mech, part_mx, part_id);
+  k_adj_alpha<NS><<<1, 256, 0, st>>>(S, g, mech, part_mx, part_id, nb, adj_alpha, nu);
   return cudaGetLastError();
 }
 

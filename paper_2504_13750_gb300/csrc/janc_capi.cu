@@ -616,7 +616,7 @@ AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every) {
   L.lam = 7 * align256(sizeof(double) * (size_t)nv * n);
   L.cfx = align256(sizeof(double) * (size_t)nv * g->gd.ny * (g->gd.nx + 1) * 10);
   L.cfy = align256(sizeof(double) * (size_t)nv * (g->gd.ny + 1) * g->gd.nx * 10);
-  L.small = 256;
+  L.small = 256 + rhs_vjp_scratch_bytes(g->gd);  // [0] loss, then the RHS-VJP scratch at +256
   L.total = L.ckpt + L.seg + L.alog + L.lam + L.cfx + L.cfy + L.small;
   return L;
 }
@@ -637,7 +637,7 @@ int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, s
   const size_t nvn = (size_t)g->nv * g->n;
   const size_t bx = align256(sizeof(double) * (size_t)g->nv * g->gd.ny * (g->gd.nx + 1) * 10);
   const size_t by = align256(sizeof(double) * (size_t)g->nv * (g->gd.ny + 1) * g->gd.nx * 10);
-  const size_t need = 2 * align256(sizeof(double) * nvn) + bx + by + 256;
+  const size_t need = 2 * align256(sizeof(double) * nvn) + bx + by + rhs_vjp_scratch_bytes(g->gd);
   char* ws = (char*)workspace;
   bool own = false;
   if (!ws) {
@@ -678,7 +678,7 @@ struct AdjPtrs {
   double* lam[7];
   double* cfx;
   double* cfy;
-  double* small;  // [0] loss, [8..15] vjp scratch
+  double* small;  // [0] loss; from +256 bytes the RHS-VJP scratch
 };
 
 AdjPtrs adj_ptrs(const janc_grid_s* g, const AdjLayout& L, char* ws) {
@@ -710,6 +710,53 @@ void adj_release(janc_grid_s* g) {
   g->adj = janc_grid_s::AdjPending();
 }
 
+// Segment store: slots 0..len hold U^{m0+m} (with T and the aux planes),
+// then S1, S2, S* of every step of the segment.
+StateView seg_S0(const AdjPtrs& q, const AdjLayout& L, int m) {
+  return StateView{(double*)(q.seg + (size_t)m * L.state)};
+}
+StateView seg_S(const AdjPtrs& q, const AdjLayout& L, int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
+  return StateView{(double*)(q.seg + (size_t)(L.seglen + 1 + 3 * m + which - 1) * L.state)};
+}
+
+// `len` fixed-dt steps of the Lie (or explicit-source) order from segment
+// slot 0, whose alpha pair is in alog[0..1], keeping every stage state in
+// the segment store and every alpha in alog (10 slots per step: U^n, U1, U2,
+// U*, U^{n+1}). The kernels and their order are those of janc_step, so the
+// stored trajectory is the forward's, bit for bit. With `clock` the simulated
+// time advances as in janc_step; with `loss` the end-wall loss of every new
+// state accumulates into loss[0].
+cudaError_t adj_segment(janc_grid_s* g, const AdjLayout& L, const AdjPtrs& q, int len, const StepCtl& ctl,
+                        double* clock, double* loss, double w_loss) {
+  cudaStream_t st = g->stream;
+  const int nv = g->nv;
+  const bool chem = g->d.chemistry == JANC_CHEM_LIE;
+  unsigned long long* alog = q.alog;
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < len && e == cudaSuccess; ++m) {
+    unsigned long long* a = alog + 10 * m;
+    if (m > 0) e = cudaMemcpyAsync(a, alog + 10 * (m - 1) + 8, 16, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = launch_face_flux(nv, seg_S0(q, L, m), a, g->Fx, g->Gy, g->gd, st);
+    if (e == cudaSuccess)
+      e = launch_rk_update(g->ns, 1, seg_S0(q, L, m), seg_S0(q, L, m), seg_S(q, L, m, 1), g->Fx, g->Gy, g->gd,
+                           g->mech, ctl, a, a + 2, g->status, clock, st);
+    if (e == cudaSuccess) e = launch_face_flux(nv, seg_S(q, L, m, 1), a + 2, g->Fx, g->Gy, g->gd, st);
+    if (e == cudaSuccess)
+      e = launch_rk_update(g->ns, 2, seg_S(q, L, m, 1), seg_S0(q, L, m), seg_S(q, L, m, 2), g->Fx, g->Gy, g->gd,
+                           g->mech, ctl, a, a + 4, g->status, nullptr, st);
+    if (e == cudaSuccess) e = launch_face_flux(nv, seg_S(q, L, m, 2), a + 4, g->Fx, g->Gy, g->gd, st);
+    if (e == cudaSuccess)
+      e = launch_rk_update(g->ns, 3, seg_S(q, L, m, 2), seg_S0(q, L, m), seg_S(q, L, m, 3), g->Fx, g->Gy, g->gd,
+                           g->mech, ctl, a, chem ? a + 6 : a + 8, g->status, nullptr, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(seg_S0(q, L, m + 1).base, seg_S(q, L, m, 3).base, L.state, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && chem)
+      e = launch_chem(g->ns, seg_S0(q, L, m + 1), g->gd, g->mech, ctl, a, a + 8, g->status, st);
+    if (e == cudaSuccess && loss) e = launch_loss_endwall(g->ns, seg_S0(q, L, m + 1), g->gd, w_loss, loss, st);
+  }
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -734,6 +781,10 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
   auto ckpt_state = [&](int c) { return StateView{(double*)(q.ckpt + (size_t)c * (L.state + 256))}; };
   auto ckpt_alpha = [&](int c) { return (unsigned long long*)(q.ckpt + (size_t)c * (L.state + 256) + L.state); };
   const double w_loss = dt / g->gd.ny;
+  // The steps of the last segment run straight into the segment store, so
+  // that the reverse sweep starts without recomputing them; with
+  // ckpt_every >= n_steps nothing is recomputed at all.
+  const int m_last = (L.ncp - 1) * ckpt_every;
   int rc = JANC_OK;
   cudaError_t e = cudaMemsetAsync(q.small, 0, 256, st);
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
@@ -744,6 +795,23 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
         e = cudaMemcpyAsync(ckpt_alpha(c), g->alpha, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
     }
     if (e != cudaSuccess) break;
+    if (s == m_last) {
+      const int len = n_steps - m_last;
+      e = cudaMemcpyAsync(seg_S0(q, L, 0).base, g->S[0], L.state, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(q.alog, 0, L.alog, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q.alog, g->alpha, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = adj_segment(g, L, q, len, adj_ctl(g, dt), g->clock2,
+                        loss_kind == JANC_LOSS_ENDWALL_P ? q.small : nullptr, w_loss);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->S[0], seg_S0(q, L, len).base, L.state, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->alpha, q.alog + 10 * (len - 1) + 8, 2 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, st);
+      g->steps_done += len;
+      break;
+    }
     rc = janc_step(g, 1, dt, 0.0, nullptr, nullptr);
     if (rc) break;
     if (loss_kind == JANC_LOSS_ENDWALL_P) e = launch_loss_endwall(g->ns, sv(g, 0), g->gd, w_loss, q.small, st);
@@ -779,10 +847,8 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
   const size_t nvn = (size_t)nv * n;
   auto ckpt_state = [&](int c) { return StateView{(double*)(q.ckpt + (size_t)c * (L.state + 256))}; };
   auto ckpt_alpha = [&](int c) { return (unsigned long long*)(q.ckpt + (size_t)c * (L.state + 256) + L.state); };
-  auto segS0 = [&](int m) { return StateView{(double*)(q.seg + (size_t)m * L.state)}; };
-  auto segS = [&](int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
-    return StateView{(double*)(q.seg + (size_t)(ckpt_every + 1 + 3 * m + which - 1) * L.state)};
-  };
+  auto segS0 = [&](int m) { return seg_S0(q, L, m); };
+  auto segS = [&](int m, int which) { return seg_S(q, L, m, which); };
   const bool chem = g->d.chemistry == JANC_CHEM_LIE;
   const bool src = g->d.chemistry == JANC_CHEM_EXPLICIT;
   const double w_loss = dt / g->gd.ny;
@@ -805,30 +871,14 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
   for (int c = L.ncp - 1; c >= 0 && e == cudaSuccess && n_steps > 0; --c) {
     const int m0 = c * ckpt_every;
     const int len = (n_steps - m0) < ckpt_every ? (n_steps - m0) : ckpt_every;
-    // recompute the segment, keeping every stage state and its alpha
-    e = cudaMemcpyAsync(segS0(0).base, ckpt_state(c).base, L.state, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(alog, 0, L.alog, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(alog, ckpt_alpha(c), 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
-    for (int m = 0; m < len && e == cudaSuccess; ++m) {
-      unsigned long long* a = alog + 10 * m;
-      if (m > 0) e = cudaMemcpyAsync(a, alog + 10 * (m - 1) + 8, 16, cudaMemcpyDeviceToDevice, st);
-      if (e == cudaSuccess) e = launch_face_flux(nv, segS0(m), a, g->Fx, g->Gy, g->gd, st);
+    // recompute the segment, keeping every stage state and its alpha (the
+    // forward left the last segment in the store already)
+    if (c < L.ncp - 1) {
+      e = cudaMemcpyAsync(segS0(0).base, ckpt_state(c).base, L.state, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(alog, 0, L.alog, st);
       if (e == cudaSuccess)
-        e = launch_rk_update(g->ns, 1, segS0(m), segS0(m), segS(m, 1), g->Fx, g->Gy, g->gd, g->mech, ctl, a, a + 2,
-                             g->status, nullptr, st);
-      if (e == cudaSuccess) e = launch_face_flux(nv, segS(m, 1), a + 2, g->Fx, g->Gy, g->gd, st);
-      if (e == cudaSuccess)
-        e = launch_rk_update(g->ns, 2, segS(m, 1), segS0(m), segS(m, 2), g->Fx, g->Gy, g->gd, g->mech, ctl, a,
-                             a + 4, g->status, nullptr, st);
-      if (e == cudaSuccess) e = launch_face_flux(nv, segS(m, 2), a + 4, g->Fx, g->Gy, g->gd, st);
-      if (e == cudaSuccess)
-        e = launch_rk_update(g->ns, 3, segS(m, 2), segS0(m), segS(m, 3), g->Fx, g->Gy, g->gd, g->mech, ctl, a,
-                             chem ? a + 6 : a + 8, g->status, nullptr, st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(segS0(m + 1).base, segS(m, 3).base, L.state, cudaMemcpyDeviceToDevice, st);
-      if (e == cudaSuccess && chem)
-        e = launch_chem(g->ns, segS0(m + 1), g->gd, g->mech, ctl, a, a + 8, g->status, st);
+        e = cudaMemcpyAsync(alog, ckpt_alpha(c), 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = adj_segment(g, L, q, len, ctl, nullptr, nullptr, 0.0);
     }
     // reverse through the segment
     for (int m = len - 1; m >= 0 && e == cudaSuccess; --m) {
@@ -842,7 +892,7 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
       // stage 3: U* = U^n/3 + 2/3 (U2 + dt L(U2))
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 2.0 / 3.0 * dt, lamS, 0.0, nullptr, false, st);
       if (e == cudaSuccess)
-        e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
+        e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), mu, nu, cfx, cfy, small + 32, g->gd, g->mech,
                            st);
       if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, mu, nu, st);
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam2, 2.0 / 3.0, lamS, 1.0, nu, false, st);
@@ -850,7 +900,7 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
       // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 0.25 * dt, lam2, 0.0, nullptr, false, st);
       if (e == cudaSuccess)
-        e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), mu, nu, cfx, cfy, small + 8, g->gd, g->mech,
+        e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), mu, nu, cfx, cfy, small + 32, g->gd, g->mech,
                            st);
       if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, mu, nu, st);
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam1, 0.25, lam2, 1.0, nu, false, st);
@@ -858,7 +908,7 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
       // stage 1: U1 = U^n + dt L(U^n)
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, dt, lam1, 0.0, nullptr, false, st);
       if (e == cudaSuccess)
-        e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 8, g->gd, g->mech, st);
+        e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 32, g->gd, g->mech, st);
       if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, mu, nu, st);
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0, lam1, 1.0, nu, true, st);
       std::swap(lamN, lam0);

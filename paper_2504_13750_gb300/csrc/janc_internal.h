@@ -68,6 +68,9 @@ cudaError_t launch_rk_update_batch(int ns, int stage, const BatchReq* reqs, cons
 cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, cudaStream_t st);
 
 // Adjoint pieces (janc_adjoint.cu).
+// Scratch of one launch_rhs_vjp: the two alpha cotangents and the per-block
+// arg-max partials of the LF speeds (256-byte aligned start).
+size_t rhs_vjp_scratch_bytes(const GridDev& g);
 cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const double* mu, double* nu,
                            double* CFx, double* CFy, double* scratch, const GridDev& g, const MechDev* mech,
                            cudaStream_t st);

@@ -347,3 +347,45 @@ def test_config4_500_step_loss_and_finite_gradient(J):
     assert s == 0
     assert abs(float(L.detach()) - L0) <= 1e-10 * abs(L0), (float(L.detach()), L0)
     g.close()
+
+
+@pytest.mark.parametrize("chem", ["lie", "explicit"])
+def test_checkpoint_interval_leaves_trajectory_and_gradient_unchanged(J, chem):
+    """The forward runs the last segment straight into the segment store, so
+    a checkpoint interval of at least n steps recomputes nothing and one of 1
+    recomputes every step but the last. The final state equals janc_step's
+    bit for bit whatever the interval, and the gradient and loss agree to
+    the rounding of the atomic block sums (the alpha-VJP and loss
+    reductions)."""
+    if chem == "explicit":
+        mech = inputs.load_mechanism("global_h2o2_g129")
+        Y = inputs.premix_Y(mech, {"H2": 4.032, "O2": 31.998})
+        st = inputs.tube(mech, 24, 8, Lx=0.025 * 24 / 128, Y=Y, perturb_seed=4)
+        st["u"] = np.random.default_rng(31).normal(0.0, 40.0, st["T"].shape)
+        U = orc.prim_to_cons(mech, st["T"], st["p"], st["u"], st["v"], st["Y"])
+        mode = J.CHEM_EXPLICIT
+    else:
+        mech = H2AIR
+        st, U = _state(24, 8, 31, vel=40.0)
+        mode = True
+    n, dt = 11, 1e-8
+    g = J.Grid.from_grid_dict(mech, st["grid"], chemistry=mode)
+    g.set_state(U, st["T"])
+    g.step(n, dt=dt)
+    U_ref, T_ref = g.get_state()
+    grads, losses = [], []
+    for ck in (1, 3, n, 2 * n):
+        g.set_state(U, st["T"])
+        J.janc_adjoint_forward(g.handle, n, dt, ck, J.LOSS_ENDWALL_P)
+        UN, TN = g.get_state()
+        assert np.array_equal(UN, U_ref) and np.array_equal(TN, T_ref), ck
+        g.set_state(U, st["T"])
+        gU0 = np.zeros_like(U)
+        losses.append(J.janc_step_adjoint(g.handle, n, dt, ck, J.LOSS_ENDWALL_P, None, gU0))
+        grads.append(gU0)
+    for gr, L in zip(grads[1:], losses[1:]):
+        assert abs(L - losses[0]) <= 1e-13 * abs(losses[0])
+        for k in range(U.shape[0]):
+            s = max(np.max(np.abs(grads[0][k])), 1e-300)
+            assert np.max(np.abs(gr[k] - grads[0][k])) <= 1e-12 * s, k
+    g.close()
