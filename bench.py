@@ -524,18 +524,26 @@ def run_ours(args):
         Uh = torch.empty((nv, NY, NX), dtype=torch.float64, pin_memory=True).numpy()
         Th = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True).numpy()
         janc.janc_get_state(g.handle, Uh, Th)
-        e2e_steps = max(3, args.steps // 4)
+        e2e_steps = max(5, args.steps // 2)
         torch.cuda.synchronize()
+        parts = np.zeros(3)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
+            ta = time.perf_counter()
             janc.janc_set_state(g.handle, Uh, Th)
+            tb = time.perf_counter()
             janc.janc_step(g.handle, 1, cfl=CFL)
+            tc = time.perf_counter()
             janc.janc_get_state(g.handle, Uh, Th)
+            parts += (tb - ta, tc - tb, time.perf_counter() - tc)
         e2e_s = time.perf_counter() - t0
         e2e_s = reduce_max(pg, e2e_s)
+        nb = int(Uh.nbytes + Th.nbytes)
+        parts_ms = parts / e2e_steps * 1e3
         e2e = {"value": whole_job_rate(world, cells * e2e_steps, e2e_s), "unit": UNIT,
-               "h2d_bytes_per_step": int(Uh.nbytes + Th.nbytes), "d2h_bytes_per_step": int(Uh.nbytes + Th.nbytes),
-               "steps": e2e_steps}
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": e2e_steps,
+               "ms_per_step": {"set_state_h2d": float(parts_ms[0]), "step": float(parts_ms[1]),
+                               "get_state_d2h": float(parts_ms[2])}}
 
     # ---- roofline of the dominant kernel (face fluxes: FP64-pipe bound) ----
     ff_ms, ff_n = prof["face_flux"]

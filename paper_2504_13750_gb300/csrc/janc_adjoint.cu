@@ -277,43 +277,68 @@ __global__ void k_adj_alpha(StateView S, GridDev g, const MechDev* __restrict__ 
     }
     __syncthreads();
   }
-  if (tid != 0) return;
+  // Warp 0: lane k < NV takes component k of d(|u_0| + c)/dU at the x
+  // arg-max cell, lane 16 + k the same component of d(|v| + c)/dU at the y
+  // arg-max cell; lane k then adds both (x first), so a cell that is the
+  // arg-max of both directions receives them in that order.
+  static_assert(NV <= 16, "one half-warp per direction");
+  if (tid >= 32) return;
+  const int d = tid >> 4, k = tid & 15;
   const long long n = g.n;
-  for (int d = 0; d < 2; ++d) {
-    const int cidx = id[d][0];
-    if (cidx < 0 || cidx >= g.n) continue;
+  const int cidx = id[d][0];
+  double contrib = 0.0;
+  if (k < NV && cidx >= 0 && cidx < g.n) {
     const double a = adj_alpha[d];
     double u[NV];
-    for (int k = 0; k < NV; ++k) u[k] = S.plane(k, n)[cidx];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) u[q] = S.plane(q, n)[cidx];
     const double T = S.plane(NV, n)[cidx];
     const MechDev& m = *mech;
     CellThermo<NS> ct;
     cell_thermo<NS>(u, T, m, ct);
-    double dT[NV], dp[NV];
-    dT_dp_dU<NS>(u, T, m, ct, dT, dp);
     const double rho = u[0];
+    // component k of dT/dU and dp/dU (as dT_dp_dU forms them)
+    const double rrho = 1.0 / rho;
+    const double vx = u[1] * rrho, vy = u[2] * rrho;
+    const double fN = (ct.hR[NS - 1] - T) * m.invM[NS - 1];
+    double dF, dWk = 0.0, dz_cv = 0.0;
+    if (k == 0) {
+      dF = fN - 0.5 * (vx * vx + vy * vy) * (1.0 / RU);
+      dWk = m.invM[NS - 1];
+      dz_cv = ct.cvR[NS - 1] * m.invM[NS - 1];
+    } else if (k == 1) {
+      dF = vx * (1.0 / RU);
+    } else if (k == 2) {
+      dF = vy * (1.0 / RU);
+    } else if (k == 3) {
+      dF = -1.0 / RU;
+    } else {
+      dF = (ct.hR[k - 4] - T) * m.invM[k - 4] - fN;
+      dWk = m.invM[k - 4] - m.invM[NS - 1];
+      dz_cv = ct.cvR[k - 4] * m.invM[k - 4] - ct.cvR[NS - 1] * m.invM[NS - 1];
+    }
+    const double rCv = 1.0 / ct.Cv;
+    const double dTk = -dF * rCv;
+    const double dpk = RU * (T * dWk + ct.W * dTk);
     const double p = RU * ct.W * T;
     const double Cv = ct.Cv, Cp = ct.Cv + ct.W;
     const double c = sqrt(Cp * p / (Cv * rho));
     const double vel = u[1 + d] / rho;
     const double sgn = vel < 0.0 ? -1.0 : 1.0;
-    for (int k = 0; k < NV; ++k) {
-      // dz-weighted cv sums for dCv/dU
-      double dz_cv = 0.0, dW = 0.0;
-      if (k == 0) { dz_cv = ct.cvR[NS - 1] * m.invM[NS - 1]; dW = m.invM[NS - 1]; }
-      else if (k >= 4) {
-        dz_cv = ct.cvR[k - 4] * m.invM[k - 4] - ct.cvR[NS - 1] * m.invM[NS - 1];
-        dW = m.invM[k - 4] - m.invM[NS - 1];
-      }
-      const double dCv = dz_cv + ct.dCv * dT[k];
-      const double dCp = dCv + dW;
-      const double drho = k == 0 ? 1.0 : 0.0;
-      const double dc = 0.5 * c * (dCp / Cp + dp[k] / p - dCv / Cv - drho / rho);
-      double dvel = 0.0;
-      if (k == 0) dvel = -vel / rho;
-      if (k == 1 + d) dvel = 1.0 / rho;
-      nu[(long long)k * n + cidx] += a * (sgn * dvel + dc);
-    }
+    const double dCv = dz_cv + ct.dCv * dTk;
+    const double dCp = dCv + dWk;
+    const double drho = k == 0 ? 1.0 : 0.0;
+    const double dc = 0.5 * c * (dCp / Cp + dpk / p - dCv / Cv - drho / rho);
+    double dvel = 0.0;
+    if (k == 0) dvel = -vel / rho;
+    if (k == 1 + d) dvel = 1.0 / rho;
+    contrib = a * (sgn * dvel + dc);
+  }
+  const double cy = __shfl_down_sync(0xffffffffu, contrib, 16);
+  if (d == 0 && k < NV) {
+    const int cx = id[0][0], cyi = id[1][0];
+    if (cx >= 0 && cx < g.n) nu[(long long)k * n + cx] += contrib;
+    if (cyi >= 0 && cyi < g.n) nu[(long long)k * n + cyi] += cy;
   }
 }
 

@@ -38,7 +38,7 @@ __device__ __forceinline__ void weno_face_vjp(const double* F, double eps4, doub
   const double vv = fma(q1, s2, q2h * s1);
   const double num = fma(s0, vv, q0s * P12);
   // ---- reverse ----
-  const double R = 1.0 / den;
+  const double R = rcp(den);
   const double gnum = gW * R;
   const double gden = -gW * num * R * R;
   double gs0 = gnum * vv + gden * uu;
