@@ -28,84 +28,162 @@
 #include "janc_adjoint.cuh"
 #include "janc_device.cuh"
 #include "janc_internal.h"
+#include "janc_weno.cuh"
 
 namespace janc {
 
 // ---------------------------------------------------------------------------
 // RHS vector-Jacobian product.
 // ---------------------------------------------------------------------------
-constexpr int AF = 10;  // face contributions: 5 for F+, 5 for F-
+// Face pass, tiled like the forward face-flux kernel. A block takes
+// VLINES grid lines by VFACES consecutive faces along them (x tiles first,
+// then y tiles), stages the cells with the 5-cell stencil margin (ghosts
+// mapped on the fly) and the cotangent mu of L, and every thread owns one
+// (variable, line): it slides the F+ and F- windows along its faces exactly
+// as the forward does, and at each face reverses both reconstructions for
+// phi = (mu_i - mu_{i-1}) / h (L_i = -(F_{i+1/2} - F_{i-1/2}) / h).
+//
+// The cotangents of the split fluxes are summed per stencil position in
+// registers while the window passes, and each position is added once to
+// GF (zeroed) when the window leaves it or the tile ends: position e of a
+// line (e = -3 .. ncell + 2, ghosts included) holds (dL/dF+_e, dL/dF-_e).
+// GF layout: x faces [k][j][i + 3][2], y faces [k][j + 3][i][2]. A position
+// is touched by the faces of at most two tiles, so each slot receives at
+// most two additions onto zero, whose result does not depend on their order.
+constexpr int VLINES = 8;
+constexpr int VFACES = 16;
+constexpr int VWIN = VFACES + 5;
 
-// Face pass. Thread = (variable, face). mu: cotangent of L [nv][ny][nx].
-// CF[k][face][10]: cotangents of the split fluxes at the stencil cells.
 template <int NV>
-__global__ void k_adj_faces(StateView S, const double* __restrict__ alpha2, const double* __restrict__ mu,
-                            double* __restrict__ CF, GridDev g, int xdir) {
+__global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const double* __restrict__ alpha2,
+                                                           const double* __restrict__ mu, double* __restrict__ GFx,
+                                                           double* __restrict__ GFy, GridDev g, int nbx, int ntx_x,
+                                                           int ntx_y) {
+  __shared__ double sU[NV][VLINES][VWIN];
+  __shared__ double sLp[VLINES][VWIN], sLm[VLINES][VWIN], sHp[VLINES][VWIN], sHpu[VLINES][VWIN];
+  __shared__ double sMu[NV][VLINES][VFACES + 1];
+  const int blk = blockIdx.x;
+  const bool xdir = blk < nbx;
+  const int tile = xdir ? blk : blk - nbx;
+  const int ntl = xdir ? ntx_x : ntx_y;
+  const int ta = tile % ntl, tb = tile / ntl;
   const long long n = g.n;
   const int nx = g.nx, ny = g.ny;
-  const int nfl = xdir ? nx + 1 : ny + 1;   // faces per line
+  const int f0 = xdir ? ta * VFACES : tb * VFACES;
+  const int l0 = xdir ? tb * VLINES : ta * VLINES;
   const int nlines = xdir ? ny : nx;
-  const long long per_var = (long long)nfl * nlines;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= per_var * NV) return;
-  const int k = (int)(q / per_var);
-  const long long rem = q % per_var;
-  int f, line;
-  if (xdir) { line = (int)(rem / nfl); f = (int)(rem % nfl); }
-  else { f = (int)(rem / nlines); line = (int)(rem % nlines); }
+  const int nfaces = (xdir ? nx : ny) + 1;
   const int ncell = xdir ? nx : ny;
   const int bc_lo = xdir ? g.bc[0] : g.bc[2], bc_hi = xdir ? g.bc[1] : g.bc[3];
   const int nmom = xdir ? 1 : 2;
   const double ha = 0.5 * alpha2[xdir ? 0 : 1];
-  const double* Uk = S.plane(k, n);
-  const double* up = S.plane(xdir ? NV + 1 : NV + 2, n);
-  const double* pp = S.plane(NV + 3, n);
-  double Fp[6], Fm[6];
-#pragma unroll
-  for (int w = 0; w < 6; ++w) {
-    bool flip;
-    const int src = ghost_src(f - 3 + w, ncell, bc_lo, bc_hi, flip);
-    const long long idx = xdir ? (long long)line * nx + src : (long long)src * nx + line;
-    double un = up[idx];
-    if (flip) un = -un;
-    double U = Uk[idx];
-    if (flip && k == nmom) U = -U;
-    const double hp = 0.5 * pp[idx];
-    const double lp = fma(0.5, un, ha), lm = fma(0.5, un, -ha);
-    if (k == nmom) { Fp[w] = fma(lp, U, hp); Fm[w] = fma(lm, U, hp); }
-    else if (k == 3) { Fp[w] = fma(lp, U, hp * un); Fm[w] = fma(lm, U, hp * un); }
-    else { Fp[w] = lp * U; Fm[w] = lm * U; }
-  }
-  // cotangent of the face flux: L(i) = -(F(i+1/2) - F(i-1/2)) / h
   const double rh = xdir ? g.rdx : g.rdy;
-  auto mu_at = [&](int c) -> double {
-    if (c < 0 || c >= ncell) return 0.0;
-    const long long idx = xdir ? (long long)line * nx + c : (long long)c * nx + line;
-    return mu[(long long)k * n + idx];
-  };
-  const double phi = rh * (mu_at(f) - mu_at(f - 1));
-  double* out = CF + ((long long)k * per_var + (xdir ? (long long)line * nfl + f : (long long)f * nlines + line)) * AF;
-  double gp[5], gm[5];
-  weno_face_vjp<false>(Fp, g.eps4, phi, gp);   // window cells f-3 .. f+1
-  weno_face_vjp<true>(Fm + 1, g.eps4, phi, gm);  // window cells f-2 .. f+2
+  const double* uplane = S.plane(xdir ? NV + 1 : NV + 2, n);
+  const double* pplane = S.plane(NV + 3, n);
+
+  // ---- stage: cells f0-3 .. f0+VFACES+1 of every line, and mu at f0-1 .. f0+VFACES-1 ----
+  for (int q = threadIdx.x; q < VLINES * VWIN; q += blockDim.x) {
+    int line, w;
+    if (xdir) { line = q / VWIN; w = q % VWIN; } else { w = q / VLINES; line = q % VLINES; }
+    int lg = l0 + line;
+    if (lg >= nlines) lg = nlines - 1;  // inactive line: any valid cell
+    int cg = f0 - 3 + w;
+    if (cg > ncell + 2) cg = ncell + 2;
+    bool flip;
+    const int src = ghost_src(cg, ncell, bc_lo, bc_hi, flip);
+    const long long idx = xdir ? (long long)lg * nx + src : (long long)src * nx + lg;
+    double un = uplane[idx];
+    if (flip) un = -un;
+    const double hp = 0.5 * pplane[idx];
+    sLp[line][w] = fma(0.5, un, ha);
+    sLm[line][w] = fma(0.5, un, -ha);
+    sHp[line][w] = hp;
+    sHpu[line][w] = hp * un;
 #pragma unroll
-  for (int m = 0; m < 5; ++m) {
-    out[m] = gp[m];
-    out[5 + m] = gm[m];
+    for (int k = 0; k < NV; ++k) {
+      double v = S.plane(k, n)[idx];
+      if (flip && k == nmom) v = -v;
+      sU[k][line][w] = v;
+    }
+  }
+  for (int q = threadIdx.x; q < VLINES * (VFACES + 1); q += blockDim.x) {
+    int line, w;
+    if (xdir) { line = q / (VFACES + 1); w = q % (VFACES + 1); } else { w = q / VLINES; line = q % VLINES; }
+    const int lg = l0 + line;
+    const int c = f0 - 1 + w;
+    const bool in = lg < nlines && c >= 0 && c < ncell;
+    const long long idx = xdir ? (long long)lg * nx + c : (long long)c * nx + lg;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sMu[k][line][w] = in ? mu[(long long)k * n + idx] : 0.0;
+  }
+  __syncthreads();
+
+  const int var = threadIdx.x / VLINES;
+  const int line = threadIdx.x % VLINES;
+  const int lg = l0 + line;
+  if (lg >= nlines) return;
+  const int nf = min(VFACES, nfaces - f0);
+  const double* Ul = sU[var][line];
+  const double* lp = sLp[line];
+  const double* lm = sLm[line];
+  const double* pt = (var == nmom) ? sHp[line] : (var == 3 ? sHpu[line] : nullptr);
+  const double* ml = sMu[var][line];
+  auto Fp = [&](int w) -> double { return pt ? fma(lp[w], Ul[w], pt[w]) : lp[w] * Ul[w]; };
+  auto Fm = [&](int w) -> double { return pt ? fma(lm[w], Ul[w], pt[w]) : lm[w] * Ul[w]; };
+  // position w of the tile (cell f0 - 3 + w) -> its GF slot pair
+  double* gbase;
+  long long pstride;
+  if (xdir) {
+    gbase = GFx + (((long long)var * ny + lg) * (nx + 6) + f0) * 2;
+    pstride = 2;
+  } else {
+    gbase = GFy + (((long long)var * (ny + 6) + f0) * nx + lg) * 2;
+    pstride = 2LL * nx;
+  }
+  Win P, M;
+  P.init(Fp(0), Fp(1), Fp(2), Fp(3), Fp(4), g.eps4);
+  M.init(Fm(1), Fm(2), Fm(3), Fm(4), Fm(5), g.eps4);
+  // Ap[m]: dL/dF+ at position t + m, Am[m]: dL/dF- at position t + 1 + m (face t)
+  double Ap[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, Am[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int t = 0; t < nf; ++t) {
+    const double phi = rh * (ml[t + 1] - ml[t]);
+    double gp[5], gm[5];
+    weno_face_vjp<false>(P.D1, P.D2, P.D3, P.D4, P.S1, P.S2, P.S3, P.T1, P.T2, P.T3, phi, gp);
+    weno_face_vjp<true>(M.D1, M.D2, M.D3, M.D4, M.S1, M.S2, M.S3, M.T1, M.T2, M.T3, phi, gm);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      Ap[m] += gp[m];
+      Am[m] += gm[m];
+    }
+    atomicAdd(gbase + (long long)t * pstride, Ap[0]);
+    atomicAdd(gbase + (long long)(t + 1) * pstride + 1, Am[0]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      Ap[m] = Ap[m + 1];
+      Am[m] = Am[m + 1];
+    }
+    Ap[4] = 0.0;
+    Am[4] = 0.0;
+    if (t + 1 < nf) {
+      P.push(Fp(t + 5), g.eps4);
+      M.push(Fm(t + 6), g.eps4);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    atomicAdd(gbase + (long long)(nf + m) * pstride, Ap[m]);
+    atomicAdd(gbase + (long long)(nf + 1 + m) * pstride + 1, Am[m]);
   }
 }
 
 // Cell pass: cotangents of U, u_n and p of cell c from the faces, with the
 // ghost positions that copy cell c folded back. Returns via references.
 template <int NV>
-__device__ __forceinline__ void gather_dir(const StateView& S, const double* __restrict__ CF, const GridDev& g,
+__device__ __forceinline__ void gather_dir(const StateView& S, const double* __restrict__ GF, const GridDev& g,
                                            double ha, int xdir, int i, int j, double* aU, double& a_un, double& a_p,
                                            double& a_alpha) {
   const long long n = g.n;
   const int nx = g.nx, ny = g.ny;
-  const int nfl = xdir ? nx + 1 : ny + 1;
-  const int nlines = xdir ? ny : nx;
-  const long long per_var = (long long)nfl * nlines;
   const int ncell = xdir ? nx : ny;
   const int c = xdir ? i : j;
   const int line = xdir ? j : i;
@@ -139,17 +217,9 @@ __device__ __forceinline__ void gather_dir(const StateView& S, const double* __r
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const double U = (flip && k == nmom) ? -Uc[k] : Uc[k];
-      double fp = 0.0, fm = 0.0;
-      for (int f = e - 1; f <= e + 3; ++f) {
-        if (f < 0 || f >= nfl) continue;
-        fp += CF[((long long)k * per_var + (xdir ? (long long)line * nfl + f : (long long)f * nlines + line)) * AF +
-                 (e - f + 3)];
-      }
-      for (int f = e - 2; f <= e + 2; ++f) {
-        if (f < 0 || f >= nfl) continue;
-        fm += CF[((long long)k * per_var + (xdir ? (long long)line * nfl + f : (long long)f * nlines + line)) * AF +
-                 5 + (e - f + 2)];
-      }
+      const double* gf = GF + 2 * (xdir ? ((long long)k * ny + line) * (nx + 6) + (e + 3)
+                                        : ((long long)k * (ny + 6) + (e + 3)) * nx + line);
+      const double fp = gf[0], fm = gf[1];
       const double aUk = lp * fp + lm * fm;
       aU[k] += (flip && k == nmom) ? -aUk : aUk;
       aLp = fma(U, fp, aLp);
@@ -862,9 +932,14 @@ static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const
   int* part_id = (int*)(part_mx + 2 * nb);
   cudaError_t e = cudaMemsetAsync(adj_alpha, 0, 2 * sizeof(double), st);
   if (e != cudaSuccess) return e;
-  const long long fx = (long long)NV * g.ny * (g.nx + 1), fy = (long long)NV * (g.ny + 1) * g.nx;
-  k_adj_faces<NV><<<nblk(fx, 128), 128, 0, st>>>(S, alpha2_dev, mu, CFx, g, 1);
-  k_adj_faces<NV><<<nblk(fy, 128), 128, 0, st>>>(S, alpha2_dev, mu, CFy, g, 0);
+  // CFx / CFy hold the per-position sums (GF of k_adj_faces)
+  e = cudaMemsetAsync(CFx, 0, sizeof(double) * 2 * (size_t)NV * g.ny * (g.nx + 6), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(CFy, 0, sizeof(double) * 2 * (size_t)NV * (g.ny + 6) * g.nx, st);
+  if (e != cudaSuccess) return e;
+  const int ntx_x = (g.nx + 1 + VFACES - 1) / VFACES, nty_x = (g.ny + VLINES - 1) / VLINES;
+  const int ntx_y = (g.nx + VLINES - 1) / VLINES, nty_y = (g.ny + 1 + VFACES - 1) / VFACES;
+  const int nbx = ntx_x * nty_x;
+  k_adj_faces<NV><<<nbx + ntx_y * nty_y, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
   k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, nu, adj_alpha, g, mech, part_mx, part_id);
   k_adj_alpha<NS><<<1, 256, 0, st>>>(S, g, mech, part_mx, part_id, nb, adj_alpha, nu);

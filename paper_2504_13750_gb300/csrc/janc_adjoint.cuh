@@ -7,16 +7,16 @@
 
 namespace janc {
 
-// Reverse of weno_face<MINUS> (janc_flux.cu) written on the raw window
-// F_0..F_4: given the cotangent gW of the reconstructed value, returns the
-// cotangents g[0..4] of the five split-flux inputs. Same algebra as the
-// forward formula, reversed operation by operation.
+// Reverse of weno_face<MINUS> (janc_weno.cuh) on the sliding-window state of
+// the 5-point stencil F_0..F_4 (differences D1..D4, second differences
+// S1..S3, indicator parts T1..T3, as the Win struct carries them): given the
+// cotangent gW of the reconstructed value, returns the cotangents g[0..4] of
+// the five split-flux inputs. Same algebra as the forward formula, reversed
+// operation by operation.
 template <bool MINUS>
-__device__ __forceinline__ void weno_face_vjp(const double* F, double eps4, double gW, double* g) {
+__device__ __forceinline__ void weno_face_vjp(double D1, double D2, double D3, double D4, double S1, double S2,
+                                              double S3, double T1, double T2, double T3, double gW, double* g) {
   constexpr double c13 = 13.0 / 3.0;
-  const double D1 = F[1] - F[0], D2 = F[2] - F[1], D3 = F[3] - F[2], D4 = F[4] - F[3];
-  const double S1 = D2 - D1, S2 = D3 - D2, S3 = D4 - D3;
-  const double T1 = fma(c13 * S1, S1, eps4), T2 = fma(c13 * S2, S2, eps4), T3 = fma(c13 * S3, S3, eps4);
   const double X = fma(2.0, D2, S1), Z = D2 + D3, Y = fma(-2.0, D3, S3);
   const double bA = fma(X, X, T1), bB = fma(Z, Z, T2), bC = fma(Y, Y, T3);
   const double sA = bA * bA, sB = bB * bB, sC = bC * bC;
