@@ -395,12 +395,12 @@ def run_inverse(janc, iters=15):
     """Inverse-problem leg (the synthetic form of Sec. 6.2): 1000 x 400
     periodic channel, one-step global reaction as an explicit source, loss of
     Eq. 6.6 after 100 fixed-dt steps; Adam iterations per second, each one a
-    forward of 100 steps plus janc_step_adjoint over them (checkpoint every
-    20) plus the two state set-ups of dU_0/dtheta."""
+    forward of 100 steps with the whole trajectory kept on the device (20.5 GB),
+    the reverse sweep over them and the two state set-ups of dU_0/dtheta."""
     from paper_2504_13750_gb300 import inverse
 
     t0 = time.perf_counter()
-    P = inverse.ChannelInverse(nx=1000, ny=400, n_steps=100, dev_steps=400, ckpt_every=20)
+    P = inverse.ChannelInverse(nx=1000, ny=400, n_steps=100, dev_steps=400)
     setup = time.perf_counter() - t0
     P.loss_and_grad(0.8)  # warm-up
     hist, wall = P.optimize(0.8, iters=iters, lr=0.01)

@@ -38,11 +38,15 @@ def _h2o2_Y(mech, phi):
 
 
 class ChannelInverse:
-    def __init__(self, nx=250, ny=100, Lx=0.10, Ly=0.04, n_steps=100, dev_steps=400, ckpt_every=20, seed=0):
+    def __init__(self, nx=250, ny=100, Lx=0.10, Ly=0.04, n_steps=100, dev_steps=400, ckpt_every=None, seed=0):
+        """ckpt_every=None keeps the whole trajectory on the device (one
+        segment: the reverse sweep recomputes nothing); about
+        (4 n_steps + 2) x 16 x nx x ny x 8 bytes."""
         import torch
 
         self.torch = torch
         self.mech = inputs.load_mechanism(MECH)
+        ckpt_every = n_steps if ckpt_every is None else ckpt_every
         self.nx, self.ny, self.n_steps, self.ckpt = nx, ny, n_steps, ckpt_every
         dx, dy = Lx / nx, Ly / ny
         self.grid = inputs.grid_dict(nx, ny, dx, dy, [2, 2, 0, 1])
