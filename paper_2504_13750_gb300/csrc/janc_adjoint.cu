@@ -36,7 +36,8 @@ namespace janc {
 // RHS vector-Jacobian product.
 // ---------------------------------------------------------------------------
 // Face pass, tiled like the forward face-flux kernel. A block takes
-// VLINES grid lines by VFACES consecutive faces along them (x tiles first,
+// VLINES grid lines by VFACES (16, or 8 on small grids) consecutive faces
+// along them (x tiles first,
 // then y tiles), stages the cells with the 5-cell stencil margin (ghosts
 // mapped on the fly) and the cotangent mu of L, and every thread owns one
 // (variable, line): it slides the F+ and F- windows along its faces exactly
@@ -51,14 +52,13 @@ namespace janc {
 // is touched by the faces of at most two tiles, so each slot receives at
 // most two additions onto zero, whose result does not depend on their order.
 constexpr int VLINES = 8;
-constexpr int VFACES = 16;
-constexpr int VWIN = VFACES + 5;
 
-template <int NV>
+template <int NV, int VFACES>
 __global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const double* __restrict__ alpha2,
                                                            const double* __restrict__ mu, double* __restrict__ GFx,
                                                            double* __restrict__ GFy, GridDev g, int nbx, int ntx_x,
                                                            int ntx_y) {
+  constexpr int VWIN = VFACES + 5;
   __shared__ double sU[NV][VLINES][VWIN];
   __shared__ double sLp[VLINES][VWIN], sLm[VLINES][VWIN], sHp[VLINES][VWIN], sHpu[VLINES][VWIN];
   __shared__ double sMu[NV][VLINES][VFACES + 1];
@@ -936,10 +936,28 @@ static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const
   e = cudaMemsetAsync(CFx, 0, sizeof(double) * 2 * (size_t)NV * g.ny * (g.nx + 6), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(CFy, 0, sizeof(double) * 2 * (size_t)NV * (g.ny + 6) * g.nx, st);
   if (e != cudaSuccess) return e;
-  const int ntx_x = (g.nx + 1 + VFACES - 1) / VFACES, nty_x = (g.ny + VLINES - 1) / VLINES;
-  const int ntx_y = (g.nx + VLINES - 1) / VLINES, nty_y = (g.ny + 1 + VFACES - 1) / VFACES;
-  const int nbx = ntx_x * nty_x;
-  k_adj_faces<NV><<<nbx + ntx_y * nty_y, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+  // tiles of 16 faces while that gives at least 8 blocks per SM, else 8
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  auto tiles = [&](int vf, int* nbx, int* ntx_x, int* ntx_y) {
+    *ntx_x = (g.nx + 1 + vf - 1) / vf;
+    *ntx_y = (g.nx + VLINES - 1) / VLINES;
+    *nbx = *ntx_x * ((g.ny + VLINES - 1) / VLINES);
+    return *nbx + *ntx_y * ((g.ny + 1 + vf - 1) / vf);
+  };
+  int nbx, ntx_x, ntx_y;
+  int total = tiles(16, &nbx, &ntx_x, &ntx_y);
+  if (total >= 8 * sms) {
+    k_adj_faces<NV, 16><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+  } else {
+    total = tiles(8, &nbx, &ntx_x, &ntx_y);
+    k_adj_faces<NV, 8><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+  }
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
   k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, nu, adj_alpha, g, mech, part_mx, part_id);
   k_adj_alpha<NS><<<1, 256, 0, st>>>(S, g, mech, part_mx, part_id, nb, adj_alpha, nu);

@@ -5,7 +5,9 @@
 //
 // One launch covers both directions: blocks [0, nbx) take x-face tiles and the
 // rest take y-face tiles. A tile is LINES grid lines (rows for x, columns for
-// y) by FACES consecutive faces along them. Its cells, with the 5-cell stencil
+// y) by 32 consecutive faces along them (16 or 8 on grids too small to fill
+// the GPU with 32-face tiles; the batched launch always uses 32). Its cells,
+// with the 5-cell stencil
 // margin, are staged in shared memory once; every thread then owns one
 // (line, variable) and slides two 5-point windows (F+ and F-) along its line,
 // so the first and second differences and the 13/3 S^2 part of the
@@ -21,15 +23,16 @@
 namespace janc {
 
 constexpr int LINES = 8;
-constexpr int FACES = 32;
-constexpr int WIN = FACES + 5;
+constexpr int FACES = 32;  // faces per tile of the batched launch and of large grids
 
-// One tile of the face-flux launch; `blk` is the tile's index in the
-// launch (x tiles first). Shared by the single-grid and the batched kernels.
-template <int NV>
+// One tile of the face-flux launch (FC faces per line); `blk` is the tile's
+// index in the launch (x tiles first). Shared by the single-grid and the
+// batched kernels.
+template <int NV, int FC = FACES>
 __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigned long long* __restrict__ alpha,
                                                double* __restrict__ Fx, double* __restrict__ Gy, const GridDev& g,
                                                int blk, int nbx, int ntx_x, int ntx_y, double* smem) {
+  constexpr int WIN = FC + 5;
   double* sU = smem;                       // [NV][LINES][WIN]
   double* sLp = sU + NV * LINES * WIN;     // lambda+ = (u_n + alpha) / 2
   double* sLm = sLp + LINES * WIN;         // lambda- = (u_n - alpha) / 2
@@ -44,7 +47,7 @@ __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigne
   const long long n = g.n;
   const int nx = g.nx, ny = g.ny;
   // x tiles: faces along x (ta), rows (tb). y tiles: columns (ta), faces along y (tb).
-  const int f0 = xdir ? ta * FACES : tb * FACES;
+  const int f0 = xdir ? ta * FC : tb * FC;
   const int l0 = xdir ? tb * LINES : ta * LINES;
   const int nlines = xdir ? ny : nx;          // number of lines in the domain
   const int nfaces = (xdir ? nx : ny) + 1;    // faces per line
@@ -87,7 +90,7 @@ __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigne
   __syncthreads();
 
   // ---- reconstruct and store: thread = (variable, line), both signs ----
-  const int nf = min(FACES, nfaces - f0);
+  const int nf = min(FC, nfaces - f0);
   const int var = threadIdx.x / LINES;
   const int line = threadIdx.x % LINES;
   const int lg = l0 + line;
@@ -102,12 +105,12 @@ __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigne
   }
 }
 
-template <int NV>
+template <int NV, int FC>
 __global__ void __launch_bounds__(LINES * NV) k_face_flux(StateView S, const unsigned long long* __restrict__ alpha,
                                                           double* __restrict__ Fx, double* __restrict__ Gy,
                                                           GridDev g, int nbx, int ntx_x, int ntx_y) {
   extern __shared__ double smem[];
-  face_flux_tile<NV>(S, alpha, Fx, Gy, g, blockIdx.x, nbx, ntx_x, ntx_y, smem);
+  face_flux_tile<NV, FC>(S, alpha, Fx, Gy, g, blockIdx.x, nbx, ntx_x, ntx_y, smem);
 }
 
 // Batched form: a persistent grid walks the flattened (request, tile) list;
@@ -126,38 +129,69 @@ __global__ void __launch_bounds__(LINES * NV) k_face_flux_batch(const BatchReq* 
   }
 }
 
-template <int NV>
+template <int NV, int FC = FACES>
 static size_t flux_smem_bytes() {
-  return sizeof(double) * (size_t)(NV + 4) * LINES * WIN;
+  return sizeof(double) * (size_t)(NV + 4) * LINES * (FC + 5);
+}
+
+// Tiles of FC faces: x tiles first, then y tiles.
+static void tiles_of(const GridDev& g, int fc, int* nbx, int* ntx_x, int* ntx_y, int* total) {
+  *ntx_x = (g.nx + 1 + fc - 1) / fc;
+  const int nty_x = (g.ny + LINES - 1) / LINES;
+  *ntx_y = (g.nx + LINES - 1) / LINES;
+  const int nty_y = (g.ny + 1 + fc - 1) / fc;
+  *nbx = *ntx_x * nty_x;
+  *total = *nbx + *ntx_y * nty_y;
+}
+
+template <int NV, int FC>
+static cudaError_t launch_face_flux_fc(const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
+                                       const GridDev& g, cudaStream_t st) {
+  int nbx, ntx_x, ntx_y, total;
+  tiles_of(g, FC, &nbx, &ntx_x, &ntx_y, &total);
+  const size_t smem = flux_smem_bytes<NV, FC>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_face_flux<NV, FC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_face_flux<NV, FC><<<total, LINES * NV, smem, st>>>(S, alpha, Fx, Gy, g, nbx, ntx_x, ntx_y);
+  return cudaGetLastError();
+}
+
+// Tile length by grid size: 32 faces while that gives at least 8 blocks per
+// SM, 16 while that gives at least 2, else 8. Shorter tiles mean more blocks
+// and a larger share of stencil margin; on small grids, whose launches are a
+// fraction of a wave and latency-bound, the blocks win (measured on one
+// GB300: 256 x 32 runs best at 8, 512 x 64 at 16, 4096 x 512 at 32).
+static int flux_tile_faces(const GridDev& g) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int nbx, ntx_x, ntx_y, total;
+  tiles_of(g, 32, &nbx, &ntx_x, &ntx_y, &total);
+  if (total >= 8 * sms) return 32;
+  tiles_of(g, 16, &nbx, &ntx_x, &ntx_y, &total);
+  return total >= 2 * sms ? 16 : 8;
 }
 
 template <int NV>
 static cudaError_t launch_face_flux_t(const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
                                       const GridDev& g, cudaStream_t st) {
-  const int ntx_x = (g.nx + 1 + FACES - 1) / FACES;
-  const int nty_x = (g.ny + LINES - 1) / LINES;
-  const int ntx_y = (g.nx + LINES - 1) / LINES;
-  const int nty_y = (g.ny + 1 + FACES - 1) / FACES;
-  const int nbx = ntx_x * nty_x;
-  const int nby = ntx_y * nty_y;
-  const size_t smem = flux_smem_bytes<NV>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_face_flux<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  switch (flux_tile_faces(g)) {
+    case 32: return launch_face_flux_fc<NV, 32>(S, alpha, Fx, Gy, g, st);
+    case 16: return launch_face_flux_fc<NV, 16>(S, alpha, Fx, Gy, g, st);
+    default: return launch_face_flux_fc<NV, 8>(S, alpha, Fx, Gy, g, st);
   }
-  k_face_flux<NV><<<nbx + nby, LINES * NV, smem, st>>>(S, alpha, Fx, Gy, g, nbx, ntx_x, ntx_y);
-  return cudaGetLastError();
 }
 
 void face_flux_tiles(const GridDev& g, int* nbx, int* ntx_x, int* ntx_y, int* total) {
-  *ntx_x = (g.nx + 1 + FACES - 1) / FACES;
-  const int nty_x = (g.ny + LINES - 1) / LINES;
-  *ntx_y = (g.nx + LINES - 1) / LINES;
-  const int nty_y = (g.ny + 1 + FACES - 1) / FACES;
-  *nbx = *ntx_x * nty_x;
-  *total = *nbx + *ntx_y * nty_y;
+  tiles_of(g, FACES, nbx, ntx_x, ntx_y, total);
 }
 
 template <int NV>
