@@ -35,7 +35,7 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
   constexpr int NV = NS + 3;
   const MechDev& m = *mech;
   const long long n = g.n;
-  const long long idx = blk * CHEM_THREADS + threadIdx.x;
+  const long long idx = blk * blockDim.x + threadIdx.x;
   const double dt = step_dt(ctl, alpha_step) * ctl.chem_frac;
   unsigned long long sx = 0, sy = 0;
   int st = 0;
@@ -274,13 +274,31 @@ cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, in
 
 int chem_blocks(const GridDev& g) { return (int)((g.n + CHEM_THREADS - 1) / CHEM_THREADS); }
 
+// Threads per block: CHEM_THREADS while that gives at least 4 blocks per SM,
+// else 64 or 32, so that a small grid's cells spread over all SMs (each
+// cell is one long dependent FP64 chain; a launch of a few blocks per SM is
+// latency-bound).
+static int chem_threads(long long n) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  for (int t = CHEM_THREADS; t > 32; t /= 2)
+    if ((n + t - 1) / t >= 4LL * sms) return t;
+  return 32;
+}
+
 cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
                         const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,
                         cudaStream_t st) {
-  const unsigned blocks = (unsigned)((g.n + CHEM_THREADS - 1) / CHEM_THREADS);
+  const int thr = chem_threads(g.n);
+  const unsigned blocks = (unsigned)((g.n + thr - 1) / thr);
   switch (ns) {
-    case 3: k_chem<3><<<blocks, CHEM_THREADS, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
-    case 9: k_chem<9><<<blocks, CHEM_THREADS, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
+    case 3: k_chem<3><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
+    case 9: k_chem<9><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -25,7 +25,7 @@ __device__ __forceinline__ void finish_cell(const StateView& S, long long n, lon
   sy = dbits(dabs(vy) + c);
 }
 
-// One UPD_BX x UPD_BY block (bx, by) of the stage update; shared by the
+// One block (bx, by) of blockDim.x x blockDim.y cells of the stage update; shared by the
 // single-grid and the batched kernels.
 template <int NS, int STAGE, bool SRC = false>
 __device__ __forceinline__ void rk_update_block(const StateView& Sin, const StateView& S0, const StateView& Sout,
@@ -35,8 +35,8 @@ __device__ __forceinline__ void rk_update_block(const StateView& Sin, const Stat
                                                 unsigned long long* alpha_out, int* status, double* clock2, int bx,
                                                 int by) {
   constexpr int NV = NS + 3;
-  const int i = bx * UPD_BX + threadIdx.x;
-  const int j = by * UPD_BY + threadIdx.y;
+  const int i = bx * blockDim.x + threadIdx.x;
+  const int j = by * blockDim.y + threadIdx.y;
   const long long n = g.n;
   const double dt = step_dt(ctl, alpha_step);
   if (STAGE == 1 && clock2 && bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -171,7 +171,20 @@ static cudaError_t launch_rk_update_t(int stage, const StateView& Sin, const Sta
                                       const double* Fx, const double* Gy, const GridDev& g, const MechDev* mech,
                                       const StepCtl& ctl, const unsigned long long* a_step, unsigned long long* a_out,
                                       int* status, double* clock2, cudaStream_t st) {
-  dim3 blk(UPD_BX, UPD_BY), grd((g.nx + UPD_BX - 1) / UPD_BX, (g.ny + UPD_BY - 1) / UPD_BY);
+  // UPD_BX x UPD_BY blocks while that gives at least 4 blocks per SM; on
+  // smaller grids shorter blocks (UPD_BX x 4, 2, 1) spread the cells over
+  // all SMs.
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const long long bxs = (g.nx + UPD_BX - 1) / UPD_BX;
+  int by = UPD_BY;
+  while (by > 1 && bxs * ((g.ny + by - 1) / by) < 4LL * sms) by /= 2;
+  dim3 blk(UPD_BX, by), grd((unsigned)bxs, (g.ny + by - 1) / by);
   if (ctl.source && NS > 1) {
     if (stage == 1)
       k_rk_update<NS, 1, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
