@@ -182,16 +182,16 @@ __global__ void __launch_bounds__(AB2) k_amr_update(StateView Sin, StateView S0,
     const double* fx = Fx + ((long long)blk * AB + j) * (AB + 1) + i;
     const double* gy = Gy + ((long long)blk * (AB + 1) + j) * AB + i;
     const long long sfx = (long long)L.nblk * AB * (AB + 1);
+    const double cx = dt * L.rdx, cy = dt * L.rdy;  // as the grid's stage update
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const double dF = fx[k * sfx + 1] - fx[k * sfx];
       const double dG = gy[k * sfx + AB] - gy[k * sfx];
-      const double Lk = -fma(dF, L.rdx, dG * L.rdy);
       const double uin = Sin.plane(k, n)[idx];
+      const double t = fma(-cx, dF, fma(-cy, dG, uin));
       if (STAGE == 1) {
-        u[k] = fma(dt, Lk, uin);
+        u[k] = t;
       } else {
-        const double t = fma(dt, Lk, uin);
         const double u0 = S0.plane(k, n)[idx];
         u[k] = (STAGE == 2) ? fma(0.75, u0, 0.25 * t) : fma(1.0 / 3.0, u0, (2.0 / 3.0) * t);
       }

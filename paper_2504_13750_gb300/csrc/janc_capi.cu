@@ -108,6 +108,12 @@ int build_mech(const janc_mechanism* m, MechDev* h) {
     h->gc[k][6] = a[6] - a[0];
     h->mratio[k] = m->M[k] / m->M[ns - 1];
   }
+  h->WN = h->invM[ns - 1];
+  for (int q = 0; q < 6; ++q) h->hcN[q] = h->hc[ns - 1][q] * h->invM[ns - 1];
+  for (int k = 0; k < ns - 1; ++k) {
+    h->Wd[k] = h->invM[k] - h->WN;
+    for (int q = 0; q < 6; ++q) h->hcd[k][q] = h->hc[k][q] * h->invM[k] - h->hcN[q];
+  }
   for (int i = 0; i < m->nr; ++i) {
     if (!(m->A[i] > 0.0)) return fail(JANC_E_INVALID, "Arrhenius A must be > 0");
     h->lnA[i] = std::log(m->A[i]);

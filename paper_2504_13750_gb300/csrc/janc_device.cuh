@@ -54,6 +54,14 @@ struct MechDev {
   // eff_il - (M_l / M_ns) eff_i,ns for l < ns - 1.
   double ceff[MAX_NR][MAX_NS];
   double mratio[MAX_NS];  // M_l / M_ns
+  // Mixture sums in the carried variables: since rho Y_ns = rho - sum_{k<ns-1}
+  // rho Y_k, sum_k (rho Y_k / M_k) c_k = rho cN + sum_{k<ns-1} rho Y_k cd_k
+  // with cN = c_ns / M_ns and cd_k = c_k / M_k - cN. For the enthalpy
+  // coefficients (hcN, hcd) and for c = 1 (WN, Wd: W = sum_k z_k).
+  double hcN[6];
+  double hcd[MAX_NS][6];
+  double WN;
+  double Wd[MAX_NS];
 };
 
 // Grid constants passed by value to every kernel.
@@ -180,29 +188,30 @@ __device__ __forceinline__ double step_dt(const StepCtl& c, const unsigned long 
   return c.cfl * c.hmin / amax;
 }
 
+// W = sum_k z_k and the first NH mixture enthalpy coefficients
+// h[q] = sum_k z_k hc_k[q] (z_k = rho Y_k / M_k) from the carried variables,
+// through the folded tables of MechDev: 1 + (ns - 1) FP64 operations each.
+template <int NS, int NH>
+__device__ __forceinline__ void mixture_sums(const double* u, const MechDev& m, double& W, double* h) {
+  const double rho = u[0];
+  W = rho * m.WN;
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) W = fma(u[4 + k], m.Wd[k], W);
+#pragma unroll
+  for (int q = 0; q < NH; ++q) {
+    double s = rho * m.hcN[q];
+#pragma unroll
+    for (int k = 0; k < NS - 1; ++k) s = fma(u[4 + k], m.hcd[k][q], s);
+    h[q] = s;
+  }
+}
+
 // Sound speed exactly as newton_cell finishes it, from the stored T.
 template <int NS>
 __device__ __forceinline__ double sound_speed(const double* u, double t, const MechDev& m) {
   const double rrho = rcp(u[0]);
-  double z[NS];
-  double rest = u[0];
-#pragma unroll
-  for (int k = 0; k < NS - 1; ++k) {
-    z[k] = u[4 + k] * m.invM[k];
-    rest -= u[4 + k];
-  }
-  z[NS - 1] = rest * m.invM[NS - 1];
-  double W = z[0];
-#pragma unroll
-  for (int k = 1; k < NS; ++k) W += z[k];
-  double h[5];
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    double s = z[0] * m.hc[0][q];
-#pragma unroll
-    for (int k = 1; k < NS; ++k) s = fma(z[k], m.hc[k][q], s);
-    h[q] = s;
-  }
+  double W, h[5];
+  mixture_sums<NS, 5>(u, m, W, h);
   const double c1 = 2.0 * h[1], c2 = 3.0 * h[2], c3 = 4.0 * h[3], c4 = 5.0 * h[4];
   const double K1 = h[0] - W;
   const double Cv = fma(t, fma(t, fma(t, fma(t, c4, c3), c2), c1), K1);
@@ -340,7 +349,7 @@ __device__ __forceinline__ void block_reduce_alpha_status(unsigned long long sx,
 
 // Newton-Raphson T recovery (end of Sec. 4.2) from the energy, warm-started
 // at Tw, followed by p (Eq. 4.2) and the frozen sound speed. The mixture is
-// reduced to polynomial coefficients once per cell:
+// reduced to polynomial coefficients once per cell (mixture_sums):
 //   H(T) = sum_k z_k h_k(T)/Ru with z_k = rho Y_k / M_k,
 //   F(T) = H(T) - W T - rho e / Ru  (W = sum_k z_k, rho e = E - |rho u|^2 / (2 rho)),
 //   F'(T) = sum_k z_k cv_k / Ru.
@@ -350,25 +359,8 @@ __device__ __forceinline__ int newton_cell(const double* u, double Tw, const Mec
                                            double& T, double& p, double& c, double& rrho) {
   const double rho = u[0];
   rrho = rcp(rho);
-  double z[NS];
-  double rest = rho;
-#pragma unroll
-  for (int k = 0; k < NS - 1; ++k) {
-    z[k] = u[4 + k] * m.invM[k];
-    rest -= u[4 + k];
-  }
-  z[NS - 1] = rest * m.invM[NS - 1];
-  double W = z[0];
-#pragma unroll
-  for (int k = 1; k < NS; ++k) W += z[k];
-  double h[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    double s = z[0] * m.hc[0][q];
-#pragma unroll
-    for (int k = 1; k < NS; ++k) s = fma(z[k], m.hc[k][q], s);
-    h[q] = s;
-  }
+  double W, h[6];
+  mixture_sums<NS, 6>(u, m, W, h);
   const double c1 = 2.0 * h[1], c2 = 3.0 * h[2], c3 = 4.0 * h[3], c4 = 5.0 * h[4];
   const double ke = fma(u[1], u[1], u[2] * u[2]);
   const double rhoe_R = fma(-0.5 * rrho, ke, u[3]) * (1.0 / RU);
