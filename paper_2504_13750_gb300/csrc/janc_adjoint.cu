@@ -4,21 +4,24 @@
 // checkpoint-and-recompute over the trajectory.
 //
 //  * Right-hand side L(U) (Eq. 4.10-4.11, WENO5, ghost layers): the
-//    vector-Jacobian product is taken face by face (the reverse of the
-//    reconstruction formula for both split signs) into a face-contribution
-//    buffer, then gathered per cell over the faces whose stencils touch it,
-//    ghost images included and folded back with the wall flips; the chain
-//    through u, v and p(T(U)) uses the implicit derivative of the Newton T
-//    recovery. The global LF speeds alpha (Eq. 4.11) receive the summed
-//    cotangent, which flows to the cell that attains the maximum (ties:
-//    lowest linear index).
+//    vector-Jacobian product reverses the reconstruction formula of both
+//    split signs face by face, in tiles that slide along grid lines like the
+//    forward kernel, and sums the split-flux cotangents per stencil position
+//    (ghost positions included); each cell then reads the sums of its own
+//    position and of the ghost images that copy it, folded back with the
+//    wall flips. The chain through u, v and p(T(U)) uses the implicit
+//    derivative of the Newton T recovery. The global LF speeds alpha
+//    (Eq. 4.11) receive the summed cotangent, which flows to the cell that
+//    attains the maximum (ties: lowest linear index).
 //  * Point-implicit chemistry (Eq. 4.12-4.13): one transposed solve with the
 //    LU factors of the forward system, then the gradient of a scalar
 //    (sum over reactions of the weighted rate and its derivative along the
 //    solution) in reverse mode, chained through T* = T(U*) (see
 //    chem_vjp_rev).
 //  * TVD-RK3: the Shu-Osher stages reversed.
-// No atomics touch state cotangents: every cell gathers its own.
+// No atomics touch state cotangents: every cell gathers its own. (The
+// per-position split-flux sums take at most two atomic additions per slot
+// onto zero, whose result does not depend on their order.)
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -176,8 +179,9 @@ __global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const do
   }
 }
 
-// Cell pass: cotangents of U, u_n and p of cell c from the faces, with the
-// ghost positions that copy cell c folded back. Returns via references.
+// Cell pass: cotangents of U, u_n and p of cell c from the per-position sums
+// of k_adj_faces, with the ghost positions that copy cell c folded back.
+// Returns via references.
 template <int NV>
 __device__ __forceinline__ void gather_dir(const StateView& S, const double* __restrict__ GF, const GridDev& g,
                                            double ha, int xdir, int i, int j, double* aU, double& a_un, double& a_p,
@@ -246,8 +250,8 @@ __device__ __forceinline__ void argmax_merge(unsigned long long& m, int& i, unsi
 // (atomically added) and the arg-max of |u|+c and |v|+c over its cells in
 // part_mx / part_id [2 * block + direction].
 template <int NS>
-__global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, const double* __restrict__ CFx,
-                            const double* __restrict__ CFy, double* __restrict__ nu, double* adj_alpha, GridDev g,
+__global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, const double* __restrict__ GFx,
+                            const double* __restrict__ GFy, double* __restrict__ nu, double* adj_alpha, GridDev g,
                             const MechDev* __restrict__ mech, unsigned long long* __restrict__ part_mx,
                             int* __restrict__ part_id) {
   constexpr int NV = NS + 3;
@@ -263,8 +267,8 @@ __global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, cons
 #pragma unroll
     for (int k = 0; k < NV; ++k) aU[k] = 0.0;
     double a_u = 0.0, a_v = 0.0, a_p = 0.0;
-    gather_dir<NV>(S, CFx, g, 0.5 * alpha2[0], 1, i, j, aU, a_u, a_p, ax);
-    gather_dir<NV>(S, CFy, g, 0.5 * alpha2[1], 0, i, j, aU, a_v, a_p, ay);
+    gather_dir<NV>(S, GFx, g, 0.5 * alpha2[0], 1, i, j, aU, a_u, a_p, ax);
+    gather_dir<NV>(S, GFy, g, 0.5 * alpha2[1], 0, i, j, aU, a_v, a_p, ay);
     double u[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) u[k] = S.plane(k, n)[idx];
