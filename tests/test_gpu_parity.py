@@ -87,8 +87,15 @@ def test_face_fluxes_and_rhs(J, nx, ny, bc):
     assert rel_err(L, L0) < 1e-10
 
 
-def test_one_step_tube(J):
-    st = inputs.tube(H2AIR, 256, 32)
+@pytest.mark.parametrize("nx,ny", [(256, 32), (512, 96), (1024, 96)])
+def test_one_step_tube(J, nx, ny):
+    """One step against the oracle at sizes that take each launch shape the
+    grid kernels choose by size: 256 x 32 (8-face flux tiles, 32 x 1 update
+    blocks, 32-thread chemistry blocks), 512 x 96 (16-face tiles, 32 x 2,
+    64 threads), 1024 x 96 (16-face tiles, 32 x 4, 128 threads); the
+    4096 x 512 bench grid (32-face tiles, 32 x 8) is covered by
+    test_full_size_config2_two_steps."""
+    st = inputs.tube(H2AIR, nx, ny, Lx=0.05 * nx / 256, perturb_seed=5)
     U = _cons(H2AIR, st)
     g = _grid(J, H2AIR, st)
     g.set_state(U, st["T"])
