@@ -35,6 +35,7 @@
 
 #include "../../include/janc.h"
 #include "janc_device.cuh"
+#include "janc_host.h"
 #include "janc_internal.h"
 #include "janc_weno.cuh"
 
@@ -46,7 +47,8 @@ constexpr int AH = AB / 2;        // parent cells per block edge
 constexpr int NGH = 3;            // ghost cells per side = cells of the external band
 constexpr int ALINES = 8;         // lines per flux tile
 constexpr int AWIN = AB + 1 + 5;  // window of a line: 17 faces with the 5-point stencils
-enum : int { NB_EXTERNAL = -1, NB_PHYSICAL = -2 };
+constexpr int NB_EXTERNAL = host::NB_EXTERNAL, NB_PHYSICAL = host::NB_PHYSICAL;
+static_assert(host::BC_PERIODIC_CODE == BC_PERIODIC, "boundary codes of janc_host.h");
 
 struct LayerDev {
   int nblk;
@@ -559,35 +561,11 @@ cudaError_t f2c_t(janc_amr_s* A, int i) {
   return cudaGetLastError();
 }
 
-// New block list of layer i from the flags; neighbours (periodic wrap,
-// physical sides, external sides) and the position map.
-void build_lists(const janc_amr_s* A, int i, const std::vector<unsigned char>& flags, AmrLayer& N,
-                 std::vector<int>& nbr) {
-  N.pos.clear();
-  N.map.assign((size_t)N.nbx * N.nby, -1);
-  for (int by = 0; by < N.nby; ++by)
-    for (int bx = 0; bx < N.nbx; ++bx)
-      if (flags[(size_t)by * N.nbx + bx]) {
-        N.map[(size_t)by * N.nbx + bx] = (int)N.pos.size();
-        N.pos.push_back(bx | (by << 16));
-      }
+// New block list of a layer from the flags; neighbours (periodic wrap,
+// physical sides, external sides) and the position map (janc_host.h).
+void build_lists(const janc_amr_s* A, const std::vector<unsigned char>& flags, AmrLayer& N, std::vector<int>& nbr) {
+  janc::host::build_block_lists(flags.data(), N.nbx, N.nby, A->d.bc, N.pos, N.map, nbr);
   N.nblk = (int)N.pos.size();
-  nbr.assign((size_t)4 * N.nblk, NB_EXTERNAL);
-  const int dxs[4] = {0, 0, -1, 1}, dys[4] = {1, -1, 0, 0}, side[4] = {3, 2, 0, 1};
-  for (int b = 0; b < N.nblk; ++b) {
-    const int bx = N.pos[b] & 0xffff, by = N.pos[b] >> 16;
-    for (int s = 0; s < 4; ++s) {
-      int qx = bx + dxs[s], qy = by + dys[s];
-      const bool inside = qx >= 0 && qx < N.nbx && qy >= 0 && qy < N.nby;
-      if (!inside) {
-        if (A->d.bc[side[s]] != BC_PERIODIC) { nbr[(size_t)4 * b + s] = NB_PHYSICAL; continue; }
-        qx = (qx + N.nbx) % N.nbx;
-        qy = (qy + N.nby) % N.nby;
-      }
-      nbr[(size_t)4 * b + s] = N.map[(size_t)qy * N.nbx + qx];
-    }
-  }
-  (void)i;
 }
 
 int regrid(janc_amr_s* A) {
@@ -630,7 +608,7 @@ int regrid(janc_amr_s* A) {
     N.nby = O.nby;
     N.alpha = O.alpha;
     std::vector<int> nbr;
-    build_lists(A, i, flags, N, nbr);
+    build_lists(A, flags, N, nbr);
     std::vector<int> oldidx((size_t)N.nblk);
     for (int b = 0; b < N.nblk; ++b) {
       const int bx = N.pos[b] & 0xffff, by = N.pos[b] >> 16;

@@ -24,9 +24,11 @@
 
 #include "../../include/janc.h"
 #include "janc_device.cuh"
+#include "janc_host.h"
 #include "janc_internal.h"
 
 using namespace janc;
+using janc::host::Pool;
 
 namespace {
 
@@ -36,50 +38,6 @@ double now_s() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
-
-// First-fit allocator over [0, size) in 256-byte units; free blocks are kept
-// by offset and merged with their neighbours on release.
-struct Pool {
-  size_t size = 0, used = 0;
-  std::map<size_t, size_t> free_;
-  void init(size_t s) {
-    size = s & ~size_t(255);
-    used = 0;
-    free_.clear();
-    if (size) free_[0] = size;
-  }
-  bool alloc(size_t n, size_t* off) {
-    n = a256(n);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        *off = it->first;
-        const size_t rest = it->second - n, o2 = it->first + n;
-        free_.erase(it);
-        if (rest) free_[o2] = rest;
-        used += n;
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t n) {
-    n = a256(n);
-    used -= n;
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-};
 
 enum RState { R_QUEUED = 0, R_ACTIVE = 1, R_COPYING = 2, R_DONE = 3, R_FAILED = 4, R_FETCHED = 5 };
 
@@ -210,30 +168,22 @@ int admit(janc_server_s* s, Req* r) {
   return JANC_OK;
 }
 
+// One admission pass (janc_host.h): slots, cell budget with aging, pool.
 void try_admit(janc_server_s* s) {
-  for (auto it = s->queue.begin(); it != s->queue.end();) {
-    if ((int)s->active.size() >= s->max_active) break;
-    Req* r = s->reqs[*it];
-    // the cell budget admits a request that would exceed it only into an empty
-    // active set; later requests may pass it until it has waited max_skip_s,
-    // then nothing behind it is admitted (the active set drains for it)
-    if (s->cell_budget > 0 && !s->active.empty() && s->active_cells + r->n > s->cell_budget) {
-      if (now_s() - r->t_submit >= s->max_skip_s) break;
-      ++it;
-      continue;
-    }
-    size_t off;
-    if (s->pool.alloc(r->footprint, &off)) {
-      r->off = off;
-      if (admit(s, r) != JANC_OK) {
-        s->pool.release(off, r->footprint);
+  janc::host::admission_pass(
+      s->queue, s->pool, s->max_active, s->cell_budget, s->max_skip_s, now_s(),
+      [&](int id) {
+        const Req* r = s->reqs[id];
+        return janc::host::Pending{r->n, r->footprint, r->t_submit};
+      },
+      [&] { return (int)s->active.size(); }, [&] { return s->active_cells; },
+      [&](int id, size_t off) {
+        Req* r = s->reqs[id];
+        r->off = off;
+        if (admit(s, r) == JANC_OK) return true;
         r->state = R_FAILED;
-      }
-      it = s->queue.erase(it);
-    } else {
-      ++it;
-    }
-  }
+        return false;
+      });
 }
 
 void reap(janc_server_s* s) {
