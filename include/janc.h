@@ -221,7 +221,12 @@ int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
 #define JANC_LOSS_ENDWALL_P 0  /* L = sum_n dt * mean_j p(nx-1, j) of U^{n+1} */
 #define JANC_LOSS_SEEDED 1     /* L = <seed, U^N> (seed: nv planes) */
 
-/* Device bytes janc_step_adjoint needs as workspace. */
+/* Device bytes janc_step_adjoint needs as workspace: checkpoints every
+ * ckpt_every steps, the stage states of one segment of ckpt_every steps,
+ * cotangent and face buffers. The forward writes the last segment's stages
+ * directly, so the reverse recomputes every segment but the last; with
+ * ckpt_every >= n_steps the whole trajectory is kept and nothing is
+ * recomputed (about (4 n_steps + 2) (nv + 4) nx ny doubles). */
 int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, size_t* bytes);
 
 /* From the grid's current state U^0 (set beforehand), run n_steps fixed-dt
@@ -255,8 +260,9 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
  * WENO5, the ghost layers and the global LF speeds) at the grid's current
  * state: nu = (dL/dU)^T mu, both [nv][ny][nx], host or device. workspace:
  * device memory for 2 nv planes plus 10 nv values per x- and y-face, each
- * piece rounded up to 256 bytes, plus 256 bytes (NULL: allocated here).
- * Synchronous. */
+ * piece rounded up to 256 bytes, plus 256 bytes and 24 bytes per 32 x 8
+ * block of cells rounded up to 256 (NULL: allocated here); a smaller
+ * workspace returns JANC_E_NOMEM. Synchronous. */
 int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, size_t workspace_bytes, int where);
 
 /* dL/dT [ny][nx] of the primitive initialisation of Eq. 4.2 at fixed p, u,
