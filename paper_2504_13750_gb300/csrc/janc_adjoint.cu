@@ -941,13 +941,7 @@ static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const
   if (e == cudaSuccess) e = cudaMemsetAsync(CFy, 0, sizeof(double) * 2 * (size_t)NV * (g.ny + 6) * g.nx, st);
   if (e != cudaSuccess) return e;
   // tiles of 16 faces while that gives at least 8 blocks per SM, else 8
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  const int sms = sm_count();
   auto tiles = [&](int vf, int* nbx, int* ntx_x, int* ntx_y) {
     *ntx_x = (g.nx + 1 + vf - 1) / vf;
     *ntx_y = (g.nx + VLINES - 1) / VLINES;

@@ -259,9 +259,7 @@ __global__ void __launch_bounds__(CHEM_THREADS) k_chem_batch(const BatchReq* __r
 }
 
 cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, cudaStream_t st) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   const int grid = total < sms * 16 ? total : sms * 16;
   if (grid <= 0) return cudaSuccess;
   switch (ns) {
@@ -279,13 +277,7 @@ int chem_blocks(const GridDev& g) { return (int)((g.n + CHEM_THREADS - 1) / CHEM
 // cell is one long dependent FP64 chain; a launch of a few blocks per SM is
 // latency-bound).
 static int chem_threads(long long n) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  const int sms = sm_count();
   for (int t = CHEM_THREADS; t > 32; t /= 2)
     if ((n + t - 1) / t >= 4LL * sms) return t;
   return 32;

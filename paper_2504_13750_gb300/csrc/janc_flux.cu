@@ -134,6 +134,18 @@ static size_t flux_smem_bytes() {
   return sizeof(double) * (size_t)(NV + 4) * LINES * (FC + 5);
 }
 
+int sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int s = 0;
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = s > 0 ? s : 1;
+  }
+  return cache[dev];
+}
+
 // Tiles of FC faces: x tiles first, then y tiles.
 static void tiles_of(const GridDev& g, int fc, int* nbx, int* ntx_x, int* ntx_y, int* total) {
   *ntx_x = (g.nx + 1 + fc - 1) / fc;
@@ -166,13 +178,7 @@ static cudaError_t launch_face_flux_fc(const StateView& S, const unsigned long l
 // fraction of a wave and latency-bound, the blocks win (measured on one
 // GB300: 256 x 32 runs best at 8, 512 x 64 at 16, 4096 x 512 at 32).
 static int flux_tile_faces(const GridDev& g) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  const int sms = sm_count();
   int nbx, ntx_x, ntx_y, total;
   tiles_of(g, 32, &nbx, &ntx_x, &ntx_y, &total);
   if (total >= 8 * sms) return 32;
@@ -204,9 +210,7 @@ static cudaError_t launch_face_flux_batch_t(const BatchReq* reqs, const int* fir
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   const int grid = total < sms * 8 ? total : sms * 8;
   if (grid > 0) k_face_flux_batch<NV><<<grid, LINES * NV, smem, st>>>(reqs, first, nreq, state);
   return cudaGetLastError();

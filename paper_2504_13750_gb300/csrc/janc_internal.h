@@ -67,6 +67,9 @@ cudaError_t launch_rk_update_batch(int ns, int stage, const BatchReq* reqs, cons
                                    int chem, cudaStream_t st);
 cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, cudaStream_t st);
 
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
+
 // Adjoint pieces (janc_adjoint.cu).
 // Scratch of one launch_rhs_vjp: the two alpha cotangents and the per-block
 // arg-max partials of the LF speeds (256-byte aligned start).

@@ -135,9 +135,7 @@ __global__ void k_batch_prep(BatchReq* reqs, int nreq) {
 template <int NS>
 static cudaError_t launch_rk_update_batch_t(int stage, const BatchReq* reqs, const int* first, int nreq, int total,
                                             int chem, cudaStream_t st) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   const int grid = total < sms * 8 ? total : sms * 8;
   if (grid <= 0) return cudaSuccess;
   dim3 blk(UPD_BX, UPD_BY);
@@ -176,13 +174,7 @@ static cudaError_t launch_rk_update_t(int stage, const StateView& Sin, const Sta
   // UPD_BX x UPD_BY blocks while that gives at least 4 blocks per SM; on
   // smaller grids shorter blocks (UPD_BX x 4, 2, 1) spread the cells over
   // all SMs.
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  const int sms = sm_count();
   const long long bxs = (g.nx + UPD_BX - 1) / UPD_BX;
   int by = UPD_BY;
   while (by > 1 && bxs * ((g.ny + by - 1) / by) < 4LL * sms) by /= 2;
