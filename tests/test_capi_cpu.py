@@ -113,3 +113,33 @@ def test_new_entry_points_validate_without_gpu(libjanc):
         janc.janc_server_set_cell_budget(None, 1000)
     with pytest.raises(janc.JancError):                              # null grid
         janc.janc_source_step(None, 1, 1e-8)
+
+
+def test_binding_marshals_host_arrays_and_rejects_the_rest():
+    """The binding only marshals: C-contiguous float64 numpy arrays are host
+    arguments, anything else is refused before the C call (there is no
+    conversion or CPU path), and one call never mixes host and device."""
+    from paper_2504_13750_gb300 import janc
+
+    a = np.zeros((3, 4))
+    ptr, where, keep = janc._arg(a, True)
+    assert where == janc.JANC_HOST and keep is a and ptr.value == a.ctypes.data
+    assert janc._arg(None) == (None, janc.JANC_HOST, None)
+    for bad in (np.zeros((3, 4), dtype=np.float32), np.zeros((4, 3)).T, [0.0, 1.0]):
+        with pytest.raises(ValueError):
+            janc._arg(bad)
+    ro = np.zeros(5)
+    ro.flags.writeable = False
+    janc._arg(ro)                       # read-only input is fine
+    with pytest.raises(ValueError):
+        janc._arg(ro, True)             # but not as an output
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        janc._arg(torch.zeros(4, dtype=torch.float64))   # a CPU tensor is not a device array
+    host = janc._arg(a)
+    fake_dev = (ctypes.c_void_p(1), janc.JANC_DEVICE, object())
+    assert janc._where(host, janc._arg(None)) == janc.JANC_HOST
+    with pytest.raises(ValueError):
+        janc._where(host, fake_dev)
+    assert janc.chem_mode(True) == janc.CHEM_LIE and janc.chem_mode(False) == janc.CHEM_OFF
+    assert janc.chem_mode(janc.CHEM_EXPLICIT) == 3
