@@ -366,7 +366,10 @@ void janc_server_destroy(janc_server_t s);
  * ((nv + 4) nx ny + nv (2 nx ny + nx + ny) doubles plus small tables) does
  * not fit is rejected with JANC_E_INVALID. No allocation of any kind. The
  * first call on each device looks up the array's device address, so make it
- * before any stream capture. All calls share the array: calls that overlap
+ * before any stream capture. That address is kept for the life of the
+ * process: after cudaDeviceReset (or anything else that destroys the primary
+ * context) it is stale, so a process that resets a device must not call this
+ * entry point on that device again. All calls share the array: calls that overlap
  * on the GPU race and must be serialised by the caller. Synchronises
  * cuda_stream before returning; JANC_E_DEVICE if the state's Newton T
  * recovery flagged a bad cell. */

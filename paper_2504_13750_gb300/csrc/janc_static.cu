@@ -16,7 +16,10 @@
 // name is a host-side stand-in, not a device address. The device address is
 // looked up once per device with cudaGetSymbolAddress, with that device
 // current, on the first call made on that device; that first call should
-// therefore come before any stream capture. All calls share the one array
+// therefore come before any stream capture. The address is kept until the
+// process exits: a device reset (which destroys the primary context) leaves
+// it stale, and this entry point must not be used on that device again. All
+// calls share the one array
 // and it keeps the previous call's contents: the LF-speed slot and the status
 // word are cleared on every call, everything else is overwritten before it is
 // read. Calls that overlap on the GPU (different streams or threads without

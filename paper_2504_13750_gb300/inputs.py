@@ -106,19 +106,21 @@ TUBE_Y = {"H2": 0.028, "O2": 0.226, "N2": 0.746}
 
 
 def tube(mech: dict, nx: int, ny: int, Lx: float = 0.05, T0=300.0, p0=ATM, Ti=2000.0, pi=20 * ATM,
-         ign_frac=0.05, Y=None, perturb_seed=None, perturb_amp=0.01):
+         ign_frac=0.05, Y=None, perturb_seed=None, perturb_amp=0.01, aspect=1.0):
     """Detonation-tube initial state (primitive fields, each [ny, nx]).
 
-    Returns dict(T, p, u, v, Y[ns, ny, nx], grid). Cells whose centre lies at
+    Returns dict(T, p, u, v, Y[ns, ny, nx], grid). dx = Lx / nx and
+    dy = aspect * dx (Ly = ny * dy). Cells whose centre lies at
     x < ign_frac * Lx form the igniter. With ``perturb_seed`` the unburnt gas
     gets rho -> rho (1 + amp sin(2 pi m y / Ly + phase)) at fixed p, i.e.
     T -> T / (1 + amp sin(...)), with m in {2..8} and phase in [0, 2 pi) drawn
     from the seed.
     """
     dx = Lx / nx
-    Ly = ny * dx
+    dy = float(aspect) * dx
+    Ly = ny * dy
     x = (np.arange(nx) + 0.5) * dx
-    y = (np.arange(ny) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
     X, Yc = np.meshgrid(x, y)
     ign = X < ign_frac * Lx
     T = np.where(ign, Ti, T0).astype(np.float64)
@@ -133,7 +135,7 @@ def tube(mech: dict, nx: int, ny: int, Lx: float = 0.05, T0=300.0, p0=ATM, Ti=20
     Yf = np.broadcast_to(Yv[:, None, None], (mech["ns"], ny, nx)).copy()
     z = np.zeros((ny, nx))
     return {"T": T, "p": p, "u": z.copy(), "v": z.copy(), "Y": Yf,
-            "grid": grid_dict(nx, ny, dx, dx, [BC_WALL] * 4)}
+            "grid": grid_dict(nx, ny, dx, dy, [BC_WALL] * 4)}
 
 
 def sod(mech: dict, nx: int = 400, R_gas: float = 287.0):

@@ -251,13 +251,33 @@ def janc_status(g):
             "alpha": (s.alpha[0], s.alpha[1])}
 
 
+def _rhs_static_shapes(desc, ns, U, T, L, alpha, device):
+    """Refuses, before the C call, buffers that do not match the grid (the
+    kernels would read or write past their ends) or that sit on another
+    device than `device` (the current one, whose scratch the call uses)."""
+    cells = int(desc.nx) * int(desc.ny)
+    want = {"U": (U, (ns + 3) * cells), "T": (T, cells), "L": (L, (ns + 3) * cells)}
+    for name, (t, n) in want.items():
+        if t is None or t.numel() != n:
+            raise ValueError(f"janc_rhs_static: {name} must hold {n} elements for a {desc.nx} x {desc.ny} grid")
+    if alpha is not None and alpha.numel() < 2:
+        raise ValueError("janc_rhs_static: alpha must hold 2 elements")
+    if any(t is not None and t.device.index != device for t in (U, T, L, alpha)):
+        raise ValueError(f"janc_rhs_static: every tensor must be on the current device (cuda:{device})")
+
+
 def janc_rhs_static(desc, mech: Mechanism, U, T, L, alpha=None, stream=None):
     """Right-hand side with no device allocation (see include/janc.h): for
     callers that cannot allocate, e.g. inside another framework's memory pool.
-    U, T, L (and alpha) must be CUDA tensors the caller owns."""
+    U, T, L (and alpha) must be CUDA tensors the caller owns, on the current
+    device (the one whose copy of the static scratch array the call uses):
+    U and L of (ns + 3) nx ny elements, T of nx ny, alpha of at least 2."""
     args = [_arg(x, True) for x in (U, T, L, alpha)]
     if any(a[2] is not None and a[1] != JANC_DEVICE for a in args):
         raise ValueError("janc_rhs_static takes device tensors only")
+    import torch
+
+    _rhs_static_shapes(desc, mech.ns, U, T, L, alpha, torch.cuda.current_device())
     _check(lib().janc_rhs_static(ctypes.byref(desc), ctypes.byref(mech.c), args[0][0], args[1][0], args[2][0],
                                  args[3][0], ctypes.c_void_p(stream) if stream else None))
 

@@ -143,3 +143,27 @@ def test_binding_marshals_host_arrays_and_rejects_the_rest():
         janc._where(host, fake_dev)
     assert janc.chem_mode(True) == janc.CHEM_LIE and janc.chem_mode(False) == janc.CHEM_OFF
     assert janc.chem_mode(janc.CHEM_EXPLICIT) == 3
+
+
+def test_rhs_static_refuses_mismatched_buffers_before_the_call():
+    """janc_rhs_static's binding checks every buffer's size against the grid
+    and its device against the current one, so that an undersized or foreign
+    tensor never reaches the kernels (checked on stand-ins: no GPU here)."""
+    from paper_2504_13750_gb300 import janc
+
+    class Buf:
+        def __init__(self, n, dev=0):
+            self.n, self.device = n, type("D", (), {"index": dev})()
+
+        def numel(self):
+            return self.n
+
+    d = janc.make_desc(10, 4, 1e-4, 1e-4, [0, 0, 0, 0])
+    ns, cells = 9, 40
+    ok = dict(U=Buf(12 * cells), T=Buf(cells), L=Buf(12 * cells), alpha=Buf(2))
+    janc._rhs_static_shapes(d, ns, device=0, **ok)
+    janc._rhs_static_shapes(d, ns, device=0, **dict(ok, alpha=None))
+    for bad in (dict(U=Buf(12 * cells - 1)), dict(T=Buf(cells + 1)), dict(L=Buf(11 * cells)), dict(alpha=Buf(1)),
+                dict(L=Buf(12 * cells, dev=1)), dict(T=None)):
+        with pytest.raises(ValueError):
+            janc._rhs_static_shapes(d, ns, device=0, **dict(ok, **bad))

@@ -25,8 +25,8 @@ def J():
     return janc
 
 
-def _state(nx, ny, seed, vel=80.0, bc=(0, 0, 0, 0)):
-    st = inputs.tube(H2AIR, nx, ny, perturb_seed=seed)
+def _state(nx, ny, seed, vel=80.0, bc=(0, 0, 0, 0), aspect=1.0):
+    st = inputs.tube(H2AIR, nx, ny, perturb_seed=seed, aspect=aspect)
     rng = np.random.default_rng(seed)
     st["T"] = st["T"] + rng.normal(0.0, 5.0, st["T"].shape)  # unique arg-max of the LF speeds
     st["u"] = rng.normal(0.0, vel, (ny, nx))
@@ -42,9 +42,11 @@ def _dirs(U, n, seed):
     return rng.normal(size=(n,) + U.shape) * (1e-3 * scale)[None]
 
 
-@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (2, 2, 1, 1), (1, 1, 0, 0)])
-def test_rhs_vjp_dot_product(J, bc):
-    st, U = _state(24, 12, 3, bc=bc)
+@pytest.mark.parametrize("bc,aspect", [((0, 0, 0, 0), 1.0), ((2, 2, 1, 1), 1.0), ((1, 1, 0, 0), 1.0),
+                                       ((0, 0, 0, 0), 1.7), ((2, 2, 1, 1), 0.6)])
+def test_rhs_vjp_dot_product(J, bc, aspect):
+    """<mu, J_L v> = <J_L^T mu, v>; the last two grids have dy != dx."""
+    st, U = _state(24, 12, 3, bc=bc, aspect=aspect)
     g = J.Grid.from_grid_dict(H2AIR, st["grid"])
     g.set_state(U, st["T"])
     rng = np.random.default_rng(4)
@@ -59,8 +61,9 @@ def test_rhs_vjp_dot_product(J, bc):
     g.close()
 
 
-def test_trajectory_dot_product_with_chemistry(J):
-    st, U = _state(16, 8, 6, vel=40.0)
+@pytest.mark.parametrize("aspect", [1.0, 1.7])
+def test_trajectory_dot_product_with_chemistry(J, aspect):
+    st, U = _state(16, 8, 6, vel=40.0, aspect=aspect)
     dt = 1e-8
     g = J.Grid.from_grid_dict(H2AIR, st["grid"])
     g.set_state(U, st["T"])

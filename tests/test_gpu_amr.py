@@ -79,11 +79,12 @@ def _compare(J, mech, st, chem, levels, thr, nbuf, every, nsteps, cfl=0.5, dt=0.
     return a, o
 
 
-@pytest.mark.parametrize("sync,levels", [(False, 2), (True, 2), (False, 3)])
-def test_amr_reacting_tube_with_walls(J, sync, levels):
+@pytest.mark.parametrize("sync,levels,aspect", [(False, 2, 1.0), (True, 2, 1.0), (False, 3, 1.0), (False, 2, 1.7)])
+def test_amr_reacting_tube_with_walls(J, sync, levels, aspect):
     """Crossover (Fig. 2a) and synchronous (Fig. 2b) advance; three layers
-    exercise a refined layer whose parent is itself refined."""
-    st = inputs.tube(H2AIR, 64, 16, Lx=0.05 * 64 / 256, perturb_seed=3)
+    exercise a refined layer whose parent is itself refined; the last case has
+    dy = 1.7 dx on every layer."""
+    st = inputs.tube(H2AIR, 64, 16, Lx=0.05 * 64 / 256, perturb_seed=3, aspect=aspect)
     dx = st["grid"]["dx"]
     a, o = _compare(J, H2AIR, st, True, levels=levels, thr=100.0 / dx, nbuf=2, every=2, nsteps=5, sync=sync)
     assert all(o.layers[i].pos for i in range(1, levels + 1))

@@ -68,10 +68,14 @@ def test_set_state_matches_oracle_eos(J):
     assert np.max(np.abs(T2 - st["T"]) / st["T"]) < 1e-12
 
 
-@pytest.mark.parametrize("nx,ny,bc", [(256, 32, [0, 0, 0, 0]), (37, 11, [0, 0, 0, 0]), (45, 7, [2, 2, 1, 1]),
-                                      (33, 9, [1, 1, 0, 0]), (3, 3, [0, 0, 0, 0]), (1, 1, [1, 1, 1, 1])])
-def test_face_fluxes_and_rhs(J, nx, ny, bc):
-    st = inputs.tube(H2AIR, nx, ny, perturb_seed=5)
+@pytest.mark.parametrize("nx,ny,bc,aspect", [(256, 32, [0, 0, 0, 0], 1.0), (37, 11, [0, 0, 0, 0], 1.0),
+                                             (45, 7, [2, 2, 1, 1], 1.0), (33, 9, [1, 1, 0, 0], 1.0),
+                                             (3, 3, [0, 0, 0, 0], 1.0), (1, 1, [1, 1, 1, 1], 1.0),
+                                             (45, 7, [0, 0, 0, 0], 1.7), (33, 9, [2, 2, 1, 1], 0.6)])
+def test_face_fluxes_and_rhs(J, nx, ny, bc, aspect):
+    """Face fluxes, L and alpha of one state; the last two grids have dy != dx
+    (Eq. 4.10 divides the x-flux difference by dx and the y one by dy)."""
+    st = inputs.tube(H2AIR, nx, ny, perturb_seed=5, aspect=aspect)
     st["grid"]["bc"] = bc
     rng = np.random.default_rng(nx * 100 + ny)
     st["u"] = rng.normal(0, 200.0, (ny, nx))
@@ -87,15 +91,17 @@ def test_face_fluxes_and_rhs(J, nx, ny, bc):
     assert rel_err(L, L0) < 1e-10
 
 
-@pytest.mark.parametrize("nx,ny", [(256, 32), (512, 96), (1024, 96)])
-def test_one_step_tube(J, nx, ny):
+@pytest.mark.parametrize("nx,ny,aspect", [(256, 32, 1.0), (512, 96, 1.0), (1024, 96, 1.0), (256, 64, 1.7),
+                                          (256, 64, 0.6)])
+def test_one_step_tube(J, nx, ny, aspect):
     """One step against the oracle at sizes that take each launch shape the
     grid kernels choose by size: 256 x 32 (8-face flux tiles, 32 x 1 update
     blocks, 32-thread chemistry blocks), 512 x 96 (16-face tiles, 32 x 2,
     64 threads), 1024 x 96 (16-face tiles, 32 x 4, 128 threads); the
     4096 x 512 bench grid (32-face tiles, 32 x 8) is covered by
-    test_full_size_config2_two_steps."""
-    st = inputs.tube(H2AIR, nx, ny, Lx=0.05 * nx / 256, perturb_seed=5)
+    test_full_size_config2_two_steps. The 256 x 64 tubes have dy = 1.7 dx and
+    dy = 0.6 dx, so the CFL step takes dx in one and dy in the other."""
+    st = inputs.tube(H2AIR, nx, ny, Lx=0.05 * nx / 256, perturb_seed=5, aspect=aspect)
     U = _cons(H2AIR, st)
     g = _grid(J, H2AIR, st)
     g.set_state(U, st["T"])
@@ -123,6 +129,23 @@ def test_200_steps_tube_config1(J):
     assert rel_err(Tg[None], To[None]) < 1e-8
     # the GPU conserves mass and elements on its own to roundoff
     assert abs(Ug[0].sum() - U[0].sum()) / U[0].sum() < 1e-12
+
+
+def test_200_steps_anisotropic_tube(J):
+    """256 x 64 detonation tube with dy = 1.7 dx, chemistry on, CFL 0.5,
+    200 steps (the 200-step bar on a grid whose two spacings differ)."""
+    st = inputs.tube(H2AIR, 256, 64, perturb_seed=6, aspect=1.7)
+    U = _cons(H2AIR, st)
+    g = _grid(J, H2AIR, st)
+    g.set_state(U, st["T"])
+    t, _ = g.step(200, cfl=0.5, want_time=True)
+    Ug, Tg = g.get_state()
+    Uo, To, s, to, _ = orc.step(H2AIR, st["grid"], U, st["T"], 200, cfl=0.5)
+    assert s == 0
+    assert abs(t - to) / to < 1e-12
+    assert rel_err(Ug, Uo) < 1e-8
+    assert rel_err(Tg[None], To[None]) < 1e-8
+    g.close()
 
 
 @pytest.mark.parametrize("steps", [1, 60])

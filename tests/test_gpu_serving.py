@@ -11,7 +11,9 @@ from paper_2504_13750_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 H2AIR = inputs.load_mechanism("h2air_synth")
-SIZES = [(64, 16, 12), (96, 24, 7), (128, 16, 20), (40, 40, 9), (256, 32, 15), (33, 17, 11), (70, 9, 5)]
+# (nx, ny, steps, dy / dx): two requests have dy != dx
+SIZES = [(64, 16, 12, 1.0), (96, 24, 7, 1.0), (128, 16, 20, 1.7), (40, 40, 9, 1.0), (256, 32, 15, 1.0),
+         (33, 17, 11, 0.6), (70, 9, 5, 1.0)]
 
 
 @pytest.fixture(scope="module")
@@ -28,13 +30,13 @@ def J():
 def _requests():
     rng = np.random.default_rng(11)
     out = []
-    for k, (nx, ny, steps) in enumerate(SIZES):
+    for k, (nx, ny, steps, aspect) in enumerate(SIZES):
         req = {"nx": nx, "ny": ny, "phi": float(rng.uniform(0.5, 1.5)), "p0": float(rng.uniform(0.5, 2.0)) * inputs.ATM,
                "steps": steps}
         st = inputs.request_state(H2AIR, req)
-        if k % 2:
+        if k % 2 or aspect != 1.0:
             st = inputs.tube(H2AIR, nx, ny, p0=req["p0"], pi=20 * req["p0"], Y=inputs.h2air_Y(H2AIR, req["phi"]),
-                             perturb_seed=k)
+                             perturb_seed=k, aspect=aspect)
         out.append((req, st))
     return out
 
@@ -145,8 +147,11 @@ def test_cell_budget_bounds_the_active_set(J, max_skip_s):
         assert np.array_equal(Ua, Um) and np.array_equal(Ta, Tm)
 
 
-def test_served_request_matches_oracle(J):
-    req, st = _requests()[0]
+@pytest.mark.parametrize("k", [0, 2])
+def test_served_request_matches_oracle(J, k):
+    """Requests 0 (dy = dx) and 2 (dy = 1.7 dx) served alone against the oracle."""
+    req, st = _requests()[k]
+    assert st["grid"]["dy"] == SIZES[k][3] * st["grid"]["dx"]
     (U, T), = _serve(J, [(req, st)])
     U0 = orc.prim_to_cons(H2AIR, st["T"], st["p"], st["u"], st["v"], st["Y"])
     Uo, To, s, _, _ = orc.step(H2AIR, st["grid"], U0, st["T"], req["steps"], cfl=0.5)
