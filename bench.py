@@ -5,10 +5,13 @@ CFL 0.5, seeded 1 % density perturbation), one JSON line on stdout.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 A step is one advance_one_step (CFL dt, 3 LF-split WENO5 RK stages with
-Newton T recovery, point-implicit chemistry) over the whole grid. Each rank
-runs its own replica of the tube (the solve is independent per GPU: weak
-scaling, no data-path collective); `value` is the sum over ranks of
-cells x steps / the max over ranks of the device-timed region.
+Newton T recovery, point-implicit chemistry) over the whole grid. By default
+each rank runs its own replica of the tube (the solve is independent per GPU:
+weak scaling, no data-path collective); `value` is the sum over ranks of
+cells x steps / the max over ranks of the device-timed region. With --split
+the ranks share one tube as x-slabs (Sec. 4.4: halo exchange and LF-speed
+max through NCCL after every state-producing phase; strong scaling); `value`
+is the tube's cells x steps / the max over ranks of the timed region.
 
 `--impl reference` times the CPU FP64 oracle (the plain restatement of the
 method used by the tests) on the host cores on a slab of the same workload.
@@ -189,7 +192,10 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 def serve_stream(janc, mech_c, reqs, states, arrivals, max_active, pool_bytes, stream, cell_budget=0, max_skip_s=0.0):
     """Replays the request stream in real time through one server: a request
-    is submitted once its arrival time has passed. Returns per-request
+    is submitted once its arrival time has passed. Between arrivals the
+    server runs on its own (janc_server_run_until: macro-steps until a
+    request finishes or the next arrival is due) and returns the ids of the
+    requests that finished; nothing polls the others. Returns per-request
     latencies (completion - arrival, s) and the makespan."""
     s = janc.janc_server_create(mech_c, chemistry=True, pool_bytes=pool_bytes, max_active=max_active,
                                 stream=stream.cuda_stream)
@@ -197,33 +203,37 @@ def serve_stream(janc, mech_c, reqs, states, arrivals, max_active, pool_bytes, s
         janc.janc_server_set_cell_budget(s, cell_budget, max_skip_s)
     try:
         n = len(reqs)
-        ids = [None] * n
+        index = {}
         done_t = [None] * n
         nxt = 0
         t0 = time.perf_counter()
         finished = 0
+        idle = True
         while finished < n:
             now = time.perf_counter() - t0
             while nxt < n and arrivals[nxt] <= now:
                 st, rq = states[nxt], reqs[nxt]
                 g = st["grid"]
                 d = janc.make_desc(g["nx"], g["ny"], g["dx"], g["dy"], g["bc"], chemistry=True)
-                ids[nxt] = janc.janc_server_submit(s, d, st["T"], st["p"], st["u"], st["v"], st["Y"], rq["steps"],
-                                                   cfl=CFL)
+                index[janc.janc_server_submit(s, d, st["T"], st["p"], st["u"], st["v"], st["Y"], rq["steps"],
+                                              cfl=CFL)] = nxt
                 nxt += 1
-            info = janc.janc_server_run(s, 1)
+                idle = False
+            if idle and nxt < n:  # nothing submitted and unfinished: wait for the next arrival
+                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+                continue
+            budget = arrivals[nxt] - (time.perf_counter() - t0) if nxt < n else 1e9
+            ids, info = janc.janc_server_run_until(s, max_wall_s=max(budget, 0.0), cap=n)
             now = time.perf_counter() - t0
-            for k in range(nxt):
-                if done_t[k] is None and ids[k] is not None:
-                    r = janc.janc_server_poll(s, ids[k])
-                    if r["state"] in (janc.REQ_DONE, janc.REQ_FAILED):
-                        if r["state"] == janc.REQ_FAILED or r["status"] != 0:
-                            raise RuntimeError(f"request {k} failed with status {r['status']}")
-                        done_t[k] = now
-                        finished += 1
-                        janc.janc_server_fetch(s, ids[k])
-            if info["n_active"] == 0 and info["n_queued"] == 0 and info["n_copying"] == 0 and nxt < n:
-                time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.01)))
+            for rid in ids:
+                k = index[rid]
+                r = janc.janc_server_poll(s, rid)
+                if r["state"] == janc.REQ_FAILED or r["status"] != 0:
+                    raise RuntimeError(f"request {k} failed with status {r['status']}")
+                done_t[k] = now
+                finished += 1
+                janc.janc_server_fetch(s, rid)
+            idle = info["n_active"] == 0 and info["n_queued"] == 0 and info["n_copying"] == 0
         lat = [done_t[k] - arrivals[k] for k in range(n)]
         return lat, max(done_t) - arrivals[0]
     finally:
@@ -429,6 +439,34 @@ def whole_job_rate(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
+def run_split_leg(janc, stream, n_slabs=4, steps=10, warm=3):
+    """The tube cut into n_slabs x-slabs on one GPU (janc_split_*, Sec. 4.4):
+    the rate over `steps` CFL steps, for comparison with the undivided grid's
+    (the exchange's cost: one pack launch per slab and state-producing phase,
+    and the smaller launches of each slab)."""
+    import torch
+
+    mech, st = tube_state()
+    s = janc.Split(mech, NX, NY, st["grid"]["dx"], st["grid"]["dy"], st["grid"]["bc"], n_slabs, chemistry=True,
+                   stream=stream)
+    s.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    s.step(warm, cfl=CFL)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps, cfl=CFL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st_ = s.status()
+    cols = s.columns()
+    s.close()
+    if st_["status"] != 0:
+        raise RuntimeError(f"split: device status {st_['status']:#x}")
+    return {"workload": workload_name(), "slabs": n_slabs, "columns": cols, "steps": steps,
+            "value": NX * NY * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps}
+
+
 def run_config1(janc, stream, with_cpu=True):
     """The 256 x 32 tube of config 1, all 200 steps at CFL 0.5: on the GPU
     (one janc_step call, CUDA events) and, on rank 0, through the oracle on
@@ -488,9 +526,20 @@ def run_ours(args):
                "single_thread": {"value": v1, "unit": UNIT, "sample": f"1 step of a {NX}x32 slab on 1 thread"}}
 
     stream = torch.cuda.Stream()
-    g = janc.Grid(mech, NX, NY, st["grid"]["dx"], st["grid"]["dy"], st["grid"]["bc"], chemistry=True,
-                  stream=stream)
-    g.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    if args.split:
+        # this rank's x-slab of the one tube; halos and alpha through NCCL
+        from paper_2504_13750_gb300 import slab
+
+        comm = slab.TorchExchange(rank, world, periodic=False)
+        g = slab.Slab(mech, st["grid"], rank, world, comm, chemistry=True, stream=stream)
+        x0, nxl = g.columns()
+        cut = lambda a: np.ascontiguousarray(a[..., x0:x0 + nxl])  # noqa: E731
+        g.set_primitive(cut(st["T"]), cut(st["p"]), cut(st["u"]), cut(st["v"]), cut(st["Y"]))
+    else:
+        nxl = NX
+        g = janc.Grid(mech, NX, NY, st["grid"]["dx"], st["grid"]["dy"], st["grid"]["bc"], chemistry=True,
+                      stream=stream)
+        g.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
     g.step(args.warmup, cfl=CFL)
     torch.cuda.synchronize()
 
@@ -514,15 +563,17 @@ def run_ours(args):
     if stt["status"] != 0:
         raise RuntimeError(f"device status {stt['status']:#x} after the timed region")
     ms = reduce_max(pg, ms)
-    cells = NX * NY
-    value = whole_job_rate(world, cells * args.steps, ms * 1e-3)
+    cells = nxl * NY  # this rank's cells
+    # replicas: every rank's tube counts; split: the ranks share one tube
+    value = (NX * NY * args.steps / (ms * 1e-3) if args.split
+             else whole_job_rate(world, cells * args.steps, ms * 1e-3))
 
     # ---- end to end through the C ABI with pinned host buffers ----
     nv = g.nv
     e2e = None
     if not args.no_e2e:
-        Uh = torch.empty((nv, NY, NX), dtype=torch.float64, pin_memory=True).numpy()
-        Th = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True).numpy()
+        Uh = torch.empty((nv, NY, nxl), dtype=torch.float64, pin_memory=True).numpy()
+        Th = torch.empty((NY, nxl), dtype=torch.float64, pin_memory=True).numpy()
         janc.janc_get_state(g.handle, Uh, Th)
         e2e_steps = max(5, args.steps // 2)
         torch.cuda.synchronize()
@@ -530,9 +581,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             ta = time.perf_counter()
-            janc.janc_set_state(g.handle, Uh, Th)
+            g.set_state(Uh, Th)
             tb = time.perf_counter()
-            janc.janc_step(g.handle, 1, cfl=CFL)
+            g.step(1, cfl=CFL)
             tc = time.perf_counter()
             janc.janc_get_state(g.handle, Uh, Th)
             parts += (tb - ta, tc - tb, time.perf_counter() - tc)
@@ -540,14 +591,15 @@ def run_ours(args):
         e2e_s = reduce_max(pg, e2e_s)
         nb = int(Uh.nbytes + Th.nbytes)
         parts_ms = parts / e2e_steps * 1e3
-        e2e = {"value": whole_job_rate(world, cells * e2e_steps, e2e_s), "unit": UNIT,
+        e2e_rate = (NX * NY * e2e_steps / e2e_s if args.split else whole_job_rate(world, cells * e2e_steps, e2e_s))
+        e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": e2e_steps,
                "ms_per_step": {"set_state_h2d": float(parts_ms[0]), "step": float(parts_ms[1]),
                                "get_state_d2h": float(parts_ms[2])}}
 
     # ---- roofline of the dominant kernel (face fluxes: FP64-pipe bound) ----
     ff_ms, ff_n = prof["face_flux"]
-    faces = (NX + 1) * NY + NX * (NY + 1)
+    faces = (nxl + 1) * NY + nxl * (NY + 1)
     flops_launch = nv * faces * (2 * weno_flops() + 1)
     achieved = flops_launch / (ff_ms / ff_n * 1e-3) / 1e12
     peaks = measured_peaks()
@@ -573,10 +625,11 @@ def run_ours(args):
                for k, v in prof.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if args.split else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(), "nx": NX, "ny": NY, "cells": cells, "species": 9, "reactions": 19,
-                   "cfl": CFL, "parallelism": f"replicas x{world}",
+                   "cfl": CFL, "parallelism": f"x-slab x{world}" if args.split else f"replicas x{world}",
                    "l2": f"inputs larger than L2 (129 MB): each state buffer is 16 planes x {cells} cells = {16 * 8 * cells / 1e6:.0f} MB"},
         "e2e": e2e,
         "roofline": roof,
@@ -592,6 +645,10 @@ def run_ours(args):
         line["adjoint"] = run_adjoint(janc, stream)
     if rank == 0:
         line["config1"] = run_config1(janc, stream, with_cpu=world == 1 and not args.no_cpu_baseline)
+    if rank == 0 and world == 1 and not args.no_split:
+        sp = run_split_leg(janc, stream)
+        sp["vs_undivided"] = sp["value"] / value
+        line["split"] = sp
     if rank == 0 and not args.no_amr:
         line["amr"] = run_amr(janc, stream)
     if rank == 0 and not args.no_inverse:
@@ -618,6 +675,8 @@ def run_only(args):
         out = run_inverse(janc, iters=args.leg_steps or 15)
     elif args.only == "serving":
         out = run_serving(janc, stream, args.serving_requests, tuple(args.serving_steps))
+    elif args.only == "split":
+        out = run_split_leg(janc, stream, steps=args.leg_steps or 10)
     else:
         out = run_amr(janc, stream, steps=args.leg_steps or 40)
     print(json.dumps(out), flush=True)
@@ -636,12 +695,15 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-inverse", action="store_true")
+    ap.add_argument("--no-split", action="store_true", help="skip the 4-slab split leg (N = 1)")
+    ap.add_argument("--split", action="store_true",
+                    help="ranks share one tube as x-slabs (strong scaling) instead of running replicas")
     ap.add_argument("--serving-requests", type=int, default=64,
                     help="requests in the serving leg (the full stream is 256 with --serving-steps 100 1000)")
     ap.add_argument("--serving-steps", type=int, nargs=2, default=(50, 150))
     ap.add_argument("--nx", type=int, default=NX, help="tube cells along x (default: the 4096 x 512 workload)")
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--only", choices=("adjoint", "amr", "inverse", "serving"), default=None,
+    ap.add_argument("--only", choices=("adjoint", "amr", "inverse", "serving", "split"), default=None,
                     help="run one side leg alone and print its JSON object (for profiling)")
     ap.add_argument("--leg-steps", type=int, default=None,
                     help="with --only: adjoint trajectory steps (checkpoint every steps/10) or timed AMR base steps")

@@ -45,6 +45,7 @@ extern "C" {
 #define JANC_E_CUDA (-3)        /* a CUDA runtime call failed */
 #define JANC_E_NOMEM (-4)       /* device allocation failed or workspace too small */
 #define JANC_E_DEVICE (-5)      /* the device status word reports a failure */
+#define JANC_E_EXCHANGE (-6)    /* an x-slab exchange callback reported a failure */
 
 /* Boundary kinds (user boundary hooks of Sec. 4.3 reduced to three forms). */
 #define JANC_BC_WALL 0      /* slip wall: mirror ghosts, wall-normal momentum negated */
@@ -214,19 +215,22 @@ int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
  * implicit chemistry), with checkpoint-and-recompute: the state is stored
  * every ckpt_every steps and each segment is recomputed (bit for bit) during
  * the reverse sweep. Memory: ceil(n/ckpt_every) + 4 ckpt_every + 1 states of
- * (nv + 4) planes, 7 cotangent arrays and the face-contribution buffers; see
- * janc_adjoint_workspace_bytes. The continuous adjoint of Sec. 6.1 (Eq. 6.5)
+ * (nv + 4) planes (twice the 4 ckpt_every + 1 when there is more than one
+ * segment: the next segment is recomputed on a second stream while the
+ * current one is reversed), 7 cotangent arrays and the face-contribution
+ * buffers; see janc_adjoint_workspace_bytes. The continuous adjoint of Sec. 6.1 (Eq. 6.5)
  * is replaced by this exact discrete one.
  * ---------------------------------------------------------------------- */
 #define JANC_LOSS_ENDWALL_P 0  /* L = sum_n dt * mean_j p(nx-1, j) of U^{n+1} */
 #define JANC_LOSS_SEEDED 1     /* L = <seed, U^N> (seed: nv planes) */
 
 /* Device bytes janc_step_adjoint needs as workspace: checkpoints every
- * ckpt_every steps, the stage states of one segment of ckpt_every steps,
- * cotangent and face buffers. The forward writes the last segment's stages
- * directly, so the reverse recomputes every segment but the last; with
- * ckpt_every >= n_steps the whole trajectory is kept and nothing is
- * recomputed (about (4 n_steps + 2) (nv + 4) nx ny doubles). */
+ * ckpt_every steps, the stage states of one segment of ckpt_every steps (two
+ * such stores when n_steps > ckpt_every), cotangent and face buffers. The
+ * forward writes the last segment's stages directly, so the reverse
+ * recomputes every segment but the last; with ckpt_every >= n_steps the
+ * whole trajectory is kept and nothing is recomputed (about
+ * (4 n_steps + 2) (nv + 4) nx ny doubles). */
 int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, size_t* bytes);
 
 /* From the grid's current state U^0 (set beforehand), run n_steps fixed-dt
@@ -340,6 +344,19 @@ int janc_server_submit(janc_server_t s, const janc_grid_desc* d, const double* T
  * Asynchronous with respect to the GPU except for admission bookkeeping. */
 int janc_server_run(janc_server_t s, int macro_steps, janc_server_info* info);
 
+/* Run macro-steps as janc_server_run does until a request finishes: returns
+ * once at least one request is done or failed that no earlier call returned
+ * (its id in done_ids[0 .. *n_done), at most cap of them; any others come
+ * with the next call), or after max_macro_steps macro-steps, or once
+ * max_wall_s seconds of host time have passed since the call (checked after
+ * each macro-step; give the time to the next expected arrival), or when
+ * nothing is active or queued (after the last results have reached host
+ * memory). At most two macro-steps are in flight on the GPU, so a finished
+ * request is seen within about one macro-step. Lets a caller serve a stream
+ * without polling every request. */
+int janc_server_run_until(janc_server_t s, int max_macro_steps, double max_wall_s, int* done_ids, int cap,
+                          int* n_done, janc_server_info* info);
+
 /* State and timing of one request. */
 int janc_server_poll(janc_server_t s, int id, janc_request_info* r);
 
@@ -350,6 +367,92 @@ int janc_server_fetch(janc_server_t s, int id, double* U, double* T);
 
 /* Release the server (waits for its streams). */
 void janc_server_destroy(janc_server_t s);
+
+/* ------------------------------------------------------------------------
+ * x-slab domain decomposition (Sec. 4.4, Fig. 3). The domain's nx columns
+ * are cut into slabs of whole columns. Each slab is a grid whose x sides
+ * shared with a neighbour read their 3 ghost columns from halo buffers; its
+ * y sides and the domain's outer x sides keep the physical boundaries of the
+ * descriptor, and a periodic x axis joins the last slab to the first. After
+ * every phase of a step whose output state a neighbour's next face fluxes
+ * read (RK stages 1 and 2, the step's final state) and after a state load,
+ * the exchange fills each neighbour's halo with the slab's 3 edge columns of
+ * all ns + 7 stored planes and makes the LF speeds of Eq. 4.11 the max over
+ * all slabs (the CFL dt follows). The slabs together give the undivided
+ * grid's result bit for bit: every face sees the same stencil values and
+ * alpha, every cell runs the same arithmetic, and a max is exact. The
+ * adjoint, the server and AMR take whole grids only.
+ * ---------------------------------------------------------------------- */
+
+/* Columns [*x0, *x0 + *nx_local) of slab k of n_slabs over nx columns: the
+ * first nx % n_slabs slabs take one column more. JANC_E_INVALID unless
+ * every slab has at least 3 columns (a halo is 3 columns of one neighbour).
+ * Host arithmetic only. */
+int janc_slab_partition(int nx, int n_slabs, int k, int* x0, int* nx_local);
+
+/* Doubles in one halo buffer of a slab of the domain d: (ns + 7) ny 3,
+ * laid out [plane][ny][3] (planes: the nv conserved variables, T, u, v, p;
+ * column c of a low-side buffer is ghost column c - 3 of the receiving slab,
+ * of a high-side buffer its column nx_local + c). */
+int janc_slab_halo_doubles(const janc_grid_desc* d, const janc_mechanism* m, size_t* count);
+
+/* Exchange callback of a stand-alone slab (one slab per process or rank).
+ * Before each call the library has enqueued on cuda_stream the packing of
+ * the slab's columns 0..2 into send_lo and nx_local-3..nx_local-1 into
+ * send_hi (shared sides only) and the copy of the slab's LF speeds into
+ * alpha2. The callback must enqueue, on cuda_stream or in a way ordered
+ * with it (e.g. NCCL on that stream, or synchronously), the transfer of the
+ * low neighbour's send_hi into recv_lo and of the high neighbour's send_lo
+ * into recv_hi, and the replacement of alpha2[0..1] by the max over all
+ * slabs (bit patterns of non-negative doubles: an unsigned 64-bit max).
+ * It must not reuse send buffers before those transfers are done. Returns
+ * 0, or non-zero to fail the library call with JANC_E_EXCHANGE. */
+typedef int (*janc_exchange_fn)(void* user, void* cuda_stream);
+
+typedef struct {
+  double* send_lo;             /* device, janc_slab_halo_doubles each; the  */
+  double* send_hi;             /* buffers of a side without a neighbour may */
+  double* recv_lo;             /* be NULL. recv_lo / recv_hi are the slab's */
+  double* recv_hi;             /* halos, read by every face-flux launch.    */
+  unsigned long long* alpha2;  /* device, 2 values */
+  janc_exchange_fn fn;
+  void* user;                  /* passed to fn */
+} janc_slab_exchange;
+
+/* Create slab [x0, x0 + nx_local) of the domain d (nx_local >= 3) as a grid
+ * of nx_local x d->ny cells: janc_set_state / janc_set_state_primitive take
+ * and janc_get_state gives the slab's own arrays, and janc_step runs the
+ * step with the exchange of *x after every state-producing phase (the loads
+ * run it once too). Buffers of *x are owned by the caller and must stay
+ * valid until janc_destroy_grid. workspace as janc_create_grid, sized by
+ * janc_workspace_bytes of d with nx = nx_local (NULL: allocated here). */
+int janc_slab_create(const janc_grid_desc* d, const janc_mechanism* m, int x0, int nx_local,
+                     const janc_slab_exchange* x, void* workspace, size_t workspace_bytes, void* cuda_stream,
+                     janc_grid_t* out);
+
+/* Single-process split: the domain d cut into n_slabs slabs on the current
+ * device (janc_slab_partition), all on cuda_stream. The slabs share one set
+ * of alpha slots (so every update kernel's max already covers all slabs) and
+ * exchange halos by a pack kernel that writes each slab's edge columns
+ * straight into its neighbours' halo buffers. Set-up allocates each slab's
+ * workspace (janc_workspace_bytes of its own size plus two halos). */
+typedef struct janc_split_s* janc_split_t;
+int janc_split_create(const janc_grid_desc* d, const janc_mechanism* m, int n_slabs, void* cuda_stream,
+                      janc_split_t* out);
+/* Whole-domain state in, as janc_set_state / janc_set_state_primitive. */
+int janc_split_set_state(janc_split_t s, const double* U, const double* T0, int where);
+int janc_split_set_state_primitive(janc_split_t s, const double* T, const double* p, const double* u, const double* v,
+                                   const double* Y, int where);
+/* n_steps steps of all slabs in lockstep, as janc_step. */
+int janc_split_step(janc_split_t s, int n_steps, double dt, double cfl, double* t_out, double* dt_last_out);
+/* Whole-domain state out, as janc_get_state (status: OR over the slabs). */
+int janc_split_get_state(janc_split_t s, double* U, double* T, int where);
+/* Status as janc_status: OR of the slabs' status words, slab 0's clock. */
+int janc_split_status(janc_split_t s, janc_status_info* info);
+/* Handle of slab k (owned by the split: never pass it to janc_destroy_grid),
+ * e.g. for janc_profile. */
+int janc_split_slab(janc_split_t s, int k, janc_grid_t* slab);
+void janc_split_destroy(janc_split_t s);
 
 /* Size of the device array behind janc_rhs_static (32 MiB per GPU). */
 #define JANC_STATIC_SCRATCH_BYTES (32u << 20)

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libjanc.so")
-SOURCES = ["janc_flux.cu", "janc_update.cu", "janc_chem.cu", "janc_capi.cu", "janc_probe.cu", "janc_static.cu", "janc_server.cu", "janc_adjoint.cu", "janc_amr.cu"]
+SOURCES = ["janc_flux.cu", "janc_update.cu", "janc_chem.cu", "janc_capi.cu", "janc_probe.cu", "janc_static.cu", "janc_server.cu", "janc_adjoint.cu", "janc_amr.cu",
+           "janc_slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -44,6 +45,9 @@ def up_to_date() -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link libjanc.so if it is missing or older than its sources."""
+    from . import mech_codegen
+
+    mech_codegen.generate()  # rewrites csrc/janc_mech_fixed.cuh only when its text changes
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)

@@ -23,6 +23,7 @@
 
 #include "../../include/janc.h"
 #include "janc_device.cuh"
+#include "janc_grid.h"
 #include "janc_internal.h"
 
 using namespace janc;
@@ -40,16 +41,13 @@ int fail_cuda(cudaError_t e, const char* where) {
   return JANC_E_CUDA;
 }
 
-constexpr int CHUNK = 256;  // steps per alpha-slot chunk
-constexpr int SLOTS_PER_STEP = 5;
-
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-struct Layout {
-  size_t state, fx, gy, alpha, clock, status, mech, total;
-};
+}  // namespace
 
-Layout layout_of(int nx, int ny, int nv) {
+namespace janc {
+
+Layout layout_of(int nx, int ny, int nv, bool halos) {
   Layout L;
   const size_t n = (size_t)nx * ny;
   L.state = align256(sizeof(double) * (size_t)(nv + 4) * n);
@@ -59,9 +57,17 @@ Layout layout_of(int nx, int ny, int nv) {
   L.clock = align256(sizeof(double) * 2);
   L.status = align256(sizeof(int));
   L.mech = align256(sizeof(MechDev));
-  L.total = 3 * L.state + L.fx + L.gy + L.alpha + L.clock + L.status + L.mech;
+  L.halo = halos ? align256(sizeof(double) * (size_t)(nv + 4) * ny * 3) : 0;
+  L.total = 3 * L.state + L.fx + L.gy + L.alpha + L.clock + L.status + L.mech + 2 * L.halo;
   return L;
 }
+
+int fail_cuda_at(cudaError_t e, const char* where) { return fail_cuda(e, where); }
+int fail_msg(int code, const char* msg) { return fail(code, msg); }
+
+}  // namespace janc
+
+namespace {
 
 int check_desc(const janc_grid_desc* d, const janc_mechanism* m) {
   if (!d || !m) return fail(JANC_E_INVALID, "null descriptor");
@@ -166,37 +172,6 @@ int build_mech_table(const janc_mechanism* m, MechDev* h) { return build_mech(m,
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace janc
 
-struct janc_grid_s {
-  janc_grid_desc d;
-  int ns, nv;
-  long long n;
-  GridDev gd;
-  Layout L;
-  char* ws;
-  bool owns_ws;
-  cudaStream_t stream;
-  double* S[3];
-  double* Fx;
-  double* Gy;
-  unsigned long long* alpha;
-  double* clock2;
-  int* status;
-  MechDev* mech;
-  int steps_done;
-  // trajectory of the last janc_adjoint_forward, for janc_adjoint_reverse
-  struct AdjPending {
-    bool valid = false;
-    int n_steps = 0, ckpt_every = 1, loss_kind = 0;
-    double dt = 0.0;
-    char* ws = nullptr;
-    bool own = false;
-  } adj;
-  // per-kernel event timing (janc_profile)
-  bool prof_on = false;
-  struct Mark { cudaEvent_t a, b; int cls; };
-  std::vector<Mark> marks;
-  std::vector<cudaEvent_t> pool;
-};
 
 namespace {
 
@@ -244,23 +219,13 @@ GridParts grid_parts(janc_grid_t g) {
 }
 }  // namespace janc
 
-extern "C" {
-
-const char* janc_last_error(void) { return g_err.c_str(); }
-
-int janc_workspace_bytes(const janc_grid_desc* d, const janc_mechanism* m, size_t* bytes) {
-  int rc = check_desc(d, m);
-  if (rc) return rc;
-  if (!bytes) return fail(JANC_E_INVALID, "null output");
-  *bytes = layout_of(d->nx, d->ny, m->ns + 3).total;
-  return JANC_OK;
-}
-
-int janc_create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* workspace, size_t workspace_bytes,
-                     void* cuda_stream, janc_grid_t* out) {
+int janc::create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* workspace, size_t workspace_bytes,
+                      void* cuda_stream, const SlabOpts* so, janc_grid_s** out) {
   int rc = check_desc(d, m);
   if (rc) return rc;
   if (!out) return fail(JANC_E_INVALID, "null output handle");
+  if (so && (so->halo_lo || so->halo_hi) && d->nx < 3)
+    return fail(JANC_E_INVALID, "a slab needs nx >= 3 (its halo is 3 columns of its neighbour)");
   MechDev hm;
   rc = build_mech(m, &hm);
   if (rc) return rc;
@@ -272,7 +237,8 @@ int janc_create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* wor
   g->ns = m->ns;
   g->nv = m->ns + 3;
   g->n = (long long)d->nx * d->ny;
-  g->L = layout_of(d->nx, d->ny, g->nv);
+  const bool own_halos = so && ((so->halo_lo && !so->halo_ext[0]) || (so->halo_hi && !so->halo_ext[1]));
+  g->L = layout_of(d->nx, d->ny, g->nv, own_halos);
   g->stream = (cudaStream_t)cuda_stream;
   GridDev& gd = g->gd;
   gd.nx = d->nx;
@@ -286,6 +252,8 @@ int janc_create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* wor
   gd.eps4 = 4.0 * g->d.weno_eps;
   gd.newton_tol = g->d.newton_tol;
   gd.newton_maxit = g->d.newton_maxit;
+  gd.halo_lo = gd.halo_hi = nullptr;
+  gd.chem_fixed = fixed_structure(m) ? 1 : 0;
   if (workspace) {
     if (workspace_bytes < g->L.total || ((uintptr_t)workspace & 255u)) {
       delete g;
@@ -309,10 +277,31 @@ int janc_create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* wor
   g->clock2 = (double*)p; p += g->L.clock;
   g->status = (int*)p; p += g->L.status;
   g->mech = (MechDev*)p; p += g->L.mech;
+  if (so) {
+    // a slab: shared x sides read their ghosts from halo buffers
+    const bool side[2] = {so->halo_lo, so->halo_hi};
+    for (int k = 0; k < 2; ++k) {
+      if (!side[k]) continue;
+      g->halo_side[k] = true;
+      if (so->halo_ext[k]) {
+        g->halo[k] = so->halo_ext[k];
+      } else {
+        g->halo[k] = (double*)p;
+        p += g->L.halo;
+      }
+      gd.bc[k] = BC_HALO;
+    }
+    gd.halo_lo = g->halo[0];
+    gd.halo_hi = g->halo[1];
+    if (so->alpha) {
+      g->alpha = so->alpha;
+      g->alpha_shared = true;
+    }
+  }
   cudaError_t e = cudaMemcpyAsync(g->mech, &hm, sizeof(MechDev), cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->clock2, 0, 2 * sizeof(double), g->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(g->status, 0, sizeof(int), g->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g->alpha, 0, g->L.alpha, g->stream);
+  if (e == cudaSuccess && !g->alpha_shared) e = cudaMemsetAsync(g->alpha, 0, g->L.alpha, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) {
     if (g->owns_ws) cudaFree(g->ws);
@@ -324,6 +313,134 @@ int janc_create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* wor
   return JANC_OK;
 }
 
+// The step loop of janc_step (advance_one_step of Sec. 4.3, n times) over
+// ng grids advanced in lockstep. Per step, with the alpha slots a0 = U^n
+// (dt source), aH = after the first half chemistry (Strang order only), a1,
+// a2 = stages, a3 = U^*, a4 = U^{n+1} (the next step's a0):
+//   [Strang: chem(dt/2) -> aH, exchange]
+//   flux(S0) -> update1 -> S1, a1, exchange
+//   flux(S1) -> update2 -> S2, a2, exchange
+//   flux(S2) -> update3 -> S0 (a3 with chemistry, else a4) [no chemistry: exchange]
+//   [chemistry: chem -> S0, a4, exchange]
+// Each phase is launched for every grid before the exchange; the exchange
+// runs only between phases, so every face-flux launch of a slab reads halos
+// and alpha values that all slabs finished. A stage-3 output that chemistry
+// consumes next needs no exchange: chemistry is per cell and reads a0 only.
+int janc::step_grids(janc_grid_s* const* gs, int ng, Exchanger* ex, int n_steps, double dt, double cfl,
+                     double* t_out, double* dt_last_out) {
+  if (!gs || ng < 1 || !gs[0]) return fail(JANC_E_INVALID, "null grid");
+  if (n_steps < 0) return fail(JANC_E_INVALID, "n_steps < 0");
+  if ((dt > 0.0) == (cfl > 0.0)) return fail(JANC_E_INVALID, "give exactly one of dt > 0 or cfl > 0");
+  janc_grid_s* g = gs[0];  // alpha slots, stream and clock of the lockstep set
+  StepCtl ctl;
+  ctl.dt_fixed = dt > 0.0 ? dt : 0.0;
+  ctl.cfl = cfl > 0.0 ? cfl : 0.0;
+  ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
+  const bool strang = g->d.chemistry == JANC_CHEM_STRANG;
+  ctl.chem_frac = strang ? 0.5 : 1.0;
+  ctl.source = g->d.chemistry == JANC_CHEM_EXPLICIT ? 1 : 0;
+  double t_before = 0.0;
+  if (t_out) {
+    cudaError_t e = cudaMemcpyAsync(&t_before, g->clock2, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "janc_step clock read");
+  }
+  const bool chem = g->d.chemistry == JANC_CHEM_LIE || g->d.chemistry == JANC_CHEM_STRANG;
+  cudaStream_t st = g->stream;
+  // one phase: `launch(grid)` for every grid, then (xk >= 0) the exchange of
+  // state buffer xk with alpha slot xa
+  auto phase = [&](int cls, auto&& launch, int xk, unsigned long long* xa) -> int {
+    for (int q = 0; q < ng; ++q) {
+      janc_grid_s* h = gs[q];
+      const cudaError_t e = timed(h, cls, [&] { return launch(h); });
+      if (e != cudaSuccess) return fail_cuda(e, "step launch");
+    }
+    if (ex && xk >= 0) return ex->after(xk, xa);
+    return JANC_OK;
+  };
+  int done = 0;
+  while (done < n_steps) {
+    const int nc = (n_steps - done) < CHUNK ? (n_steps - done) : CHUNK;
+    cudaError_t e = cudaMemsetAsync(g->alpha + 2, 0, sizeof(unsigned long long) * 2 * SLOTS_PER_STEP * nc, st);
+    if (e != cudaSuccess) return fail_cuda(e, "alpha reset");
+    for (int s = 0; s < nc; ++s) {
+      unsigned long long* a0 = g->alpha + 2 * (SLOTS_PER_STEP * s);
+      unsigned long long* aH = a0 + 2;
+      unsigned long long* a1 = a0 + 4;
+      unsigned long long* a2 = a0 + 6;
+      unsigned long long* a3 = a0 + 8;
+      unsigned long long* a4 = a0 + 10;
+      unsigned long long* aF = a0;  // alpha of the flux stage-1 input
+      int rc = JANC_OK;
+      if (strang) {
+        rc = phase(2, [&](janc_grid_s* h) { return launch_chem(h->ns, sv(h, 0), h->gd, h->mech, ctl, a0, aH, h->status, h->stream); },
+                   0, aH);
+        if (rc) return rc;
+        aF = aH;
+      }
+      rc = phase(0, [&](janc_grid_s* h) { return launch_face_flux(h->nv, sv(h, 0), aF, h->Fx, h->Gy, h->gd, h->stream); },
+                 -1, nullptr);
+      if (!rc)
+        rc = phase(1, [&](janc_grid_s* h) {
+          return launch_rk_update(h->ns, 1, sv(h, 0), sv(h, 0), sv(h, 1), h->Fx, h->Gy, h->gd, h->mech, ctl, a0, a1,
+                                  h->status, h->clock2, h->stream);
+        }, 1, a1);
+      if (!rc)
+        rc = phase(0, [&](janc_grid_s* h) { return launch_face_flux(h->nv, sv(h, 1), a1, h->Fx, h->Gy, h->gd, h->stream); },
+                   -1, nullptr);
+      if (!rc)
+        rc = phase(1, [&](janc_grid_s* h) {
+          return launch_rk_update(h->ns, 2, sv(h, 1), sv(h, 0), sv(h, 2), h->Fx, h->Gy, h->gd, h->mech, ctl, a0, a2,
+                                  h->status, nullptr, h->stream);
+        }, 2, a2);
+      if (!rc)
+        rc = phase(0, [&](janc_grid_s* h) { return launch_face_flux(h->nv, sv(h, 2), a2, h->Fx, h->Gy, h->gd, h->stream); },
+                   -1, nullptr);
+      if (!rc)
+        rc = phase(1, [&](janc_grid_s* h) {
+          return launch_rk_update(h->ns, 3, sv(h, 2), sv(h, 0), sv(h, 0), h->Fx, h->Gy, h->gd, h->mech, ctl, a0,
+                                  chem ? a3 : a4, h->status, nullptr, h->stream);
+        }, chem ? -1 : 0, a4);
+      if (!rc && chem)
+        rc = phase(2, [&](janc_grid_s* h) { return launch_chem(h->ns, sv(h, 0), h->gd, h->mech, ctl, a0, a4, h->status, h->stream); },
+                   0, a4);
+      if (rc) return rc;
+    }
+    // the last state's alpha becomes slot 0
+    e = cudaMemcpyAsync(g->alpha, g->alpha + 2 * (SLOTS_PER_STEP * nc), 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail_cuda(e, "alpha carry");
+    done += nc;
+  }
+  for (int q = 0; q < ng; ++q) gs[q]->steps_done += n_steps;
+  if (t_out || dt_last_out) {
+    double c2[2];
+    cudaError_t e = cudaMemcpyAsync(c2, g->clock2, sizeof(c2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e, "janc_step clock read");
+    if (t_out) *t_out = c2[0] - t_before;
+    if (dt_last_out) *dt_last_out = c2[1];
+  }
+  return JANC_OK;
+}
+
+extern "C" {
+
+const char* janc_last_error(void) { return g_err.c_str(); }
+
+int janc_workspace_bytes(const janc_grid_desc* d, const janc_mechanism* m, size_t* bytes) {
+  int rc = check_desc(d, m);
+  if (rc) return rc;
+  if (!bytes) return fail(JANC_E_INVALID, "null output");
+  *bytes = layout_of(d->nx, d->ny, m->ns + 3, false).total;
+  return JANC_OK;
+}
+
+int janc_create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* workspace, size_t workspace_bytes,
+                     void* cuda_stream, janc_grid_t* out) {
+  return janc::create_grid(d, m, workspace, workspace_bytes, cuda_stream, nullptr, out);
+}
+
 void janc_destroy_grid(janc_grid_t g) {
   if (!g) return;
   cudaStreamSynchronize(g->stream);
@@ -331,6 +448,7 @@ void janc_destroy_grid(janc_grid_t g) {
   for (auto e : g->pool) cudaEventDestroy(e);
   if (g->owns_ws) cudaFree(g->ws);
   if (g->adj.own && g->adj.ws) cudaFree(g->adj.ws);  // a forward never reversed
+  delete g->ex;
   delete g;
 }
 
@@ -366,6 +484,7 @@ int janc_set_state(janc_grid_t g, const double* U, const double* T0, int where) 
   if (e != cudaSuccess) return fail_cuda(e, "janc_set_state");
   e = launch_set_conserved(g->ns, sv(g, 0), t0, g->gd, g->mech, g->alpha, g->status, g->stream);
   if (e != cudaSuccess) return fail_cuda(e, "set_conserved launch");
+  if (g->ex) return g->ex->after(0, g->alpha);  // a stand-alone slab: halos and alpha of the loaded state
   return JANC_OK;
 }
 
@@ -391,6 +510,10 @@ int janc_set_state_primitive(janc_grid_t g, const double* T, const double* p, co
   if (e != cudaSuccess) return fail_cuda(e, "janc_set_state_primitive");
   e = launch_set_primitive(g->ns, sv(g, 0), dT, dp, du, dv, dY, g->gd, g->mech, g->alpha, g->status, g->stream);
   if (e != cudaSuccess) return fail_cuda(e, "set_primitive launch");
+  if (g->ex) {
+    const int rc = g->ex->after(0, g->alpha);
+    if (rc) return rc;
+  }
   if (where == JANC_HOST) {
     e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return fail_cuda(e, "set_primitive");
@@ -400,89 +523,14 @@ int janc_set_state_primitive(janc_grid_t g, const double* T, const double* p, co
 
 int janc_step(janc_grid_t g, int n_steps, double dt, double cfl, double* t_out, double* dt_last_out) {
   if (!g) return fail(JANC_E_INVALID, "null grid");
-  if (n_steps < 0) return fail(JANC_E_INVALID, "n_steps < 0");
-  if ((dt > 0.0) == (cfl > 0.0)) return fail(JANC_E_INVALID, "give exactly one of dt > 0 or cfl > 0");
-  StepCtl ctl;
-  ctl.dt_fixed = dt > 0.0 ? dt : 0.0;
-  ctl.cfl = cfl > 0.0 ? cfl : 0.0;
-  ctl.hmin = g->gd.dx < g->gd.dy ? g->gd.dx : g->gd.dy;
-  const bool strang = g->d.chemistry == JANC_CHEM_STRANG;
-  ctl.chem_frac = strang ? 0.5 : 1.0;
-  ctl.source = g->d.chemistry == JANC_CHEM_EXPLICIT ? 1 : 0;
-  double t_before = 0.0;
-  if (t_out) {
-    cudaError_t e = cudaMemcpyAsync(&t_before, g->clock2, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    if (e != cudaSuccess) return fail_cuda(e, "janc_step clock read");
-  }
-  const StateView S0 = sv(g, 0), S1 = sv(g, 1), S2 = sv(g, 2);
-  const bool chem = g->d.chemistry == JANC_CHEM_LIE || g->d.chemistry == JANC_CHEM_STRANG;
-  int done = 0;
-  while (done < n_steps) {
-    const int nc = (n_steps - done) < CHUNK ? (n_steps - done) : CHUNK;
-    cudaError_t e = cudaMemsetAsync(g->alpha + 2, 0, sizeof(unsigned long long) * 2 * SLOTS_PER_STEP * nc, g->stream);
-    if (e != cudaSuccess) return fail_cuda(e, "alpha reset");
-    for (int s = 0; s < nc; ++s) {
-      // slots: a0 = U^n (dt source), aH = after the first half chemistry
-      // (Strang order only), a1, a2 = stages, a3 = U^*, a4 = U^{n+1} (the
-      // next step's a0)
-      unsigned long long* a0 = g->alpha + 2 * (SLOTS_PER_STEP * s);
-      unsigned long long* aH = a0 + 2;
-      unsigned long long* a1 = a0 + 4;
-      unsigned long long* a2 = a0 + 6;
-      unsigned long long* a3 = a0 + 8;
-      unsigned long long* a4 = a0 + 10;
-      unsigned long long* aF = a0;  // alpha of the flux stage-1 input
-      if (strang) {
-        e = timed(g, 2, [&] { return launch_chem(g->ns, S0, g->gd, g->mech, ctl, a0, aH, g->status, g->stream); });
-        if (e != cudaSuccess) return fail_cuda(e, "step launch");
-        aF = aH;
-      }
-      e = timed(g, 0, [&] { return launch_face_flux(g->nv, S0, aF, g->Fx, g->Gy, g->gd, g->stream); });
-      if (e == cudaSuccess)
-        e = timed(g, 1, [&] {
-          return launch_rk_update(g->ns, 1, S0, S0, S1, g->Fx, g->Gy, g->gd, g->mech, ctl, a0, a1, g->status,
-                                  g->clock2, g->stream);
-        });
-      if (e == cudaSuccess)
-        e = timed(g, 0, [&] { return launch_face_flux(g->nv, S1, a1, g->Fx, g->Gy, g->gd, g->stream); });
-      if (e == cudaSuccess)
-        e = timed(g, 1, [&] {
-          return launch_rk_update(g->ns, 2, S1, S0, S2, g->Fx, g->Gy, g->gd, g->mech, ctl, a0, a2, g->status,
-                                  nullptr, g->stream);
-        });
-      if (e == cudaSuccess)
-        e = timed(g, 0, [&] { return launch_face_flux(g->nv, S2, a2, g->Fx, g->Gy, g->gd, g->stream); });
-      if (e == cudaSuccess)
-        e = timed(g, 1, [&] {
-          return launch_rk_update(g->ns, 3, S2, S0, S0, g->Fx, g->Gy, g->gd, g->mech, ctl, a0, chem ? a3 : a4,
-                                  g->status, nullptr, g->stream);
-        });
-      if (e == cudaSuccess && chem)
-        e = timed(g, 2, [&] { return launch_chem(g->ns, S0, g->gd, g->mech, ctl, a0, a4, g->status, g->stream); });
-      if (e != cudaSuccess) return fail_cuda(e, "step launch");
-    }
-    // the last state's alpha becomes slot 0
-    e = cudaMemcpyAsync(g->alpha, g->alpha + 2 * (SLOTS_PER_STEP * nc), 2 * sizeof(unsigned long long),
-                        cudaMemcpyDeviceToDevice, g->stream);
-    if (e != cudaSuccess) return fail_cuda(e, "alpha carry");
-    done += nc;
-  }
-  g->steps_done += n_steps;
-  if (t_out || dt_last_out) {
-    double c2[2];
-    cudaError_t e = cudaMemcpyAsync(c2, g->clock2, sizeof(c2), cudaMemcpyDeviceToHost, g->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    if (e != cudaSuccess) return fail_cuda(e, "janc_step clock read");
-    if (t_out) *t_out = c2[0] - t_before;
-    if (dt_last_out) *dt_last_out = c2[1];
-  }
-  return JANC_OK;
+  janc_grid_s* gs[1] = {g};
+  return janc::step_grids(gs, 1, g->ex, n_steps, dt, cfl, t_out, dt_last_out);
 }
 
 int janc_source_step(janc_grid_t g, int n_steps, double dt) {
   if (!g || n_steps < 0 || !(dt > 0.0)) return fail(JANC_E_INVALID, "janc_source_step: bad argument");
   if (g->d.chemistry == JANC_CHEM_OFF) return fail(JANC_E_INVALID, "janc_source_step: the grid has no chemistry");
+  if (g->halo_side[0] || g->halo_side[1]) return fail(JANC_E_UNSUPPORTED, "janc_source_step: not on an x-slab");
   StepCtl ctl;
   ctl.dt_fixed = dt;
   ctl.cfl = 0.0;
@@ -607,6 +655,7 @@ namespace {
 struct AdjLayout {
   size_t state, ckpt, seg, alog, lam, cfx, cfy, small, total;
   int ncp, seglen;
+  int nstore;  // segment stores: 2 when segments are recomputed (the next one while the current is reversed)
 };
 
 AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every) {
@@ -617,13 +666,14 @@ AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every) {
   L.ncp = n_steps > 0 ? (n_steps + ckpt_every - 1) / ckpt_every : 1;
   L.state = align256(sizeof(double) * (size_t)(nv + 4) * n);
   L.ckpt = (size_t)L.ncp * (L.state + 256);              // state + its alpha pair
-  L.seg = (size_t)(4 * ckpt_every + 1) * L.state;        // S0[0..len], S1, S2, S* per step
+  L.nstore = L.ncp > 1 ? 2 : 1;
+  L.seg = (size_t)(4 * ckpt_every + 1) * L.state;        // S0[0..len], S1, S2, S* per step (one store)
   L.alog = align256(sizeof(unsigned long long) * 10 * ckpt_every);
   L.lam = 7 * align256(sizeof(double) * (size_t)nv * n);
   L.cfx = align256(sizeof(double) * (size_t)nv * g->gd.ny * (g->gd.nx + 1) * 10);
   L.cfy = align256(sizeof(double) * (size_t)nv * (g->gd.ny + 1) * g->gd.nx * 10);
   L.small = 256 + rhs_vjp_scratch_bytes(g->gd);  // [0] loss, then the RHS-VJP scratch at +256
-  L.total = L.ckpt + L.seg + L.alog + L.lam + L.cfx + L.cfy + L.small;
+  L.total = L.ckpt + L.nstore * (L.seg + L.alog) + L.lam + L.cfx + L.cfy + L.small;
   return L;
 }
 
@@ -639,6 +689,7 @@ int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, siz
 
 int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, size_t workspace_bytes, int where) {
   if (!g || !mu || !nu) return fail(JANC_E_INVALID, "null argument");
+  if (g->halo_side[0] || g->halo_side[1]) return fail(JANC_E_UNSUPPORTED, "janc_rhs_vjp runs on whole grids, not x-slabs");
   if (where != JANC_HOST && where != JANC_DEVICE) return fail(JANC_E_INVALID, "bad where");
   const size_t nvn = (size_t)g->nv * g->n;
   const size_t bx = align256(sizeof(double) * (size_t)g->nv * g->gd.ny * (g->gd.nx + 1) * 10);
@@ -676,11 +727,16 @@ int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, s
 
 namespace {
 
+// One segment store: the states of a segment and their alpha log.
+struct SegStore {
+  char* seg;
+  unsigned long long* alog;
+};
+
 // Pointers into an adjoint workspace (see adj_layout).
 struct AdjPtrs {
   char* ckpt;
-  char* seg;
-  unsigned long long* alog;
+  SegStore store[2];  // store[c % nstore] holds segment c
   double* lam[7];
   double* cfx;
   double* cfy;
@@ -692,8 +748,11 @@ AdjPtrs adj_ptrs(const janc_grid_s* g, const AdjLayout& L, char* ws) {
   const size_t lamb = align256(sizeof(double) * (size_t)g->nv * (size_t)g->n);
   char* p = ws;
   q.ckpt = p; p += L.ckpt;
-  q.seg = p; p += L.seg;
-  q.alog = (unsigned long long*)p; p += L.alog;
+  for (int k = 0; k < L.nstore; ++k) {
+    q.store[k].seg = p; p += L.seg;
+    q.store[k].alog = (unsigned long long*)p; p += L.alog;
+  }
+  if (L.nstore == 1) q.store[1] = q.store[0];
   for (int k = 0; k < 7; ++k) { q.lam[k] = (double*)p; p += lamb; }
   q.cfx = (double*)p; p += L.cfx;
   q.cfy = (double*)p; p += L.cfy;
@@ -718,10 +777,10 @@ void adj_release(janc_grid_s* g) {
 
 // Segment store: slots 0..len hold U^{m0+m} (with T and the aux planes),
 // then S1, S2, S* of every step of the segment.
-StateView seg_S0(const AdjPtrs& q, const AdjLayout& L, int m) {
+StateView seg_S0(const SegStore& q, const AdjLayout& L, int m) {
   return StateView{(double*)(q.seg + (size_t)m * L.state)};
 }
-StateView seg_S(const AdjPtrs& q, const AdjLayout& L, int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
+StateView seg_S(const SegStore& q, const AdjLayout& L, int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
   return StateView{(double*)(q.seg + (size_t)(L.seglen + 1 + 3 * m + which - 1) * L.state)};
 }
 
@@ -731,10 +790,10 @@ StateView seg_S(const AdjPtrs& q, const AdjLayout& L, int m, int which) {  // wh
 // U*, U^{n+1}). The kernels and their order are those of janc_step, so the
 // stored trajectory is the forward's, bit for bit. With `clock` the simulated
 // time advances as in janc_step; with `loss` the end-wall loss of every new
-// state accumulates into loss[0].
-cudaError_t adj_segment(janc_grid_s* g, const AdjLayout& L, const AdjPtrs& q, int len, const StepCtl& ctl,
-                        double* clock, double* loss, double w_loss) {
-  cudaStream_t st = g->stream;
+// state accumulates into loss[0]. Runs on stream st; it uses the grid's face
+// flux arrays, so two segments never run at once.
+cudaError_t adj_segment(janc_grid_s* g, const AdjLayout& L, const SegStore& q, int len, const StepCtl& ctl,
+                        double* clock, double* loss, double w_loss, cudaStream_t st) {
   const int nv = g->nv;
   const bool chem = g->d.chemistry == JANC_CHEM_LIE;
   unsigned long long* alog = q.alog;
@@ -772,6 +831,7 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
   if (!g || n_steps < 0 || !(dt > 0.0) || ckpt_every <= 0) return fail(JANC_E_INVALID, "bad argument");
   if (loss_kind != JANC_LOSS_ENDWALL_P && loss_kind != JANC_LOSS_SEEDED) return fail(JANC_E_INVALID, "loss kind");
   if (g->d.chemistry == JANC_CHEM_STRANG) return fail(JANC_E_UNSUPPORTED, "the adjoint reverses the Lie order only");
+  if (g->halo_side[0] || g->halo_side[1]) return fail(JANC_E_UNSUPPORTED, "the adjoint runs on whole grids, not x-slabs");
   adj_release(g);
   const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
   char* ws = (char*)workspace;
@@ -803,17 +863,18 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
     if (e != cudaSuccess) break;
     if (s == m_last) {
       const int len = n_steps - m_last;
-      e = cudaMemcpyAsync(seg_S0(q, L, 0).base, g->S[0], L.state, cudaMemcpyDeviceToDevice, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(q.alog, 0, L.alog, st);
+      const SegStore& sq = q.store[(L.ncp - 1) % L.nstore];
+      e = cudaMemcpyAsync(seg_S0(sq, L, 0).base, g->S[0], L.state, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(sq.alog, 0, L.alog, st);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(q.alog, g->alpha, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+        e = cudaMemcpyAsync(sq.alog, g->alpha, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
       if (e == cudaSuccess)
-        e = adj_segment(g, L, q, len, adj_ctl(g, dt), g->clock2,
-                        loss_kind == JANC_LOSS_ENDWALL_P ? q.small : nullptr, w_loss);
+        e = adj_segment(g, L, sq, len, adj_ctl(g, dt), g->clock2,
+                        loss_kind == JANC_LOSS_ENDWALL_P ? q.small : nullptr, w_loss, st);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(g->S[0], seg_S0(q, L, len).base, L.state, cudaMemcpyDeviceToDevice, st);
+        e = cudaMemcpyAsync(g->S[0], seg_S0(sq, L, len).base, L.state, cudaMemcpyDeviceToDevice, st);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(g->alpha, q.alog + 10 * (len - 1) + 8, 2 * sizeof(unsigned long long),
+        e = cudaMemcpyAsync(g->alpha, sq.alog + 10 * (len - 1) + 8, 2 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToDevice, st);
       g->steps_done += len;
       break;
@@ -853,13 +914,10 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
   const size_t nvn = (size_t)nv * n;
   auto ckpt_state = [&](int c) { return StateView{(double*)(q.ckpt + (size_t)c * (L.state + 256))}; };
   auto ckpt_alpha = [&](int c) { return (unsigned long long*)(q.ckpt + (size_t)c * (L.state + 256) + L.state); };
-  auto segS0 = [&](int m) { return seg_S0(q, L, m); };
-  auto segS = [&](int m, int which) { return seg_S(q, L, m, which); };
   const bool chem = g->d.chemistry == JANC_CHEM_LIE;
   const bool src = g->d.chemistry == JANC_CHEM_EXPLICIT;
   const double w_loss = dt / g->gd.ny;
   const StepCtl ctl = adj_ctl(g, dt);
-  unsigned long long* alog = q.alog;
   double* cfx = q.cfx;
   double* cfy = q.cfy;
   double* small = q.small;
@@ -874,18 +932,44 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
   if (seed) e = cudaMemcpyAsync(lamN, seed, sizeof(double) * nvn,
                                 where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
   else e = cudaMemsetAsync(lamN, 0, sizeof(double) * nvn, st);
-  for (int c = L.ncp - 1; c >= 0 && e == cudaSuccess && n_steps > 0; --c) {
+  // Segments other than the last are recomputed from their checkpoints on a
+  // second stream into the other segment store, one segment ahead of the
+  // reverse sweep: segment c - 1 is recomputed while segment c is reversed.
+  // On a grid too small to fill the GPU the two overlap. Store c % 2 is
+  // refilled (segment c - 2) only after segment c's reverse has finished.
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_rev = nullptr;
+  auto seg_len = [&](int c) {
     const int m0 = c * ckpt_every;
-    const int len = (n_steps - m0) < ckpt_every ? (n_steps - m0) : ckpt_every;
-    // recompute the segment, keeping every stage state and its alpha (the
-    // forward left the last segment in the store already)
-    if (c < L.ncp - 1) {
-      e = cudaMemcpyAsync(segS0(0).base, ckpt_state(c).base, L.state, cudaMemcpyDeviceToDevice, st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(alog, 0, L.alog, st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(alog, ckpt_alpha(c), 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
-      if (e == cudaSuccess) e = adj_segment(g, L, q, len, ctl, nullptr, nullptr, 0.0);
-    }
+    return (n_steps - m0) < ckpt_every ? (n_steps - m0) : ckpt_every;
+  };
+  auto recompute = [&](int c) {  // segment c into store c % 2, on s2
+    const SegStore& sq = q.store[c % L.nstore];
+    cudaError_t r = cudaMemcpyAsync(seg_S0(sq, L, 0).base, ckpt_state(c).base, L.state, cudaMemcpyDeviceToDevice, s2);
+    if (r == cudaSuccess) r = cudaMemsetAsync(sq.alog, 0, L.alog, s2);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(sq.alog, ckpt_alpha(c), 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s2);
+    if (r == cudaSuccess) r = adj_segment(g, L, sq, seg_len(c), ctl, nullptr, nullptr, 0.0, s2);
+    if (r == cudaSuccess) r = cudaEventRecord(ev_rec[c % 2], s2);
+    return r;
+  };
+  if (e == cudaSuccess && L.ncp > 1 && n_steps > 0) {
+    e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev_rec[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_rev, cudaEventDisableTiming);
+    // s2 starts after everything enqueued on the grid's stream so far
+    if (e == cudaSuccess) e = cudaEventRecord(ev_rev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_rev, 0);
+    if (e == cudaSuccess) e = recompute(L.ncp - 2);
+  }
+  for (int c = L.ncp - 1; c >= 0 && e == cudaSuccess && n_steps > 0; --c) {
+    const int len = seg_len(c);
+    const SegStore& sq = q.store[c % L.nstore];
+    const unsigned long long* alog = sq.alog;
+    auto segS0 = [&](int m) { return seg_S0(sq, L, m); };
+    auto segS = [&](int m, int which) { return seg_S(sq, L, m, which); };
+    // the forward left the last segment in its store; the others come from s2
+    if (c < L.ncp - 1) e = cudaStreamWaitEvent(st, ev_rec[c % 2], 0);
     // reverse through the segment
     for (int m = len - 1; m >= 0 && e == cudaSuccess; --m) {
       const unsigned long long* a = alog + 10 * m;
@@ -919,11 +1003,25 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0, lam1, 1.0, nu, true, st);
       std::swap(lamN, lam0);
     }
+    // segment c's store is free once its reverse is done: refill it with c - 2
+    if (e == cudaSuccess && c - 2 >= 0) {
+      e = cudaEventRecord(ev_rev, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_rev, 0);
+      if (e == cudaSuccess) e = recompute(c - 2);
+    }
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dL_dU0, lamN, sizeof(double) * nvn,
                         where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (s2) {
+    const cudaError_t e2 = cudaStreamSynchronize(s2);  // nothing is left on it once st is done; a failure shows here
+    if (e == cudaSuccess) e = e2;
+    cudaStreamDestroy(s2);
+  }
+  for (int k = 0; k < 2; ++k)
+    if (ev_rec[k]) cudaEventDestroy(ev_rec[k]);
+  if (ev_rev) cudaEventDestroy(ev_rev);
   adj_release(g);
   if (e != cudaSuccess) return fail_cuda(e, "janc_adjoint_reverse");
   return JANC_OK;

@@ -18,16 +18,80 @@
 // multiplications instead of a second exponential per reaction; the
 // exponentials use the table-driven exp_t (about half the FP64 instructions
 // of the library exp).
+//
+// The reaction loop is written once over a structure policy: DynRx reads each
+// reaction's species, coefficients and third-body data from the run-time
+// table, FixRx<I> returns them as compile-time constants of the shipped H2-air
+// mechanism (janc_mech_fixed.cuh). Both run the same operations in the same
+// order, so they give the same bits; with FixRx every index of the per-cell
+// arrays (concentrations, exp(G_k), production rates, Jacobian) is a constant
+// and the arrays live in registers instead of local memory.
+#include <utility>
+
 #include "janc_device.cuh"
 #include "janc_internal.h"
+#include "janc_mech_fixed.cuh"
 
 namespace janc {
 
 constexpr int CHEM_THREADS = 128;
 
+// Reaction i of the run-time mechanism table.
+struct DynRx {
+  const MechDev& m;
+  int i;
+  __device__ __forceinline__ int idx() const { return i; }
+  __device__ __forceinline__ int nre() const { return m.nre[i]; }
+  __device__ __forceinline__ int npr() const { return m.npr[i]; }
+  __device__ __forceinline__ int dnu() const { return m.dnu[i]; }
+  __device__ __forceinline__ int tb() const { return m.tb[i]; }
+  __device__ __forceinline__ int neff() const { return m.neff[i]; }
+  __device__ __forceinline__ int rsp(int r) const { return m.rsp[i][r]; }
+  __device__ __forceinline__ int rnu(int r) const { return m.rnu[i][r]; }
+  __device__ __forceinline__ double rnud(int r) const { return m.rnud[i][r]; }
+  __device__ __forceinline__ int psp(int r) const { return m.psp[i][r]; }
+  __device__ __forceinline__ int pnu(int r) const { return m.pnu[i][r]; }
+  __device__ __forceinline__ double pnud(int r) const { return m.pnud[i][r]; }
+  __device__ __forceinline__ int effsp(int e) const { return m.effsp[i][e]; }
+};
+
+// Reaction I of the compiled H2-air structure (numbers still come from the table).
+template <int I>
+struct FixRx {
+  using S = fixed_h2air::Rx<I>;
+  __device__ __forceinline__ static constexpr int idx() { return I; }
+  __device__ __forceinline__ static constexpr int nre() { return S::nre; }
+  __device__ __forceinline__ static constexpr int npr() { return S::npr; }
+  __device__ __forceinline__ static constexpr int dnu() { return S::dnu; }
+  __device__ __forceinline__ static constexpr int tb() { return S::tb; }
+  __device__ __forceinline__ static constexpr int neff() { return S::neff; }
+  __device__ __forceinline__ static constexpr int rsp(int r) { return S::rsp(r); }
+  __device__ __forceinline__ static constexpr int rnu(int r) { return S::rnu(r); }
+  __device__ __forceinline__ static constexpr double rnud(int r) { return (double)S::rnu(r); }
+  __device__ __forceinline__ static constexpr int psp(int r) { return S::psp(r); }
+  __device__ __forceinline__ static constexpr int pnu(int r) { return S::pnu(r); }
+  __device__ __forceinline__ static constexpr double pnud(int r) { return (double)S::pnu(r); }
+  __device__ __forceinline__ static constexpr int effsp(int e) { return S::effsp(e); }
+};
+
+template <int... I, class F>
+__device__ __forceinline__ void fixed_reactions(std::integer_sequence<int, I...>, F&& f) {
+  (f(FixRx<I>{}), ...);
+}
+
+// f(reaction) for every reaction, in order.
+template <bool FIXED, class F>
+__device__ __forceinline__ void for_reactions(const MechDev& m, F&& f) {
+  if constexpr (FIXED) {
+    fixed_reactions(std::make_integer_sequence<int, fixed_h2air::NR>{}, f);
+  } else {
+    for (int i = 0; i < m.nr; ++i) f(DynRx{m, i});
+  }
+}
+
 // One CHEM_THREADS block `blk` of cells; shared by the single-grid and the
 // batched kernels.
-template <int NS>
+template <int NS, bool FIXED>
 __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g, const MechDev* __restrict__ mech,
                                            const StepCtl& ctl, const unsigned long long* __restrict__ alpha_step,
                                            unsigned long long* alpha_out, int* status, long long blk) {
@@ -81,75 +145,98 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
       for (int l = 0; l < NSP; ++l) J[k][l] = 0.0;
     }
 
-    for (int i = 0; i < m.nr; ++i) {
-      const int nre = m.nre[i], npr = m.npr[i];
+    for_reactions<FIXED>(m, [&](auto R) {
+      const int i = R.idx();
+      const int nre = R.nre(), npr = R.npr();
       const double kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
       // k_b = k_f / K_eq,  K_eq = prod_j exp(G_j)^{nu_j} (P_ref/(Ru T))^{dnu}
       double kb = kf;
+#pragma unroll
       for (int r = 0; r < nre; ++r)
-        for (int q = 0; q < m.rnu[i][r]; ++q) kb *= eG[m.rsp[i][r]];
+#pragma unroll
+        for (int q = 0; q < R.rnu(r); ++q) kb *= eG[R.rsp(r)];
+#pragma unroll
       for (int r = 0; r < npr; ++r)
-        for (int q = 0; q < m.pnu[i][r]; ++q) kb *= reG[m.psp[i][r]];
-      const int dn = m.dnu[i];
+#pragma unroll
+        for (int q = 0; q < R.pnu(r); ++q) kb *= reG[R.psp(r)];
+      const int dn = R.dnu();
+#pragma unroll
       for (int q = 0; q < dn; ++q) kb *= rcref;
+#pragma unroll
       for (int q = 0; q < -dn; ++q) kb *= cref;
       // law of mass action and its derivatives with respect to each participant
       double xr[MAX_SIDE], xp[MAX_SIDE];
       double fwd = kf, bwd = kb;
+#pragma unroll
       for (int r = 0; r < nre; ++r) {
-        xr[r] = X[m.rsp[i][r]];
-        for (int q = 0; q < m.rnu[i][r]; ++q) fwd *= xr[r];
+        xr[r] = X[R.rsp(r)];
+#pragma unroll
+        for (int q = 0; q < R.rnu(r); ++q) fwd *= xr[r];
       }
+#pragma unroll
       for (int r = 0; r < npr; ++r) {
-        xp[r] = X[m.psp[i][r]];
-        for (int q = 0; q < m.pnu[i][r]; ++q) bwd *= xp[r];
+        xp[r] = X[R.psp(r)];
+#pragma unroll
+        for (int q = 0; q < R.pnu(r); ++q) bwd *= xp[r];
       }
       double Mi = 1.0;
-      if (m.tb[i]) {
+      if (R.tb()) {
         Mi = Ctot;
-        for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
+#pragma unroll
+        for (int e = 0; e < R.neff(); ++e) Mi = fma(m.effv[i][e], X[R.effsp(e)], Mi);
       }
       const double net = fwd - bwd;
       const double q = Mi * net;
       // sources: wdot_k += nu_ki q
+#pragma unroll
       for (int r = 0; r < nre; ++r) {
-        const int k = m.rsp[i][r];
-        if (k < NSP) wd[k] = fma(-m.rnud[i][r], q, wd[k]);
+        const int k = R.rsp(r);
+        if (k < NSP) wd[k] = fma(-R.rnud(r), q, wd[k]);
       }
+#pragma unroll
       for (int r = 0; r < npr; ++r) {
-        const int k = m.psp[i][r];
-        if (k < NSP) wd[k] = fma(m.pnud[i][r], q, wd[k]);
+        const int k = R.psp(r);
+        if (k < NSP) wd[k] = fma(R.pnud(r), q, wd[k]);
       }
       // dq/dX_j for the participants (third-body factor held fixed here)
       double dq[2 * MAX_SIDE];
       int dsp[2 * MAX_SIDE];
       int nd = 0;
+#pragma unroll
       for (int r = 0; r < nre; ++r) {
-        double d = m.rnu[i][r] == 1 ? kf : kf * m.rnud[i][r];
+        double d = R.rnu(r) == 1 ? kf : kf * R.rnud(r);
+#pragma unroll
         for (int s = 0; s < nre; ++s) {
-          const int pw = m.rnu[i][s] - (s == r ? 1 : 0);
+          const int pw = R.rnu(s) - (s == r ? 1 : 0);
+#pragma unroll
           for (int t = 0; t < pw; ++t) d *= xr[s];
         }
         dq[nd] = Mi * d;
-        dsp[nd++] = m.rsp[i][r];
+        dsp[nd++] = R.rsp(r);
       }
+#pragma unroll
       for (int r = 0; r < npr; ++r) {
-        double d = m.pnu[i][r] == 1 ? kb : kb * m.pnud[i][r];
+        double d = R.pnu(r) == 1 ? kb : kb * R.pnud(r);
+#pragma unroll
         for (int s = 0; s < npr; ++s) {
-          const int pw = m.pnu[i][s] - (s == r ? 1 : 0);
+          const int pw = R.pnu(s) - (s == r ? 1 : 0);
+#pragma unroll
           for (int t = 0; t < pw; ++t) d *= xp[s];
         }
         dq[nd] = -Mi * d;
-        dsp[nd++] = m.psp[i][r];
+        dsp[nd++] = R.psp(r);
       }
       // rows: every carried species with nonzero net coefficient
+#pragma unroll
       for (int side = 0; side < 2; ++side) {
         const int cnt = side ? npr : nre;
+#pragma unroll
         for (int r = 0; r < cnt; ++r) {
-          const int k = side ? m.psp[i][r] : m.rsp[i][r];
+          const int k = side ? R.psp(r) : R.rsp(r);
           if (k >= NSP) continue;
-          const double nu = side ? m.pnud[i][r] : -m.rnud[i][r];
-          for (int d = 0; d < nd; ++d) {
+          const double nu = side ? R.pnud(r) : -R.rnud(r);
+#pragma unroll
+          for (int d = 0; d < nre + npr; ++d) {
             const int j = dsp[d];
             if (j < NSP) {
               J[k][j] = fma(nu, dq[d], J[k][j]);
@@ -159,14 +246,14 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
               for (int l = 0; l < NSP; ++l) J[k][l] = fma(-m.mratio[l], v, J[k][l]);
             }
           }
-          if (m.tb[i]) {
+          if (R.tb()) {
             const double v = nu * net;
 #pragma unroll
             for (int l = 0; l < NSP; ++l) J[k][l] = fma(v, m.ceff[i][l], J[k][l]);
           }
         }
       }
-    }
+    });
 
     // (I - dt J'') dx = dt wd
     double A[NSP][NSP], b[NSP], ip[NSP];
@@ -186,18 +273,28 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
         const unsigned long long v = dbits(A[r][c]) & 0x7fffffffffffffffull;
         if (v > best) { best = v; piv = r; }
       }
+      // row swap c <-> piv as selects: row c takes the pivot row's values and
+      // the pivot row row c's old ones (nothing moves when piv == c). Written
+      // as one gather and one scatter per column so that every index stays a
+      // constant and the matrix stays in registers.
 #pragma unroll
-      for (int r = c + 1; r < NSP; ++r) {
-        const bool s = (piv == r);
+      for (int k = c; k < NSP; ++k) {
+        const double ac = A[c][k];
+        double v = ac;
 #pragma unroll
-        for (int k = c; k < NSP; ++k) {
-          const double a0 = A[c][k], a1 = A[r][k];
-          A[c][k] = s ? a1 : a0;
-          A[r][k] = s ? a0 : a1;
-        }
-        const double b0 = b[c], b1 = b[r];
-        b[c] = s ? b1 : b0;
-        b[r] = s ? b0 : b1;
+        for (int r = c + 1; r < NSP; ++r) v = (piv == r) ? A[r][k] : v;
+#pragma unroll
+        for (int r = c + 1; r < NSP; ++r) A[r][k] = (piv == r) ? ac : A[r][k];
+        A[c][k] = v;
+      }
+      {
+        const double bc = b[c];
+        double v = bc;
+#pragma unroll
+        for (int r = c + 1; r < NSP; ++r) v = (piv == r) ? b[r] : v;
+#pragma unroll
+        for (int r = c + 1; r < NSP; ++r) b[r] = (piv == r) ? bc : b[r];
+        b[c] = v;
       }
       if (best == 0ull) singular = true;
       ip[c] = rcp(A[c][c]);
@@ -237,34 +334,51 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
   block_reduce_alpha_status(sx, sy, st, alpha_out, status);
 }
 
-template <int NS>
+template <int NS, bool FIXED>
 __global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, const MechDev* __restrict__ mech,
                                                        StepCtl ctl, const unsigned long long* __restrict__ alpha_step,
                                                        unsigned long long* alpha_out, int* status) {
-  chem_block<NS>(S, g, mech, ctl, alpha_step, alpha_out, status, blockIdx.x);
+  chem_block<NS, FIXED>(S, g, mech, ctl, alpha_step, alpha_out, status, blockIdx.x);
 }
 
 // Batched chemistry over the flattened (request, block) list: in place on
 // each request's S[0], output alpha in slot 4.
-template <int NS>
+template <int NS, bool FIXED>
 __global__ void __launch_bounds__(CHEM_THREADS) k_chem_batch(const BatchReq* __restrict__ reqs,
                                                              const int* __restrict__ first, int nreq) {
   const int total = first[nreq];
   for (int e = blockIdx.x; e < total; e += gridDim.x) {
     const int r = batch_owner(first, nreq, e);
     const BatchReq& q = reqs[r];
-    chem_block<NS>(q.S[0], q.g, q.mech, q.ctl, q.alpha, q.alpha + 8, q.status, e - first[r]);
+    chem_block<NS, FIXED>(q.S[0], q.g, q.mech, q.ctl, q.alpha, q.alpha + 8, q.status, e - first[r]);
     __syncthreads();
   }
 }
 
-cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, cudaStream_t st) {
+bool fixed_structure(const janc_mechanism* m) {
+  using namespace fixed_h2air;
+  if (!m || m->ns != NS || m->nr != NR || !m->nuf || !m->nub || !m->tb || !m->eff) return false;
+  for (int i = 0; i < NR; ++i) {
+    if ((m->tb[i] ? 1 : 0) != kTb[i]) return false;
+    for (int j = 0; j < NS; ++j) {
+      if (m->nuf[i * NS + j] != kNuf[i * NS + j] || m->nub[i * NS + j] != kNub[i * NS + j]) return false;
+      if (kTb[i] && (m->eff[i * NS + j] != 1.0 ? 1 : 0) != kEffNe1[i * NS + j]) return false;
+    }
+  }
+  return true;
+}
+
+cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, bool fixed,
+                              cudaStream_t st) {
   const int sms = sm_count();
   const int grid = total < sms * 16 ? total : sms * 16;
   if (grid <= 0) return cudaSuccess;
   switch (ns) {
-    case 3: k_chem_batch<3><<<grid, CHEM_THREADS, 0, st>>>(reqs, first, nreq); break;
-    case 9: k_chem_batch<9><<<grid, CHEM_THREADS, 0, st>>>(reqs, first, nreq); break;
+    case 3: k_chem_batch<3, false><<<grid, CHEM_THREADS, 0, st>>>(reqs, first, nreq); break;
+    case 9:
+      if (fixed) k_chem_batch<9, true><<<grid, CHEM_THREADS, 0, st>>>(reqs, first, nreq);
+      else k_chem_batch<9, false><<<grid, CHEM_THREADS, 0, st>>>(reqs, first, nreq);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -289,8 +403,11 @@ cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const Mech
   const int thr = chem_threads(g.n);
   const unsigned blocks = (unsigned)((g.n + thr - 1) / thr);
   switch (ns) {
-    case 3: k_chem<3><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
-    case 9: k_chem<9><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
+    case 3: k_chem<3, false><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status); break;
+    case 9:
+      if (g.chem_fixed) k_chem<9, true><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status);
+      else k_chem<9, false><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

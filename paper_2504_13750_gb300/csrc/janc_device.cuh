@@ -22,7 +22,10 @@ constexpr int MAX_NR = 32;
 constexpr int MAX_SIDE = 3;  // distinct species per reaction side
 
 enum : int { ST_NONFINITE = 1, ST_NONPOSITIVE = 2, ST_NEWTON_FAIL = 4, ST_SINGULAR = 8 };
-enum : int { BC_WALL = 0, BC_ZEROGRAD = 1, BC_PERIODIC = 2 };
+// BC_HALO marks an x side shared with the neighbouring slab of an x-slab
+// decomposition (Sec. 4.4): its 3 ghost columns are read from a halo buffer
+// that the exchange fills, not derived from the slab's own cells.
+enum : int { BC_WALL = 0, BC_ZEROGRAD = 1, BC_PERIODIC = 2, BC_HALO = 3 };
 
 // Mechanism in the form the kernels consume (built on the host from the
 // user's table, copied once to device memory).
@@ -73,6 +76,14 @@ struct GridDev {
   double eps4;  // 4 * WENO epsilon (smoothness indicators are carried scaled by 4)
   double newton_tol;
   int newton_maxit;
+  // Halo buffers of the x sides whose bc is BC_HALO: [nv + 4][ny][3] each,
+  // the 3 columns nearest the side, plane by plane like the state (column c
+  // of the low halo is ghost cell c - 3, of the high halo cell nx + c).
+  const double* halo_lo;
+  const double* halo_hi;
+  // 1: the mechanism has the reaction structure compiled into the fixed
+  // chemistry kernels (same arithmetic, every index a constant)
+  int chem_fixed;
 };
 
 // One state buffer: planes 0..nv-1 conserved, nv: T, nv+1: u, nv+2: v, nv+3: p.

@@ -16,6 +16,8 @@
 //
 // Per face and sign the reconstruction costs 27 FP64 instructions plus 5 per
 // new point (Jiang-Shu weights in divide-free form, one reciprocal).
+#include <atomic>
+
 #include "janc_device.cuh"
 #include "janc_internal.h"
 #include "janc_weno.cuh"
@@ -27,8 +29,9 @@ constexpr int FACES = 32;  // faces per tile of the batched launch and of large 
 
 // One tile of the face-flux launch (FC faces per line); `blk` is the tile's
 // index in the launch (x tiles first). Shared by the single-grid and the
-// batched kernels.
-template <int NV, int FC = FACES>
+// batched kernels. HALO: the grid is a slab of an x-slab decomposition and
+// the ghost columns of its BC_HALO sides come from the halo buffers.
+template <int NV, int FC = FACES, bool HALO = false>
 __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigned long long* __restrict__ alpha,
                                                double* __restrict__ Fx, double* __restrict__ Gy, const GridDev& g,
                                                int blk, int nbx, int ntx_x, int ntx_y, double* smem) {
@@ -57,8 +60,7 @@ __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigne
   const int nmom = xdir ? 1 : 2;  // wall-normal momentum plane
   const double alph = bitsd(alpha[xdir ? 0 : 1]);
   const double ha = 0.5 * alph;
-  const double* uplane = S.plane(xdir ? NV + 1 : NV + 2, n);
-  const double* pplane = S.plane(NV + 3, n);
+  const int uk = xdir ? NV + 1 : NV + 2;  // plane of the face-normal velocity
 
   // ---- stage the tile: LINES x WIN cells, ghosts mapped on the fly ----
   const int nthr = blockDim.x;
@@ -70,11 +72,22 @@ __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigne
     int cg = f0 - 3 + w;
     if (cg > ncell + 2) cg = ncell + 2;   // beyond the last needed ghost: clamp
     bool flip;
-    const int src = ghost_src(cg, ncell, bc_lo, bc_hi, flip);
-    const long long idx = xdir ? (long long)lg * nx + src : (long long)src * nx + lg;
-    double un = uplane[idx];
+    const double* base = S.base;  // planes of `base` are `ps` apart
+    long long ps = n, idx;
+    if (HALO && xdir && ((cg < 0 && bc_lo == BC_HALO) || (cg >= ncell && bc_hi == BC_HALO))) {
+      // a ghost column of a side shared with the neighbouring slab
+      const bool lo = cg < 0;
+      base = lo ? g.halo_lo : g.halo_hi;
+      ps = 3LL * nlines;
+      idx = (long long)lg * 3 + (lo ? cg + 3 : cg - ncell);
+      flip = false;
+    } else {
+      const int src = ghost_src(cg, ncell, bc_lo, bc_hi, flip);
+      idx = xdir ? (long long)lg * nx + src : (long long)src * nx + lg;
+    }
+    double un = base[uk * ps + idx];
     if (flip) un = -un;
-    const double hp = 0.5 * pplane[idx];
+    const double hp = 0.5 * base[(NV + 3) * ps + idx];
     const int o = line * WIN + w;
     sLp[o] = fma(0.5, un, ha);
     sLm[o] = fma(0.5, un, -ha);
@@ -82,7 +95,7 @@ __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigne
     sHpu[o] = hp * un;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double v = S.plane(k, n)[idx];
+      double v = base[k * ps + idx];
       if (flip && k == nmom) v = -v;
       sU[(k * LINES + line) * WIN + w] = v;
     }
@@ -105,12 +118,12 @@ __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigne
   }
 }
 
-template <int NV, int FC>
+template <int NV, int FC, bool HALO>
 __global__ void __launch_bounds__(LINES * NV) k_face_flux(StateView S, const unsigned long long* __restrict__ alpha,
                                                           double* __restrict__ Fx, double* __restrict__ Gy,
                                                           GridDev g, int nbx, int ntx_x, int ntx_y) {
   extern __shared__ double smem[];
-  face_flux_tile<NV, FC>(S, alpha, Fx, Gy, g, blockIdx.x, nbx, ntx_x, ntx_y, smem);
+  face_flux_tile<NV, FC, HALO>(S, alpha, Fx, Gy, g, blockIdx.x, nbx, ntx_x, ntx_y, smem);
 }
 
 // Batched form: a persistent grid walks the flattened (request, tile) list;
@@ -146,6 +159,22 @@ int sm_count() {
   return cache[dev];
 }
 
+// Sets kernel attribute `attr` to `value` once per device: function
+// attributes belong to the context of the device current at the call, so a
+// process that drives several devices (or slabs on several devices) needs one
+// flag per device. The flags are atomics, so concurrent first calls from
+// several host threads set the attribute twice at worst, which is harmless.
+cudaError_t set_attr_once(const void* func, cudaFuncAttribute attr, int value, std::atomic<unsigned long long>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done->load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, attr, value);
+  if (e == cudaSuccess) done->fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 // Tiles of FC faces: x tiles first, then y tiles.
 static void tiles_of(const GridDev& g, int fc, int* nbx, int* ntx_x, int* ntx_y, int* total) {
   *ntx_x = (g.nx + 1 + fc - 1) / fc;
@@ -156,19 +185,17 @@ static void tiles_of(const GridDev& g, int fc, int* nbx, int* ntx_x, int* ntx_y,
   *total = *nbx + *ntx_y * nty_y;
 }
 
-template <int NV, int FC>
+template <int NV, int FC, bool HALO>
 static cudaError_t launch_face_flux_fc(const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
                                        const GridDev& g, cudaStream_t st) {
   int nbx, ntx_x, ntx_y, total;
   tiles_of(g, FC, &nbx, &ntx_x, &ntx_y, &total);
   const size_t smem = flux_smem_bytes<NV, FC>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_face_flux<NV, FC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  k_face_flux<NV, FC><<<total, LINES * NV, smem, st>>>(S, alpha, Fx, Gy, g, nbx, ntx_x, ntx_y);
+  static std::atomic<unsigned long long> attr_done{0};
+  cudaError_t e = set_attr_once((const void*)k_face_flux<NV, FC, HALO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem, &attr_done);
+  if (e != cudaSuccess) return e;
+  k_face_flux<NV, FC, HALO><<<total, LINES * NV, smem, st>>>(S, alpha, Fx, Gy, g, nbx, ntx_x, ntx_y);
   return cudaGetLastError();
 }
 
@@ -186,14 +213,21 @@ static int flux_tile_faces(const GridDev& g) {
   return total >= 2 * sms ? 16 : 8;
 }
 
+template <int NV, bool HALO>
+static cudaError_t launch_face_flux_h(const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
+                                      const GridDev& g, cudaStream_t st) {
+  switch (flux_tile_faces(g)) {
+    case 32: return launch_face_flux_fc<NV, 32, HALO>(S, alpha, Fx, Gy, g, st);
+    case 16: return launch_face_flux_fc<NV, 16, HALO>(S, alpha, Fx, Gy, g, st);
+    default: return launch_face_flux_fc<NV, 8, HALO>(S, alpha, Fx, Gy, g, st);
+  }
+}
+
 template <int NV>
 static cudaError_t launch_face_flux_t(const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
                                       const GridDev& g, cudaStream_t st) {
-  switch (flux_tile_faces(g)) {
-    case 32: return launch_face_flux_fc<NV, 32>(S, alpha, Fx, Gy, g, st);
-    case 16: return launch_face_flux_fc<NV, 16>(S, alpha, Fx, Gy, g, st);
-    default: return launch_face_flux_fc<NV, 8>(S, alpha, Fx, Gy, g, st);
-  }
+  if (g.bc[0] == BC_HALO || g.bc[1] == BC_HALO) return launch_face_flux_h<NV, true>(S, alpha, Fx, Gy, g, st);
+  return launch_face_flux_h<NV, false>(S, alpha, Fx, Gy, g, st);
 }
 
 void face_flux_tiles(const GridDev& g, int* nbx, int* ntx_x, int* ntx_y, int* total) {
@@ -204,12 +238,10 @@ template <int NV>
 static cudaError_t launch_face_flux_batch_t(const BatchReq* reqs, const int* first, int nreq, int total, int state,
                                             cudaStream_t st) {
   const size_t smem = flux_smem_bytes<NV>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_face_flux_batch<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  cudaError_t e = set_attr_once((const void*)k_face_flux_batch<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem, &attr_done);
+  if (e != cudaSuccess) return e;
   const int sms = sm_count();
   const int grid = total < sms * 8 ? total : sms * 8;
   if (grid > 0) k_face_flux_batch<NV><<<grid, LINES * NV, smem, st>>>(reqs, first, nreq, state);

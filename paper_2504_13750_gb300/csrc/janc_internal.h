@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "../../include/janc.h"
 #include "janc_device.cuh"
 
@@ -65,7 +67,11 @@ cudaError_t launch_face_flux_batch(int nv, const BatchReq* reqs, const int* firs
                                    cudaStream_t st);
 cudaError_t launch_rk_update_batch(int ns, int stage, const BatchReq* reqs, const int* first, int nreq, int total,
                                    int chem, cudaStream_t st);
-cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, cudaStream_t st);
+cudaError_t launch_chem_batch(int ns, const BatchReq* reqs, const int* first, int nreq, int total, bool fixed,
+                              cudaStream_t st);
+// Whether a mechanism has the reaction structure compiled into the fixed
+// chemistry kernels (janc_mech_fixed.cuh; janc_chem.cu).
+bool fixed_structure(const janc_mechanism* m);
 
 // Streaming multiprocessors of the current device (queried once per device).
 int sm_count();
@@ -89,6 +95,14 @@ cudaError_t launch_dot(long long count, const double* a, const double* b, double
 cudaError_t launch_prim_T_vjp(int ns, const double* T, const double* p, const double* u, const double* v,
                               const double* Y, const double* dLdU, double* out, const GridDev& g,
                               const MechDev* mech, cudaStream_t st);
+
+// Halo pack of the x-slab exchange: the 3 columns of each of `planes` planes
+// of S nearest each x side into [planes][ny][3] buffers (janc_update.cu).
+cudaError_t launch_halo_pack(int planes, const StateView& S, const GridDev& g, double* lo_dst, double* hi_dst,
+                             cudaStream_t st);
+
+// Sets a kernel attribute once per device (janc_flux.cu).
+cudaError_t set_attr_once(const void* func, cudaFuncAttribute attr, int value, std::atomic<unsigned long long>* done);
 
 // L = -(dF/dx + dG/dy) from the face fluxes.
 cudaError_t launch_rhs_L(int nv, const double* Fx, const double* Gy, double* L, const GridDev& g, cudaStream_t st);

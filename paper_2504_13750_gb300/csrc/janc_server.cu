@@ -56,6 +56,7 @@ struct Req {
   int fresh = 0;
   cudaEvent_t ev_done = nullptr, ev_copy = nullptr;
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+  bool reported = false;  // returned as finished by janc_server_run_until
 };
 
 // Device footprint of one request: 3 states, face fluxes, 5 alpha slots +
@@ -74,6 +75,7 @@ void req_layout(int nx, int ny, int nv, size_t* state, size_t* fx, size_t* gy, s
 struct janc_server_s {
   int ns = 0, nv = 0, chem = 0;
   MechDev* dmech = nullptr;
+  bool chem_fixed = false;  // the mechanism has the compiled reaction structure
   char* pool_base = nullptr;
   bool owns_pool = false;
   Pool pool;
@@ -94,6 +96,10 @@ struct janc_server_s {
   int tot[3] = {0, 0, 0};
   long long macro_steps = 0;
   janc_grid_desc defaults;
+  // janc_server_run_until keeps at most two macro-steps in flight: the event
+  // of each macro-step's end, alternating
+  cudaEvent_t step_ev[2] = {nullptr, nullptr};
+  int step_k = 0;
 };
 
 namespace {
@@ -129,6 +135,7 @@ void fill_batchreq(janc_server_s* s, Req* r) {
   g.eps4 = 4.0 * (r->d.weno_eps > 0.0 ? r->d.weno_eps : 1e-6);
   g.newton_tol = r->d.newton_tol > 0.0 ? r->d.newton_tol : 1e-12;
   g.newton_maxit = r->d.newton_maxit > 0 ? r->d.newton_maxit : 50;
+  g.chem_fixed = s->chem_fixed ? 1 : 0;
   for (int k = 0; k < 3; ++k) b.S[k].base = (double*)(base + k * st);
   b.Fx = (double*)(base + 3 * st);
   b.Gy = (double*)(base + 3 * st + fx);
@@ -286,6 +293,7 @@ int janc_server_create(const janc_mechanism* m, int chemistry, size_t pool_bytes
   s->stream = (cudaStream_t)cuda_stream;
   MechDev hm;
   rc = build_mech_table(m, &hm);
+  s->chem_fixed = fixed_structure(m);
   if (rc) { delete s; return rc; }
   cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
   const size_t mech_b = a256(sizeof(MechDev));
@@ -384,56 +392,132 @@ int janc_server_submit(janc_server_t s, const janc_grid_desc* d, const double* T
   return JANC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One macro-step: retire finished copies, admit, then one batched step of
+// every active request and the retirement of those that are done. *ran is
+// false when nothing was active after admission.
+int macro_step(janc_server_s* s, bool* ran) {
+  *ran = false;
+  reap(s);
+  try_admit(s);
+  if (s->active.empty()) return JANC_OK;
+  if (s->dirty) {
+    int rc = upload(s);
+    if (rc) return rc;
+  }
+  const int na = (int)s->active.size();
+  const int* f0 = s->d_first;
+  const int* f1 = s->d_first + (s->max_active + 1);
+  const int* f2 = s->d_first + 2 * (s->max_active + 1);
+  cudaError_t e = launch_batch_prep(s->d_reqs, na, s->stream);
+  for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
+    e = launch_face_flux_batch(s->nv, s->d_reqs, f0, na, s->tot[0], stage - 1, s->stream);
+    if (e == cudaSuccess) e = launch_rk_update_batch(s->ns, stage, s->d_reqs, f1, na, s->tot[1], s->chem, s->stream);
+  }
+  if (e == cudaSuccess && s->chem)
+    e = launch_chem_batch(s->ns, s->d_reqs, f2, na, s->tot[2], s->chem_fixed, s->stream);
+  if (e != cudaSuccess) return scuda(e, "batched step");
+  ++s->macro_steps;
+  *ran = true;
+  std::vector<int> still;
+  for (int id : s->active) {
+    Req* r = s->reqs[id];
+    r->fresh = 0;
+    if (++r->steps_done >= r->n_steps) {
+      int rc = retire(s, r);
+      if (rc) return rc;
+      s->dirty = true;
+    } else {
+      still.push_back(id);
+    }
+  }
+  s->active.swap(still);
+  return JANC_OK;
+}
+
+void fill_info(janc_server_s* s, janc_server_info* info) {
+  if (!info) return;
+  std::memset(info, 0, sizeof *info);
+  info->n_queued = (int)s->queue.size();
+  info->n_active = (int)s->active.size();
+  for (Req* r : s->reqs) {
+    if (!r) continue;
+    if (r->state == R_COPYING) ++info->n_copying;
+    if (r->state == R_DONE || r->state == R_FAILED) ++info->n_done;
+  }
+  info->pool_used = s->pool.used;
+  info->pool_bytes = s->pool.size;
+  info->macro_steps = s->macro_steps;
+}
+
+// Newly finished (done or failed, not yet returned) requests into ids[0..cap).
+void collect_finished(janc_server_s* s, int* ids, int cap, int* n) {
+  reap(s);
+  for (Req* r : s->reqs) {
+    if (*n >= cap) break;
+    if (!r || r->reported || (r->state != R_DONE && r->state != R_FAILED)) continue;
+    r->reported = true;
+    ids[(*n)++] = r->id;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
 int janc_server_run(janc_server_t s, int macro_steps, janc_server_info* info) {
   if (!s || macro_steps < 0) return sfail(JANC_E_INVALID, "janc_server_run: bad argument");
   for (int k = 0; k < macro_steps; ++k) {
-    reap(s);
-    try_admit(s);
-    if (s->active.empty()) break;
-    if (s->dirty) {
-      int rc = upload(s);
-      if (rc) return rc;
-    }
-    const int na = (int)s->active.size();
-    const int* f0 = s->d_first;
-    const int* f1 = s->d_first + (s->max_active + 1);
-    const int* f2 = s->d_first + 2 * (s->max_active + 1);
-    cudaError_t e = launch_batch_prep(s->d_reqs, na, s->stream);
-    for (int stage = 1; stage <= 3 && e == cudaSuccess; ++stage) {
-      e = launch_face_flux_batch(s->nv, s->d_reqs, f0, na, s->tot[0], stage - 1, s->stream);
-      if (e == cudaSuccess) e = launch_rk_update_batch(s->ns, stage, s->d_reqs, f1, na, s->tot[1], s->chem, s->stream);
-    }
-    if (e == cudaSuccess && s->chem) e = launch_chem_batch(s->ns, s->d_reqs, f2, na, s->tot[2], s->stream);
-    if (e != cudaSuccess) return scuda(e, "batched step");
-    ++s->macro_steps;
-    std::vector<int> still;
-    for (int id : s->active) {
-      Req* r = s->reqs[id];
-      r->fresh = 0;
-      if (++r->steps_done >= r->n_steps) {
-        int rc = retire(s, r);
-        if (rc) return rc;
-        s->dirty = true;
-      } else {
-        still.push_back(id);
-      }
-    }
-    s->active.swap(still);
+    bool ran = false;
+    const int rc = macro_step(s, &ran);
+    if (rc) return rc;
+    if (!ran) break;
   }
   reap(s);
-  if (info) {
-    std::memset(info, 0, sizeof *info);
-    info->n_queued = (int)s->queue.size();
-    info->n_active = (int)s->active.size();
-    for (Req* r : s->reqs) {
-      if (!r) continue;
-      if (r->state == R_COPYING) ++info->n_copying;
-      if (r->state == R_DONE || r->state == R_FAILED) ++info->n_done;
+  fill_info(s, info);
+  return JANC_OK;
+}
+
+int janc_server_run_until(janc_server_t s, int max_macro_steps, double max_wall_s, int* done_ids, int cap,
+                          int* n_done, janc_server_info* info) {
+  if (!s || max_macro_steps < 0 || !(max_wall_s >= 0.0) || !n_done || cap < 0 || (cap > 0 && !done_ids))
+    return sfail(JANC_E_INVALID, "janc_server_run_until: bad argument");
+  *n_done = 0;
+  const double t0 = now_s();
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+    if (!s->step_ev[q]) e = cudaEventCreateWithFlags(&s->step_ev[q], cudaEventDisableTiming);
+  if (e != cudaSuccess) return scuda(e, "janc_server_run_until");
+  collect_finished(s, done_ids, cap, n_done);
+  for (int k = 0; k < max_macro_steps && *n_done == 0; ++k) {
+    // at most two macro-steps in flight: wait for the end of the one before
+    // the previous, so that finished copies are seen about one step late
+    e = cudaEventSynchronize(s->step_ev[s->step_k]);
+    if (e != cudaSuccess) return scuda(e, "janc_server_run_until");
+    bool ran = false;
+    const int rc = macro_step(s, &ran);
+    if (rc) return rc;
+    if (ran) {
+      e = cudaEventRecord(s->step_ev[s->step_k], s->stream);
+      if (e != cudaSuccess) return scuda(e, "janc_server_run_until");
+      s->step_k ^= 1;
     }
-    info->pool_used = s->pool.used;
-    info->pool_bytes = s->pool.size;
-    info->macro_steps = s->macro_steps;
+    collect_finished(s, done_ids, cap, n_done);
+    if (*n_done > 0) break;
+    if (!ran) {
+      // nothing active: wait for the copies of retired requests (they hold
+      // the pool memory a queued request may be waiting for)
+      e = cudaStreamSynchronize(s->copy_stream);
+      if (e != cudaSuccess) return scuda(e, "janc_server_run_until");
+      collect_finished(s, done_ids, cap, n_done);
+      if (*n_done > 0 || s->queue.empty()) break;
+    }
+    if (now_s() - t0 >= max_wall_s) break;
   }
+  fill_info(s, info);
   return JANC_OK;
 }
 
@@ -495,6 +579,7 @@ void janc_server_destroy(janc_server_t s) {
   for (int k = 0; k < 2; ++k) {
     if (s->h_stage[k]) cudaFreeHost(s->h_stage[k]);
     if (s->stage_ev[k]) cudaEventDestroy(s->stage_ev[k]);
+    if (s->step_ev[k]) cudaEventDestroy(s->step_ev[k]);
   }
   if (s->owns_pool && s->dmech) cudaFree((void*)s->dmech);
   delete s;

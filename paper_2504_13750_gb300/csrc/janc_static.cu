@@ -103,7 +103,7 @@ int janc_rhs_static(const janc_grid_desc* d, const janc_mechanism* m, const doub
   int* status = (int*)(a + 2);
   MechDev* dm = (MechDev*)(base + state + fx + gy + slots);
 
-  GridDev g;
+  GridDev g = {};
   g.nx = d->nx;
   g.ny = d->ny;
   g.n = n;

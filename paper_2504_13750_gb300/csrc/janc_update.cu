@@ -304,6 +304,35 @@ cudaError_t launch_set_conserved(int ns, const StateView& S, const double* T0, c
   return cudaGetLastError();
 }
 
+// Halo pack of the x-slab exchange (Sec. 4.4, Fig. 3): the 3 columns of
+// every plane of S nearest each x side, into the halo layout [planes][ny][3]
+// (lo_dst: columns 0..2, hi_dst: columns nx-3..nx-1; either may be null).
+// Thread per (side, plane, row, column); the destinations are contiguous.
+__global__ void k_halo_pack(StateView S, int planes, int nx, int ny, long long n, double* __restrict__ lo_dst,
+                            double* __restrict__ hi_dst) {
+  const long long per = (long long)planes * ny * 3;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 2 * per) return;
+  const bool hi = q >= per;
+  double* dst = hi ? hi_dst : lo_dst;
+  if (!dst) return;
+  const long long r = hi ? q - per : q;
+  const int c = (int)(r % 3);
+  const long long pj = r / 3;  // plane * ny + row
+  const int k = (int)(pj / ny);
+  const int j = (int)(pj % ny);
+  const int i = hi ? nx - 3 + c : c;
+  dst[r] = S.plane(k, n)[(long long)j * nx + i];
+}
+
+cudaError_t launch_halo_pack(int planes, const StateView& S, const GridDev& g, double* lo_dst, double* hi_dst,
+                             cudaStream_t st) {
+  if (!lo_dst && !hi_dst) return cudaSuccess;
+  const long long tot = 2LL * planes * g.ny * 3;
+  k_halo_pack<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(S, planes, g.nx, g.ny, g.n, lo_dst, hi_dst);
+  return cudaGetLastError();
+}
+
 __global__ void k_rhs_L(int nv, const double* __restrict__ Fx, const double* __restrict__ Gy, double* __restrict__ L,
                         GridDev g) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -95,6 +95,7 @@ def lib():
             L.janc_server_footprint.argtypes = [p, p, ctypes.POINTER(ctypes.c_size_t)]
             L.janc_server_submit.argtypes = [p, p, p, p, p, p, p, i, d, d, ctypes.POINTER(i)]
             L.janc_server_run.argtypes = [p, i, p]
+            L.janc_server_run_until.argtypes = [p, i, d, p, i, ctypes.POINTER(i), p]
             L.janc_server_poll.argtypes = [p, i, p]
             L.janc_server_fetch.argtypes = [p, i, p, p]
             L.janc_server_set_cell_budget.argtypes = [p, ctypes.c_longlong, d]
@@ -119,6 +120,19 @@ def lib():
             L.janc_amr_cell_updates.argtypes = [p, ctypes.POINTER(ctypes.c_longlong)]
             L.janc_amr_destroy.argtypes = [p]
             L.janc_amr_destroy.restype = None
+            sz = ctypes.c_size_t
+            L.janc_slab_partition.argtypes = [i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+            L.janc_slab_halo_doubles.argtypes = [p, p, ctypes.POINTER(sz)]
+            L.janc_slab_create.argtypes = [p, p, i, i, p, p, sz, p, ctypes.POINTER(p)]
+            L.janc_split_create.argtypes = [p, p, i, p, ctypes.POINTER(p)]
+            L.janc_split_set_state.argtypes = [p, p, p, i]
+            L.janc_split_set_state_primitive.argtypes = [p, p, p, p, p, p, i]
+            L.janc_split_step.argtypes = [p, i, d, d, p, p]
+            L.janc_split_get_state.argtypes = [p, p, p, i]
+            L.janc_split_status.argtypes = [p, p]
+            L.janc_split_slab.argtypes = [p, i, ctypes.POINTER(p)]
+            L.janc_split_destroy.argtypes = [p]
+            L.janc_split_destroy.restype = None
             _lib = L
         return _lib
 
@@ -401,6 +415,17 @@ def janc_server_run(s, macro_steps=1) -> dict:
     return {k: getattr(info, k) for k, _ in janc_server_info._fields_}
 
 
+def janc_server_run_until(s, max_macro_steps=1 << 30, max_wall_s=1e9, cap=256):
+    """(ids of newly finished requests, info dict): see include/janc.h."""
+    ids = np.zeros(max(int(cap), 1), dtype=np.int32)
+    n = ctypes.c_int()
+    info = janc_server_info()
+    _check(lib().janc_server_run_until(s, int(max_macro_steps), float(max_wall_s),
+                                       ids.ctypes.data_as(ctypes.c_void_p), int(cap), ctypes.byref(n),
+                                       ctypes.byref(info)))
+    return [int(x) for x in ids[:n.value]], {k: getattr(info, k) for k, _ in janc_server_info._fields_}
+
+
 def janc_server_poll(s, rid) -> dict:
     ri = janc_request_info()
     _check(lib().janc_server_poll(s, int(rid), ctypes.byref(ri)))
@@ -481,6 +506,148 @@ class Grid:
     def close(self):
         if getattr(self, "handle", None):
             janc_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- x-slab decomposition ------------------------------------------------------------------
+
+# int (*)(void* user, void* cuda_stream): the exchange callback of a stand-alone slab.
+JANC_EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class janc_slab_exchange(ctypes.Structure):
+    _fields_ = [("send_lo", ctypes.c_void_p), ("send_hi", ctypes.c_void_p), ("recv_lo", ctypes.c_void_p),
+                ("recv_hi", ctypes.c_void_p), ("alpha2", ctypes.c_void_p), ("fn", JANC_EXCHANGE_FN),
+                ("user", ctypes.c_void_p)]
+
+
+def janc_slab_partition(nx, n_slabs, k):
+    """(x0, nx_local) of slab k of n_slabs over nx columns."""
+    x0, w = ctypes.c_int(), ctypes.c_int()
+    _check(lib().janc_slab_partition(int(nx), int(n_slabs), int(k), ctypes.byref(x0), ctypes.byref(w)))
+    return x0.value, w.value
+
+
+def janc_slab_halo_doubles(desc, mech: Mechanism) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().janc_slab_halo_doubles(ctypes.byref(desc), ctypes.byref(mech.c), ctypes.byref(out)))
+    return out.value
+
+
+def janc_slab_create(desc, mech: Mechanism, x0, nx_local, xch: janc_slab_exchange, workspace_ptr=None,
+                     workspace_bytes=0, stream=None):
+    """A slab grid handle (use it with janc_set_state, janc_step, ...). `xch`
+    and the callback it holds must stay alive until janc_destroy_grid."""
+    h = ctypes.c_void_p()
+    _check(lib().janc_slab_create(ctypes.byref(desc), ctypes.byref(mech.c), int(x0), int(nx_local), ctypes.byref(xch),
+                                  ctypes.c_void_p(workspace_ptr) if workspace_ptr else None, int(workspace_bytes),
+                                  ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+    return h
+
+
+def janc_split_create(desc, mech: Mechanism, n_slabs, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().janc_split_create(ctypes.byref(desc), ctypes.byref(mech.c), int(n_slabs),
+                                   ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+    return h
+
+
+def janc_split_set_state(s, U, T0=None):
+    a, b = _arg(U), _arg(T0)
+    _check(lib().janc_split_set_state(s, a[0], b[0], _where(a, b)))
+
+
+def janc_split_set_state_primitive(s, T, p, u, v, Y):
+    args = [_arg(x) for x in (T, p, u, v, Y)]
+    _check(lib().janc_split_set_state_primitive(s, *[x[0] for x in args], _where(*args)))
+
+
+def janc_split_step(s, n_steps, dt=0.0, cfl=0.0, want_time=False):
+    """Returns (t, dt_last) when want_time (synchronises), else None."""
+    if want_time:
+        t, dl = ctypes.c_double(), ctypes.c_double()
+        _check(lib().janc_split_step(s, int(n_steps), float(dt), float(cfl), ctypes.byref(t), ctypes.byref(dl)))
+        return t.value, dl.value
+    _check(lib().janc_split_step(s, int(n_steps), float(dt), float(cfl), None, None))
+    return None
+
+
+def janc_split_get_state(s, U=None, T=None, check=True):
+    a, b = _arg(U, True), _arg(T, True)
+    rc = lib().janc_split_get_state(s, a[0], b[0], _where(a, b))
+    if check:
+        _check(rc)
+    return rc
+
+
+def janc_split_status(s):
+    st = janc_status_info()
+    _check(lib().janc_split_status(s, ctypes.byref(st)))
+    return {"status": st.status, "steps_done": st.steps_done, "t": st.t, "dt_last": st.dt_last,
+            "alpha": (st.alpha[0], st.alpha[1])}
+
+
+def janc_split_slab(s, k):
+    h = ctypes.c_void_p()
+    _check(lib().janc_split_slab(s, int(k), ctypes.byref(h)))
+    return h
+
+
+def janc_split_destroy(s):
+    lib().janc_split_destroy(s)
+
+
+class Split:
+    """Owner of a single-process x-slab split of one domain (janc_split_*) on
+    the current CUDA device and stream; whole-domain arrays in and out."""
+
+    def __init__(self, mech: dict, nx, ny, dx, dy, bc, n_slabs, chemistry=True, stream=None, **kw):
+        import torch
+
+        self.mech = Mechanism(mech)
+        self.ns = self.mech.ns
+        self.nv = self.ns + 3
+        self.nx, self.ny, self.n_slabs = int(nx), int(ny), int(n_slabs)
+        self.desc = make_desc(nx, ny, dx, dy, bc, chemistry=chemistry, **kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = janc_split_create(self.desc, self.mech, n_slabs, self.stream.cuda_stream)
+
+    @classmethod
+    def from_grid_dict(cls, mech, g, n_slabs, chemistry=True, **kw):
+        return cls(mech, g["nx"], g["ny"], g["dx"], g["dy"], g["bc"], n_slabs, chemistry=chemistry,
+                   weno_eps=g.get("weno_eps", 1e-6), newton_tol=g.get("newton_tol", 1e-12),
+                   newton_maxit=g.get("newton_maxit", 50), **kw)
+
+    def columns(self):
+        return [janc_slab_partition(self.nx, self.n_slabs, k) for k in range(self.n_slabs)]
+
+    def set_state(self, U, T0=None):
+        janc_split_set_state(self.handle, U, T0)
+
+    def set_primitive(self, T, p, u, v, Y):
+        janc_split_set_state_primitive(self.handle, T, p, u, v, Y)
+
+    def step(self, n, dt=0.0, cfl=0.0, want_time=False):
+        return janc_split_step(self.handle, n, dt=dt, cfl=cfl, want_time=want_time)
+
+    def get_state(self, check=True):
+        U = np.zeros((self.nv, self.ny, self.nx))
+        T = np.zeros((self.ny, self.nx))
+        janc_split_get_state(self.handle, U, T, check=check)
+        return U, T
+
+    def status(self):
+        return janc_split_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            janc_split_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

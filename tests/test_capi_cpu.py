@@ -167,3 +167,20 @@ def test_rhs_static_refuses_mismatched_buffers_before_the_call():
                 dict(L=Buf(12 * cells, dev=1)), dict(T=None)):
         with pytest.raises(ValueError):
             janc._rhs_static_shapes(d, ns, device=0, **dict(ok, **bad))
+
+
+def test_fixed_structure_header_is_generated_from_the_mechanism():
+    """csrc/janc_mech_fixed.cuh is exactly what mech_codegen writes from the
+    shipped mechanism file, and encodes its structure: species and
+    coefficients of every reaction side, third-body flags, and the species
+    with a third-body coefficient other than one."""
+    from paper_2504_13750_gb300 import mech_codegen
+
+    with open(mech_codegen.HEADER) as f:
+        assert f.read() == mech_codegen.render()
+    m = inputs.load_mechanism("h2air_synth")
+    sp, rx = mech_codegen.structure()
+    assert sp == m["species"] and len(rx) == m["nr"]
+    for i, r in enumerate(rx):
+        assert r["nuf"] == list(m["nuf"][i]) and r["nub"] == list(m["nub"][i]) and r["tb"] == int(m["tb"][i])
+        assert r["eff_ne1"] == [k for k in range(m["ns"]) if m["tb"][i] and m["eff"][i][k] != 1.0]

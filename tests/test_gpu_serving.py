@@ -178,3 +178,37 @@ def test_submit_validation(J):
                                  cfl=0.5)
     finally:
         J.janc_server_destroy(s)
+
+
+def test_run_until_returns_each_request_once(J):
+    """janc_server_run_until serves the stream without polling: every request
+    is returned exactly once (at most `cap` per call, the rest on later
+    calls), and its result is the one it gets alone, bit for bit."""
+    reqs = _requests()
+    alone = [_alone(J, st, req["steps"]) for req, st in reqs]
+    mech = J.Mechanism(H2AIR)
+    s = J.janc_server_create(mech, chemistry=True, pool_bytes=2 << 30, max_active=64)
+    try:
+        ids = []
+        for req, st in reqs:
+            g = st["grid"]
+            d = J.make_desc(g["nx"], g["ny"], g["dx"], g["dy"], g["bc"], chemistry=True)
+            ids.append(J.janc_server_submit(s, d, st["T"], st["p"], st["u"], st["v"], st["Y"], req["steps"], cfl=0.5))
+        done, info = J.janc_server_run_until(s, max_macro_steps=1, cap=2)
+        assert info["macro_steps"] == 1 and done == []  # one macro-step: nothing can have finished
+        seen = []
+        for _ in range(1000):
+            done, info = J.janc_server_run_until(s, cap=2)
+            assert len(done) <= 2
+            seen += done
+            if len(seen) == len(ids):
+                break
+        assert sorted(seen) == sorted(ids) and len(set(seen)) == len(seen)
+        assert J.janc_server_run_until(s, cap=2)[0] == []
+        for rid, (req, st), (Ua, Ta) in zip(ids, reqs, alone):
+            U = np.zeros((12, req["ny"], req["nx"]))
+            T = np.zeros((req["ny"], req["nx"]))
+            J.janc_server_fetch(s, rid, U, T)
+            assert np.array_equal(U, Ua) and np.array_equal(T, Ta)
+    finally:
+        J.janc_server_destroy(s)
