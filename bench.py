@@ -126,6 +126,65 @@ def weno_flops():
         return json.load(f)["weno5"]["flops"]
 
 
+def chem_flops_per_cell(mech):
+    """Algorithmic FP64 flops of one point-implicit chemistry update of one
+    cell (Eq. 4.6-4.13) followed by the Newton T recovery (Eq. 4.2-4.4), in
+    the plain analytic form of the method, counted from the mechanism's
+    structure: a fused multiply-add is 2 flops, and exp, log, reciprocal and
+    square root 1 each (so the count is a lower bound of the work). It is
+    the method's count, not the kernel's instruction count nor the oracle's
+    (whose Jacobian comes from dual numbers).
+
+    Terms: concentrations and their sum; per species the Gibbs polynomial of
+    Eq. 4.9 and exp(G), 1/exp(G); per reaction k_f (Eq. 4.8), k_b through
+    K_eq (products of exp(G) and P_ref/RT), the mass-action products, the
+    third-body sum (Eq. 4.7), the rate of progress, the production rates and
+    the analytic Jacobian entries (participants x carried rows, the closure
+    column of the last species, the third-body rows); A = I - dt J and dt w;
+    the 8 x 8 LU with partial pivoting and the two triangular solves; the
+    update; Newton with the mixture-sum form of the thermodynamics (two
+    iterations, as the tube's cells take) and p, c."""
+    ns = int(mech["ns"])
+    nsp = ns - 1
+    f = 0
+    f += 2 * nsp + 1 + (ns - 1)             # X_k, X_ns, C_tot
+    f += 2                                  # ln T, 1/T
+    f += ns * (2 * 6 + 2)                   # G_k (6 FMA), exp, reciprocal
+    f += 2                                  # P_ref/(Ru T), its inverse
+    for i in range(int(mech["nr"])):
+        nuf, nub = mech["nuf"][i], mech["nub"][i]
+        re = [(k, int(nuf[k])) for k in range(ns) if nuf[k]]
+        pr = [(k, int(nub[k])) for k in range(ns) if nub[k]]
+        dnu = sum(n for _, n in pr) - sum(n for _, n in re)
+        f += 2 * 2 + 1                      # ln k_f = lnA + b ln T - Ea/(Ru T); exp
+        f += sum(n for _, n in re) + sum(n for _, n in pr) + abs(dnu)   # k_b
+        f += sum(n for _, n in re) + sum(n for _, n in pr)              # mass action
+        tb = int(mech["tb"][i])
+        neff = sum(1 for k in range(ns) if tb and mech["eff"][i][k] != 1.0)
+        f += 2 * neff                       # third-body sum
+        f += 2                              # net, q
+        rows = [k for k, _ in re + pr if k < nsp]
+        f += 2 * len(rows)                  # production rates
+        for side in (re, pr):               # d q / d X_j of every participant
+            for _, n in side:
+                f += (1 if n > 1 else 0) + sum(m for _, m in side) - 1 + 1
+        for k in rows:                      # Jacobian rows
+            for j, _ in re + pr:
+                f += 2 if j < nsp else 1 + 2 * nsp
+            if tb:
+                f += 1 + 2 * nsp
+    f += 2 * nsp * nsp + nsp                # A = I - dt J, b = dt w
+    for c in range(nsp):                    # LU with partial pivoting
+        f += 1 + (nsp - 1 - c) * (1 + 2 * (nsp - 1 - c) + 2)
+    f += sum(2 * (nsp - 1 - r) + 1 for r in range(nsp))   # back substitution
+    f += 2 * nsp                            # rho Y_k += M_k x_k
+    f += 1 + 2 * nsp + 6 * (1 + 2 * nsp)    # Newton: 1/rho, W and the enthalpy sums
+    f += 8                                  # kinetic energy, rho e / Ru, constants
+    f += 2 * (2 * 5 + 2 * 4 + 1 + 1 + 1)    # two iterations: F, F', dT = -F/F', T += dT
+    f += 2 * 4 + 1 + 1 + 4 + 1              # C_v, C_p, p, c (with the square root)
+    return f
+
+
 # ----------------------------------------------------------------------------
 def cpu_baseline_oracle(mech, st, steps=5):
     """The oracle as it stands on the host cores: `steps` full steps of the
@@ -244,7 +303,7 @@ SERVE_BUDGET_CELLS = 600_000   # just above the largest request (2048 x 256)
 SERVE_MAX_SKIP_S = 1.0
 
 
-def run_serving(janc, stream, n_req, steps_range, seed=1):
+def run_serving(janc, stream, n_req, steps_range, seed=1, grids="all"):
     """Serving leg: solves of mixed size and mixture arriving as a Poisson
     stream at 1.5x the one-at-a-time capacity, served by the batched server
     (active set capped at 600k cells, later requests may pass a blocked one
@@ -254,7 +313,8 @@ def run_serving(janc, stream, n_req, steps_range, seed=1):
 
     mech = inputs.load_mechanism("h2air_synth")
     mech_c = janc.Mechanism(mech)
-    reqs = inputs.serving_requests(mech, n=n_req, seed=seed, steps_range=steps_range)
+    sizes = inputs.SERVING_GRIDS if grids == "all" else inputs.SERVING_GRIDS[:2]
+    reqs = inputs.serving_requests(mech, n=n_req, seed=seed, steps_range=steps_range, grids=sizes)
     states = [inputs.request_state(mech, r) for r in reqs]
     cell_steps = [r["nx"] * r["ny"] * r["steps"] for r in reqs]
     pool = 16 << 30
@@ -270,7 +330,7 @@ def run_serving(janc, stream, n_req, steps_range, seed=1):
     rng = np.random.default_rng(seed + 100)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     arrivals = list(arrivals - arrivals[0])
-    out = {"requests": n_req, "steps_range": list(steps_range), "grids": [list(g) for g in inputs.SERVING_GRIDS],
+    out = {"requests": n_req, "steps_range": list(steps_range), "grids": [list(g) for g in sizes],
            "cell_steps": int(sum(cell_steps)),
            "capacity_solves_per_s": {"batched": n_req / span_bat, "one_at_a_time": cap_seq,
                                      "batched_uncapped": n_req / span_ps},
@@ -467,6 +527,54 @@ def run_split_leg(janc, stream, n_slabs=4, steps=10, warm=3):
             "value": NX * NY * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps}
 
 
+def tube_totals(mech, U):
+    """Host totals of a tube state for the conservation record: mass, energy
+    and the moles of each element (from the species' element counts)."""
+    ns = int(mech["ns"])
+    rhoY = np.concatenate([U[4:4 + ns - 1], (U[0] - U[4:4 + ns - 1].sum(axis=0))[None]], axis=0)
+    moles = rhoY.reshape(ns, -1).sum(axis=1) / np.asarray(mech["M"])
+    el = mech["elements"]
+    names = sorted({e for sp in mech["species"] for e in el[sp]})
+    E = np.array([[el[sp].get(e, 0) for sp in mech["species"]] for e in names], dtype=float)
+    out = {"mass": float(U[0].sum()), "energy": float(U[3].sum())}
+    out.update({f"element_{e}": float(v) for e, v in zip(names, E @ moles)})
+    return out
+
+
+def run_config2_full(janc, stream, steps=2000):
+    """The 4096 x 512 tube for its full horizon (cellular detonation): one
+    janc_step call of `steps` CFL steps, timed with CUDA events; the status
+    word afterwards, the minimum rho, p, T of the final state, and the drift
+    of mass, energy and element totals (slip walls conserve them to roundoff)."""
+    import torch
+
+    mech, st = tube_state()
+    g = janc.Grid(mech, NX, NY, st["grid"]["dx"], st["grid"]["dy"], st["grid"]["bc"], chemistry=True, stream=stream)
+    g.set_primitive(st["T"], st["p"], st["u"], st["v"], np.ascontiguousarray(st["Y"]))
+    U0, _ = g.get_state()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps, cfl=CFL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stt = g.status()
+    U1, T1 = g.get_state(check=False)
+    g.close()
+    a, b = tube_totals(mech, U0), tube_totals(mech, U1)
+    nv = U1.shape[0]
+    rho = U1[0]
+    # p = Ru T sum_k rho Y_k / M_k (Eq. 4.2), for the record of the final state
+    M = np.asarray(mech["M"])
+    rhoY = np.concatenate([U1[4:nv], (rho - U1[4:nv].sum(axis=0))[None]], axis=0)
+    p = float(np.min(8.314472 * (rhoY / M[:, None, None]).sum(axis=0) * T1))
+    return {"workload": workload_name(), "steps": steps, "value": NX * NY * steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / steps, "t_sim_s": stt["t"], "status": stt["status"],
+            "min_rho": float(rho.min()), "min_T": float(T1.min()), "max_T": float(T1.max()), "min_p": p,
+            "relative_drift": {k: (b[k] - a[k]) / abs(a[k]) for k in a}}
+
+
 def run_config1(janc, stream, with_cpu=True):
     """The 256 x 32 tube of config 1, all 200 steps at CFL 0.5: on the GPU
     (one janc_step call, CUDA events) and, on rank 0, through the oracle on
@@ -623,6 +731,16 @@ def run_ours(args):
                 "frac": bytes_launch / (ff_ms / ff_n * 1e-3) / 1e9 / hbm, "bytes_per_launch": bytes_launch}
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / total_prof if total_prof else None}
                for k, v in prof.items()}
+    # chemistry: FP64 ALU bound; algorithmic flops of the method per cell
+    ch_ms, ch_n = prof["chemistry"]
+    chem_fpc = chem_flops_per_cell(mech)
+    chem_ach = chem_fpc * cells / (ch_ms / ch_n * 1e-3) / 1e12
+    roof_chem = {"bound": "alu", "achieved": chem_ach, "peak": fp64_nominal, "unit": "TFLOP/s",
+                 "frac": chem_ach / fp64_nominal, "kernel": "k_chem", "flops_per_cell": chem_fpc,
+                 "flops_count": "plain analytic form of Eq. 4.6-4.13 and Newton T from the mechanism's structure; "
+                                "FMA = 2 flops, exp/log/reciprocal/sqrt = 1",
+                 "avg_launch_ms": ch_ms / ch_n, "frac_of_measured_dfma": chem_ach / fp64_measured,
+                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -634,6 +752,7 @@ def run_ours(args):
         "e2e": e2e,
         "roofline": roof,
         "roofline_hbm": roof_hbm,
+        "roofline_chem": roof_chem,
         "kernels": kernels,
         "gpu_launches": int(sum(v[1] for v in prof.values())),
         "clocks": clk.summary(),
@@ -674,9 +793,11 @@ def run_only(args):
     elif args.only == "inverse":
         out = run_inverse(janc, iters=args.leg_steps or 15)
     elif args.only == "serving":
-        out = run_serving(janc, stream, args.serving_requests, tuple(args.serving_steps))
+        out = run_serving(janc, stream, args.serving_requests, tuple(args.serving_steps), grids=args.serving_grids)
     elif args.only == "split":
         out = run_split_leg(janc, stream, steps=args.leg_steps or 10)
+    elif args.only == "config2":
+        out = run_config2_full(janc, stream, steps=args.leg_steps or 2000)
     else:
         out = run_amr(janc, stream, steps=args.leg_steps or 40)
     print(json.dumps(out), flush=True)
@@ -703,7 +824,9 @@ def main():
     ap.add_argument("--serving-steps", type=int, nargs=2, default=(50, 150))
     ap.add_argument("--nx", type=int, default=NX, help="tube cells along x (default: the 4096 x 512 workload)")
     ap.add_argument("--ny", type=int, default=NY)
-    ap.add_argument("--only", choices=("adjoint", "amr", "inverse", "serving", "split"), default=None,
+    ap.add_argument("--serving-grids", choices=("all", "small"), default="all",
+                    help="request grids: all five sizes, or only 128x16 and 256x32")
+    ap.add_argument("--only", choices=("adjoint", "amr", "inverse", "serving", "split", "config2"), default=None,
                     help="run one side leg alone and print its JSON object (for profiling)")
     ap.add_argument("--leg-steps", type=int, default=None,
                     help="with --only: adjoint trajectory steps (checkpoint every steps/10) or timed AMR base steps")

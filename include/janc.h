@@ -495,8 +495,11 @@ int janc_rhs_static(const janc_grid_desc* d, const janc_mechanism* m, const doub
  * values after every RK stage; chemistry over the layer's dt), then the
  * four-to-one mean from the deepest layer up, onto the parent cells none of
  * whose children lies in an external band. The base dt is fixed or the CFL
- * of layer 0 at the step's start; layer i uses dt / 2^i. Chemistry:
- * JANC_CHEM_OFF or JANC_CHEM_LIE. nx, ny of the base must be multiples of 8. */
+ * of layer 0 at the step's start (computed on the device); layer i uses
+ * dt / 2^i. A step makes no host round trip; a regrid reads back one block
+ * count per layer. Layer buffers grow as needed and are kept until
+ * janc_amr_destroy. Chemistry: JANC_CHEM_OFF or JANC_CHEM_LIE. nx, ny of the
+ * base must be multiples of 8. */
 typedef struct janc_amr_s* janc_amr_t;
 
 typedef struct {
@@ -522,6 +525,17 @@ int janc_amr_set_state_primitive(janc_amr_t a, const double* T, const double* p,
  * null) receives the simulated time advanced. A crossover step advances the
  * base dt; a synchronous step advances dt (or the CFL dt of layer 0 / 2^levels). */
 int janc_amr_step(janc_amr_t a, int n_steps, double dt, double cfl, double* t_out);
+/* The block-list builder of the regrid, run on the device for checking:
+ * from flags[nby][nbx] (host; non-zero = the candidate block is refined) the
+ * blocks in (by, bx) order, *nblk of them, with pos[2 b] = bx and
+ * pos[2 b + 1] = by, map[by nbx + bx] = the block number or -1, and
+ * nbr[4 b + s] = the block across side s (north, south, west, east; the
+ * periodic partner on a periodic side of bc = {left, right, bottom, top}),
+ * -2 on a non-periodic domain side, -1 where the layer has no block (an
+ * external side). Host outputs; pos, map and nbr sized for every candidate.
+ * Synchronous; allocates scratch. */
+int janc_amr_block_lists(const unsigned char* flags, int nbx, int nby, const int* bc, int* pos, int* map, int* nbr,
+                         int* nblk);
 /* Blocks of layer `level` (1..levels). */
 int janc_amr_layer_blocks(janc_amr_t a, int level, int* nblk);
 /* Host copy of layer `level`: pos[2 b] = bx, pos[2 b + 1] = by of block b

@@ -31,6 +31,7 @@
 #include "janc_adjoint.cuh"
 #include "janc_device.cuh"
 #include "janc_internal.h"
+#include "janc_mech_policy.cuh"
 #include "janc_weno.cuh"
 
 namespace janc {
@@ -433,53 +434,93 @@ __global__ void k_adj_alpha(StateView S, GridDev g, const MechDev* __restrict__ 
 // chained to U* through X(U*) and the implicit dT/dU* of the Newton recovery.
 // ---------------------------------------------------------------------------
 
-// A mass-action monomial prod_s X_{sp_s}^{a_s} over n <= MAX_SIDE distinct
-// species: the value, the gradient g_s, the derivative along e (D), and the
-// gradient of D (h_s = sum_t e_t d2/dX_t dX_s).
-__device__ __forceinline__ void monomial(const double* X, const int* sp, const int* a, int n, const double* e,
-                                         double& val, double* g, double& D, double* h) {
+// A mass-action monomial prod_s X_{sp(s)}^{a(s)} over n <= MAX_SIDE distinct
+// species (sp, a: accessors of the reaction side): the value, the gradient
+// g_s, the derivative along e (D), and the gradient of D
+// (h_s = sum_t e_t d2/dX_t dX_s).
+template <class SP, class A>
+__device__ __forceinline__ void monomial(const double* X, SP sp, A a, int n, const double* e, double& val, double* g,
+                                         double& D, double* h) {
   double P[MAX_SIDE], P1[MAX_SIDE], P2[MAX_SIDE];
+#pragma unroll
   for (int s = 0; s < n; ++s) {
-    const double x = X[sp[s]];
+    const double x = X[sp(s)];
     double pw = 1.0;
-    for (int q = 0; q < a[s] - 2; ++q) pw *= x;  // x^(a-2)
-    P2[s] = a[s] >= 2 ? a[s] * (a[s] - 1) * pw : 0.0;
-    const double pw1 = a[s] >= 2 ? pw * x : 1.0;  // x^(a-1)
-    P1[s] = a[s] * pw1;
+#pragma unroll
+    for (int q = 0; q < a(s) - 2; ++q) pw *= x;  // x^(a-2)
+    P2[s] = a(s) >= 2 ? a(s) * (a(s) - 1) * pw : 0.0;
+    const double pw1 = a(s) >= 2 ? pw * x : 1.0;  // x^(a-1)
+    P1[s] = a(s) * pw1;
     P[s] = pw1 * x;
   }
   val = 1.0;
+#pragma unroll
   for (int s = 0; s < n; ++s) val *= P[s];
   D = 0.0;
+#pragma unroll
   for (int s = 0; s < n; ++s) {
     double ex = P1[s];
+#pragma unroll
     for (int t = 0; t < n; ++t)
       if (t != s) ex *= P[t];
     g[s] = ex;
-    D = fma(e[sp[s]], ex, D);
+    D = fma(e[sp(s)], ex, D);
   }
+#pragma unroll
   for (int s = 0; s < n; ++s) {
     double hs = 0.0;
+#pragma unroll
     for (int t = 0; t < n; ++t) {
       double v;
       if (t == s) {
         v = P2[s];
+#pragma unroll
         for (int w = 0; w < n; ++w)
           if (w != s) v *= P[w];
       } else {
         v = P1[s] * P1[t];
+#pragma unroll
         for (int w = 0; w < n; ++w)
           if (w != s && w != t) v *= P[w];
       }
-      hs = fma(e[sp[t]], v, hs);
+      hs = fma(e[sp(t)], v, hs);
     }
     h[s] = hs;
   }
 }
 
-template <int NS>
-__device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double dt, const double* lam,
-                             double* out) {
+// The forward pass keeps k_f, k_b and their log-T derivatives of every
+// reaction for the reverse pass: in local arrays for the run-time table, in
+// shared memory (one column of 4 NR doubles per thread, every index a
+// constant) for the compiled structure.
+struct LocalRateCache {
+  double kf[MAX_NR], kb[MAX_NR], dkf[MAX_NR], dkb[MAX_NR];
+  __device__ __forceinline__ void put(int i, double a, double b, double c, double d) {
+    kf[i] = a; kb[i] = b; dkf[i] = c; dkb[i] = d;
+  }
+  __device__ __forceinline__ double k_f(int i) const { return kf[i]; }
+  __device__ __forceinline__ double k_b(int i) const { return kb[i]; }
+  __device__ __forceinline__ double dk_f(int i) const { return dkf[i]; }
+  __device__ __forceinline__ double dk_b(int i) const { return dkb[i]; }
+};
+struct SharedRateCache {
+  double* col;  // this thread's column: entry q at col[q * stride]
+  int stride;
+  __device__ __forceinline__ void put(int i, double a, double b, double c, double d) {
+    col[(4 * i) * stride] = a;
+    col[(4 * i + 1) * stride] = b;
+    col[(4 * i + 2) * stride] = c;
+    col[(4 * i + 3) * stride] = d;
+  }
+  __device__ __forceinline__ double k_f(int i) const { return col[(4 * i) * stride]; }
+  __device__ __forceinline__ double k_b(int i) const { return col[(4 * i + 1) * stride]; }
+  __device__ __forceinline__ double dk_f(int i) const { return col[(4 * i + 2) * stride]; }
+  __device__ __forceinline__ double dk_b(int i) const { return col[(4 * i + 3) * stride]; }
+};
+
+template <int NS, bool FIXED, class Cache>
+__device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double dt, const double* lam, double* out,
+                             Cache& cache) {
   constexpr int NSP = NS - 1;
   constexpr int NV = NS + 3;
   double X[NS];
@@ -509,7 +550,6 @@ __device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double
   const double rcref = (RU / P_REF) * T;
 
   // ---- forward: rates, J'' and the caches of the reverse pass ----
-  double kfa[MAX_NR], kba[MAX_NR], dkfa[MAX_NR], dkba[MAX_NR];
   double wd[NSP], A[NSP][NSP];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
@@ -517,82 +557,107 @@ __device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double
 #pragma unroll
     for (int l = 0; l < NSP; ++l) A[k][l] = 0.0;
   }
-  for (int i = 0; i < m.nr; ++i) {
-    const int nre = m.nre[i], npr = m.npr[i];
+  for_reactions<FIXED>(m, [&](auto R) {
+    const int i = R.idx();
+    const int nre = R.nre(), npr = R.npr();
     const double kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
     const double dlkf = fma(m.b[i], rT, m.EaR[i] * rT2);
     double kb = kf, dlkb = dlkf;
+#pragma unroll
     for (int r = 0; r < nre; ++r)
-      for (int q = 0; q < m.rnu[i][r]; ++q) { kb *= eG[m.rsp[i][r]]; dlkb += dG[m.rsp[i][r]]; }
+#pragma unroll
+      for (int q = 0; q < R.rnu(r); ++q) { kb *= eG[R.rsp(r)]; dlkb += dG[R.rsp(r)]; }
+#pragma unroll
     for (int r = 0; r < npr; ++r)
-      for (int q = 0; q < m.pnu[i][r]; ++q) { kb *= reG[m.psp[i][r]]; dlkb -= dG[m.psp[i][r]]; }
-    const int dn = m.dnu[i];
+#pragma unroll
+      for (int q = 0; q < R.pnu(r); ++q) { kb *= reG[R.psp(r)]; dlkb -= dG[R.psp(r)]; }
+    const int dn = R.dnu();
+#pragma unroll
     for (int q = 0; q < dn; ++q) kb *= rcref;
+#pragma unroll
     for (int q = 0; q < -dn; ++q) kb *= cref;
     dlkb = fma((double)dn, rT, dlkb);
-    kfa[i] = kf; kba[i] = kb; dkfa[i] = dlkf; dkba[i] = dlkb;
+    cache.put(i, kf, kb, dlkf, dlkb);
     double xr[MAX_SIDE], xp[MAX_SIDE];
     double fwd = kf, bwd = kb;
+#pragma unroll
     for (int r = 0; r < nre; ++r) {
-      xr[r] = X[m.rsp[i][r]];
-      for (int q = 0; q < m.rnu[i][r]; ++q) fwd *= xr[r];
+      xr[r] = X[R.rsp(r)];
+#pragma unroll
+      for (int q = 0; q < R.rnu(r); ++q) fwd *= xr[r];
     }
+#pragma unroll
     for (int r = 0; r < npr; ++r) {
-      xp[r] = X[m.psp[i][r]];
-      for (int q = 0; q < m.pnu[i][r]; ++q) bwd *= xp[r];
+      xp[r] = X[R.psp(r)];
+#pragma unroll
+      for (int q = 0; q < R.pnu(r); ++q) bwd *= xp[r];
     }
     double Mi = 1.0;
-    if (m.tb[i]) {
+    if (R.tb()) {
       Mi = Ctot;
-      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
+#pragma unroll
+      for (int e = 0; e < R.neff(); ++e) Mi = fma(m.effv[i][e], X[R.effsp(e)], Mi);
     }
     const double net = fwd - bwd;
     const double q = Mi * net;
     double dq[2 * MAX_SIDE];
     int dsp[2 * MAX_SIDE];
     int nd = 0;
+#pragma unroll
     for (int r = 0; r < nre; ++r) {
-      double dd = kf * m.rnud[i][r];
+      double dd = kf * R.rnud(r);
+#pragma unroll
       for (int s2 = 0; s2 < nre; ++s2) {
-        const int pw = m.rnu[i][s2] - (s2 == r ? 1 : 0);
+        const int pw = R.rnu(s2) - (s2 == r ? 1 : 0);
+#pragma unroll
         for (int t = 0; t < pw; ++t) dd *= xr[s2];
       }
       dq[nd] = Mi * dd;
-      dsp[nd++] = m.rsp[i][r];
+      dsp[nd++] = R.rsp(r);
     }
+#pragma unroll
     for (int r = 0; r < npr; ++r) {
-      double dd = kb * m.pnud[i][r];
+      double dd = kb * R.pnud(r);
+#pragma unroll
       for (int s2 = 0; s2 < npr; ++s2) {
-        const int pw = m.pnu[i][s2] - (s2 == r ? 1 : 0);
+        const int pw = R.pnu(s2) - (s2 == r ? 1 : 0);
+#pragma unroll
         for (int t = 0; t < pw; ++t) dd *= xp[s2];
       }
       dq[nd] = -Mi * dd;
-      dsp[nd++] = m.psp[i][r];
+      dsp[nd++] = R.psp(r);
     }
+#pragma unroll
     for (int side = 0; side < 2; ++side) {
       const int cnt = side ? npr : nre;
+#pragma unroll
       for (int r = 0; r < cnt; ++r) {
-        const int k = side ? m.psp[i][r] : m.rsp[i][r];
+        const int k = side ? R.psp(r) : R.rsp(r);
         if (k >= NSP) continue;
-        const double nu = side ? m.pnud[i][r] : -m.rnud[i][r];
+        const double nu = side ? R.pnud(r) : -R.rnud(r);
         wd[k] = fma(nu, q, wd[k]);
-        for (int d = 0; d < nd; ++d) {
+#pragma unroll
+        for (int d = 0; d < nre + npr; ++d) {
           const int jj = dsp[d];
           if (jj < NSP) {
             A[k][jj] = fma(nu, dq[d], A[k][jj]);
           } else {
             const double v = dq[d] * nu;
+#pragma unroll
             for (int l = 0; l < NSP; ++l) A[k][l] = fma(-m.mratio[l], v, A[k][l]);
           }
         }
-        if (m.tb[i]) {
+        if (R.tb()) {
           const double v = net * nu;
+#pragma unroll
           for (int l = 0; l < NSP; ++l) A[k][l] = fma(m.ceff[i][l], v, A[k][l]);
         }
       }
     }
-  }
-  // A = I - dt J'', factored P A = L U in place (partial pivoting on values)
+  });
+  // A = I - dt J'', factored P A = L U in place (partial pivoting on
+  // values). Row swaps and the final un-permutation are selects over the
+  // candidate rows, so every index stays a constant.
   double x[NSP];
   int perm[NSP];
 #pragma unroll
@@ -601,43 +666,77 @@ __device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double
 #pragma unroll
     for (int l = 0; l < NSP; ++l) A[k][l] = fma(-dt, A[k][l], k == l ? 1.0 : 0.0);
   }
+#pragma unroll
   for (int c = 0; c < NSP; ++c) {
     int piv = c;
     double best = fabs(A[c][c]);
+#pragma unroll
     for (int r = c + 1; r < NSP; ++r)
       if (fabs(A[r][c]) > best) { best = fabs(A[r][c]); piv = r; }
     perm[c] = piv;
-    if (piv != c) {
-      for (int k = 0; k < NSP; ++k) { const double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
-      const double t = x[c]; x[c] = x[piv]; x[piv] = t;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      const double ac = A[c][k];
+      double v = ac;
+#pragma unroll
+      for (int r = c + 1; r < NSP; ++r) v = (piv == r) ? A[r][k] : v;
+#pragma unroll
+      for (int r = c + 1; r < NSP; ++r) A[r][k] = (piv == r) ? ac : A[r][k];
+      A[c][k] = v;
+    }
+    {
+      const double xc = x[c];
+      double v = xc;
+#pragma unroll
+      for (int r = c + 1; r < NSP; ++r) v = (piv == r) ? x[r] : v;
+#pragma unroll
+      for (int r = c + 1; r < NSP; ++r) x[r] = (piv == r) ? xc : x[r];
+      x[c] = v;
     }
     const double ip = rcp(A[c][c]);
+#pragma unroll
     for (int r = c + 1; r < NSP; ++r) {
       const double f = A[r][c] * ip;
       A[r][c] = f;  // L
+#pragma unroll
       for (int k = c + 1; k < NSP; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
       x[r] = fma(-f, x[c], x[r]);
     }
   }
+#pragma unroll
   for (int r = NSP - 1; r >= 0; --r) {
     double s = x[r];
+#pragma unroll
     for (int k = r + 1; k < NSP; ++k) s = fma(-A[r][k], x[k], s);
     x[r] = s * rcp(A[r][r]);
   }
   // mu = A^{-T} r: U^T z = r, L^T w = z, then undo the row swaps
   double mu[NSP];
+#pragma unroll
   for (int c = 0; c < NSP; ++c) {
     double s = m.M[c] * lam[4 + c];
+#pragma unroll
     for (int k = 0; k < c; ++k) s = fma(-A[k][c], mu[k], s);
     mu[c] = s * rcp(A[c][c]);
   }
+#pragma unroll
   for (int c = NSP - 1; c >= 0; --c) {
     double s = mu[c];
+#pragma unroll
     for (int k = c + 1; k < NSP; ++k) s = fma(-A[k][c], mu[k], s);
     mu[c] = s;
   }
-  for (int c = NSP - 1; c >= 0; --c)
-    if (perm[c] != c) { const double t = mu[c]; mu[c] = mu[perm[c]]; mu[perm[c]] = t; }
+#pragma unroll
+  for (int c = NSP - 1; c >= 0; --c) {
+    const int p = perm[c];
+    const double mc = mu[c];
+    double v = mc;
+#pragma unroll
+    for (int r = c + 1; r < NSP; ++r) v = (p == r) ? mu[r] : v;
+#pragma unroll
+    for (int r = c + 1; r < NSP; ++r) mu[r] = (p == r) ? mc : mu[r];
+    mu[c] = v;
+  }
   double xe[NS];
   double xN = 0.0;
 #pragma unroll
@@ -651,42 +750,50 @@ __device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double
   double gT = 0.0, gX[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) gX[k] = 0.0;
-  for (int i = 0; i < m.nr; ++i) {
-    const int nre = m.nre[i], npr = m.npr[i];
+  for_reactions<FIXED>(m, [&](auto R) {
+    const int i = R.idx();
+    const int nre = R.nre(), npr = R.npr();
     double mi = 0.0;
+#pragma unroll
     for (int r = 0; r < nre; ++r)
-      if (m.rsp[i][r] < NSP) mi = fma(-m.rnud[i][r], mu[m.rsp[i][r]], mi);
+      if (R.rsp(r) < NSP) mi = fma(-R.rnud(r), mu[R.rsp(r)], mi);
+#pragma unroll
     for (int r = 0; r < npr; ++r)
-      if (m.psp[i][r] < NSP) mi = fma(m.pnud[i][r], mu[m.psp[i][r]], mi);
+      if (R.psp(r) < NSP) mi = fma(R.pnud(r), mu[R.psp(r)], mi);
     const double w = dt * mi;
-    const double kf = kfa[i], kb = kba[i];
+    const double kf = cache.k_f(i), kb = cache.k_b(i);
     double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
-    monomial(X, m.rsp[i], m.rnu[i], nre, xe, F, gF, DF, hF);
-    monomial(X, m.psp[i], m.pnu[i], npr, xe, B, gB, DB, hB);
+    monomial(X, [&](int s_) { return R.rsp(s_); }, [&](int s_) { return R.rnu(s_); }, nre, xe, F, gF, DF, hF);
+    monomial(X, [&](int s_) { return R.psp(s_); }, [&](int s_) { return R.pnu(s_); }, npr, xe, B, gB, DB, hB);
     const double net = fma(kf, F, -kb * B);
     const double Dnet = fma(kf, DF, -kb * DB);
     double Mi = 1.0, DMi = 0.0;
-    if (m.tb[i]) {
+    if (R.tb()) {
       Mi = Ctot;
-      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
+#pragma unroll
+      for (int e = 0; e < R.neff(); ++e) Mi = fma(m.effv[i][e], X[R.effsp(e)], Mi);
+#pragma unroll
       for (int j = 0; j < NS; ++j) DMi = fma(1.0 + m.effm1[i][j], xe[j], DMi);
     }
     const double MD = Mi + DMi;
-    const double kfp = kf * dkfa[i], kbp = kb * dkba[i];
+    const double kfp = kf * cache.dk_f(i), kbp = kb * cache.dk_b(i);
     gT = fma(w, fma(MD, fma(kfp, F, -kbp * B), Mi * fma(kfp, DF, -kbp * DB)), gT);
+#pragma unroll
     for (int r = 0; r < nre; ++r) {
-      const int j = m.rsp[i][r];
+      const int j = R.rsp(r);
       gX[j] = fma(w * kf, fma(MD, gF[r], Mi * hF[r]), gX[j]);
     }
+#pragma unroll
     for (int r = 0; r < npr; ++r) {
-      const int j = m.psp[i][r];
+      const int j = R.psp(r);
       gX[j] = fma(-w * kb, fma(MD, gB[r], Mi * hB[r]), gX[j]);
     }
-    if (m.tb[i]) {
+    if (R.tb()) {
       const double v = w * (net + Dnet);
+#pragma unroll
       for (int j = 0; j < NS; ++j) gX[j] = fma(1.0 + m.effm1[i][j], v, gX[j]);
     }
-  }
+  });
   // chain to U*: X(U*) and the implicit dT/dU* of the Newton recovery
   CellThermo<NS> ct;
   cell_thermo<NS>(u, T, m, ct);
@@ -700,11 +807,12 @@ __device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double
   for (int k = 0; k < NSP; ++k) out[4 + k] += fma(gX[k], m.invM[k], -gN);
 }
 
-template <int NS>
+template <int NS, bool FIXED>
 __global__ void __launch_bounds__(128) k_adj_chem_rev(StateView Sstar, GridDev g, const MechDev* __restrict__ mech,
                                                       double dt, const double* __restrict__ lam,
                                                       double* __restrict__ out) {
   constexpr int NV = NS + 3;
+  extern __shared__ double rate_cols[];  // FIXED: 4 NR doubles per thread, thread-major columns
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.n) return;
   const long long n = g.n;
@@ -714,7 +822,13 @@ __global__ void __launch_bounds__(128) k_adj_chem_rev(StateView Sstar, GridDev g
     u[k] = Sstar.plane(k, n)[q];
     l[k] = lam[(long long)k * n + q];
   }
-  chem_vjp_rev<NS>(u, Sstar.plane(NV, n)[q], *mech, dt, l, o);
+  if constexpr (FIXED) {
+    SharedRateCache cache{rate_cols + threadIdx.x, (int)blockDim.x};
+    chem_vjp_rev<NS, true>(u, Sstar.plane(NV, n)[q], *mech, dt, l, o, cache);
+  } else {
+    LocalRateCache cache;
+    chem_vjp_rev<NS, false>(u, Sstar.plane(NV, n)[q], *mech, dt, l, o, cache);
+  }
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[(long long)k * n + q] = o[k];
 }
@@ -787,8 +901,8 @@ __global__ void __launch_bounds__(128) k_src_vjp(StateView S, GridDev g, const M
     for (int qq = 0; qq < -dn; ++qq) kb *= cref;
     dlkb = fma((double)dn, rT, dlkb);
     double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
-    monomial(X, m.rsp[i], m.rnu[i], nre, zero, F, gF, DF, hF);
-    monomial(X, m.psp[i], m.pnu[i], npr, zero, B, gB, DB, hB);
+    monomial(X, [&](int s_) { return m.rsp[i][s_]; }, [&](int s_) { return m.rnu[i][s_]; }, nre, zero, F, gF, DF, hF);
+    monomial(X, [&](int s_) { return m.psp[i][s_]; }, [&](int s_) { return m.pnu[i][s_]; }, npr, zero, B, gB, DB, hB);
     double Mi = 1.0;
     if (m.tb[i]) {
       Mi = Ctot;
@@ -976,8 +1090,19 @@ cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev,
 cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, const MechDev* mech, double dt,
                             const double* lam, double* out, cudaStream_t st) {
   switch (ns) {
-    case 3: k_adj_chem_rev<3><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out); break;
-    case 9: k_adj_chem_rev<9><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out); break;
+    case 3: k_adj_chem_rev<3, false><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out); break;
+    case 9:
+      if (g.chem_fixed) {
+        const int smem = (int)(sizeof(double) * 4 * fixed_h2air::NR * 128);
+        static std::atomic<unsigned long long> attr_done{0};
+        const cudaError_t e = set_attr_once((const void*)k_adj_chem_rev<9, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem, &attr_done);
+        if (e != cudaSuccess) return e;
+        k_adj_chem_rev<9, true><<<nblk(g.n, 128), 128, smem, st>>>(Sstar, g, mech, dt, lam, out);
+      } else {
+        k_adj_chem_rev<9, false><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out);
+      }
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -24,9 +24,14 @@
 // then the point-implicit chemistry over the layer's dt (launch_chem).
 // Crossover advance (Fig. 2a): layer i + 1 takes two steps of dt / 2 before
 // each step of layer i; after the base step the four-to-one mean runs from the
-// deepest layer up (k_amr_f2c). Regridding (k_amr_mark, k_amr_flags, host
-// block lists, k_amr_fill) happens every regrid_every base steps before the
-// solve; a block present before and after keeps its data.
+// deepest layer up (k_amr_f2c). Regridding (k_amr_mark, k_amr_flags, the
+// block lists built on the device by k_amr_compact and k_amr_neighbours,
+// k_amr_fill) happens every regrid_every base steps before the solve; a block
+// present before and after keeps its data. With a CFL number the base dt is
+// computed on the device from the base layer's LF speeds, and layer i's dt is
+// that dt times 2^-i (exact), so a step needs no host round trip; a regrid
+// reads back one block count per layer. Layer buffers grow and are never
+// shrunk, so steady refinement allocates nothing.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -162,8 +167,10 @@ template <int NS, int STAGE>
 __global__ void __launch_bounds__(AB2) k_amr_update(StateView Sin, StateView S0, StateView Sout,
                                                     const double* __restrict__ Fx, const double* __restrict__ Gy,
                                                     LayerDev L, ParentDev P, const MechDev* __restrict__ mech,
-                                                    double dt, unsigned long long* alpha_out, int* status) {
+                                                    StepCtl ctl, const unsigned long long* __restrict__ a_step,
+                                                    unsigned long long* alpha_out, int* status) {
   constexpr int NV = NS + 3;
+  const double dt = step_dt(ctl, a_step);  // the layer's dt: fixed, or from the base layer's LF speeds
   const int blk = blockIdx.x;
   const int i = threadIdx.x % AB, j = threadIdx.x / AB;
   const long long n = L.n;
@@ -358,6 +365,69 @@ __global__ void __launch_bounds__(AB2) k_amr_fill(StateView Snew, LayerDev L, co
   }
 }
 
+// Block list of a layer from its refinement flags, in (by, bx) order, on
+// the device (one block of AMR_SCAN threads): map[cand] = the block number or
+// -1, pos[b] = bx | by << 16, old_index[b] = the block's number before the
+// regrid (old_map, or -1 for a new block), *count = the number of blocks.
+constexpr int AMR_SCAN = 1024;
+__global__ void __launch_bounds__(AMR_SCAN) k_amr_compact(const unsigned char* __restrict__ flags, int ncand, int nbx,
+                                                         const int* __restrict__ old_map, int* __restrict__ map,
+                                                         int* __restrict__ pos, int* __restrict__ old_index,
+                                                         int* __restrict__ count) {
+  __shared__ int part[AMR_SCAN];
+  const int t = threadIdx.x;
+  const int per = (ncand + AMR_SCAN - 1) / AMR_SCAN;
+  const int c0 = min(t * per, ncand), c1 = min(c0 + per, ncand);
+  int mine = 0;
+  for (int c = c0; c < c1; ++c) mine += flags[c] ? 1 : 0;
+  part[t] = mine;
+  __syncthreads();
+  // inclusive scan of the per-thread counts (Hillis-Steele)
+  for (int o = 1; o < AMR_SCAN; o <<= 1) {
+    const int v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int b = part[t] - mine;  // this thread's first block number
+  for (int c = c0; c < c1; ++c) {
+    if (flags[c]) {
+      map[c] = b;
+      pos[b] = (c % nbx) | ((c / nbx) << 16);
+      old_index[b] = old_map ? old_map[c] : -1;
+      ++b;
+    } else {
+      map[c] = -1;
+    }
+  }
+  if (t == AMR_SCAN - 1) *count = part[t];
+}
+
+// Neighbour table of a layer's blocks (north, south, west, east): the block
+// across that side (its periodic partner on a periodic side), NB_PHYSICAL on
+// a non-periodic domain side, NB_EXTERNAL where no block of the layer is
+// there.
+__global__ void k_amr_neighbours(const int* __restrict__ pos, const int* __restrict__ map, int nblk, int nbx, int nby,
+                                 int bcl, int bcr, int bcb, int bct, int* __restrict__ nbr) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 4 * nblk) return;
+  const int b = q >> 2, s = q & 3;
+  const int bx = pos[b] & 0xffff, by = pos[b] >> 16;
+  const int dxs[4] = {0, 0, -1, 1}, dys[4] = {1, -1, 0, 0};
+  const int side_bc[4] = {bct, bcb, bcl, bcr};
+  int qx = bx + dxs[s], qy = by + dys[s];
+  if (qx < 0 || qx >= nbx || qy < 0 || qy >= nby) {
+    if (side_bc[s] != BC_PERIODIC) {
+      nbr[q] = NB_PHYSICAL;
+      return;
+    }
+    qx = (qx + nbx) % nbx;
+    qy = (qy + nby) % nby;
+  }
+  const int m = map[qy * nbx + qx];
+  nbr[q] = m >= 0 ? m : NB_EXTERNAL;
+}
+
 }  // namespace janc
 
 using namespace janc;
@@ -378,29 +448,45 @@ int afail_cuda(cudaError_t e, const char* where) {
   return afail(JANC_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// One refined layer. The index buffers (positions, neighbours, old block
+// numbers, two position maps used in turn by consecutive regrids) are sized
+// for every candidate block of the layer's index space once, at creation.
+// The state and face-flux buffers hold `cap` blocks and grow (never shrink)
+// when a regrid needs more; a state is stored with plane stride nblk * 256
+// inside them. `spare` receives the regridded state, then trades places
+// with S[0].
 struct AmrLayer {
   int nbx = 0, nby = 0;          // blocks of the layer's index space
   int nblk = 0;
-  std::vector<int> pos;          // bx | by << 16, in (by, bx) order
-  std::vector<int> map;          // [nby][nbx] block number or -1
-  int* d_pos = nullptr;
-  int* d_nbr = nullptr;
-  int* d_map = nullptr;
+  int cap = 0;                   // blocks the state and flux buffers hold
+  int cur = 0;                   // d_mapv[cur] is the current position map
+  int* d_pos = nullptr;          // [nbx nby] bx | by << 16, in (by, bx) order
+  int* d_nbr = nullptr;          // [4 nbx nby]
+  int* d_oldidx = nullptr;       // [nbx nby]
+  int* d_mapv[2] = {nullptr, nullptr};  // [nby][nbx] block number or -1
+  int* d_count = nullptr;
+  int* d_map = nullptr;          // = d_mapv[cur]
   double* S[3] = {nullptr, nullptr, nullptr};
+  double* spare = nullptr;
   double* Fx = nullptr;
   double* Gy = nullptr;
   unsigned long long* alpha = nullptr;  // 6 slots x 2
 };
 
-void free_layer_bufs(AmrLayer& L) {
+void free_state_bufs(AmrLayer& L) {
   for (double*& p : L.S) { if (p) cudaFree(p); p = nullptr; }
+  if (L.spare) cudaFree(L.spare);
   if (L.Fx) cudaFree(L.Fx);
   if (L.Gy) cudaFree(L.Gy);
-  if (L.d_pos) cudaFree(L.d_pos);
-  if (L.d_nbr) cudaFree(L.d_nbr);
-  if (L.d_map) cudaFree(L.d_map);
-  L.Fx = L.Gy = nullptr;
-  L.d_pos = L.d_nbr = L.d_map = nullptr;
+  L.spare = L.Fx = L.Gy = nullptr;
+  L.cap = 0;
+}
+
+void free_layer_bufs(AmrLayer& L) {
+  free_state_bufs(L);
+  for (int* p : {L.d_pos, L.d_nbr, L.d_oldidx, L.d_mapv[0], L.d_mapv[1], L.d_count})
+    if (p) cudaFree(p);
+  L.d_pos = L.d_nbr = L.d_oldidx = L.d_mapv[0] = L.d_mapv[1] = L.d_count = L.d_map = nullptr;
 }
 
 }  // namespace
@@ -415,11 +501,10 @@ struct janc_amr_s {
   unsigned char* d_mask = nullptr;   // largest parent index space
   unsigned char* d_flags = nullptr;  // largest candidate set
   int* d_status = nullptr;
-  int* d_oldidx = nullptr;
-  size_t mask_bytes = 0, flags_bytes = 0, oldidx_count = 0;
+  size_t mask_bytes = 0, flags_bytes = 0;
   long long nstep = 0;
-  double t = 0.0;
   long long updates_last = 0;
+  long long grow_events = 0;         // regrids that had to enlarge a layer's buffers
 };
 
 namespace {
@@ -488,8 +573,11 @@ cudaError_t launch_alpha(int ns, const StateView& S, long long n, const MechDev*
   return cudaGetLastError();
 }
 
+// lc: the layer's step control, a fixed dt or the CFL number with the
+// layer's scaled spacing, so that step_dt() of the base layer's LF speeds
+// gives this layer's dt on the device.
 template <int NS>
-cudaError_t solve_layer_t(janc_amr_s* A, int i, double dt) {
+cudaError_t solve_layer_t(janc_amr_s* A, int i, const StepCtl& lc) {
   constexpr int NV = NS + 3;
   AmrLayer& L = A->L[i];
   const GridParts gp = grid_parts(A->g0);
@@ -509,46 +597,51 @@ cudaError_t solve_layer_t(janc_amr_s* A, int i, double dt) {
     e = cudaGetLastError();
     if (e != cudaSuccess) break;
     if (s == 0)
-      k_amr_update<NS, 1><<<L.nblk, AB2, 0, st>>>(ins[s], S0, outs[s], L.Fx, L.Gy, D, P, gp.mech, dt, a + 2,
+      k_amr_update<NS, 1><<<L.nblk, AB2, 0, st>>>(ins[s], S0, outs[s], L.Fx, L.Gy, D, P, gp.mech, lc, gp.alpha, a + 2,
                                                   A->d_status);
     else if (s == 1)
-      k_amr_update<NS, 2><<<L.nblk, AB2, 0, st>>>(ins[s], S0, outs[s], L.Fx, L.Gy, D, P, gp.mech, dt, a + 4,
+      k_amr_update<NS, 2><<<L.nblk, AB2, 0, st>>>(ins[s], S0, outs[s], L.Fx, L.Gy, D, P, gp.mech, lc, gp.alpha, a + 4,
                                                   A->d_status);
     else
-      k_amr_update<NS, 3><<<L.nblk, AB2, 0, st>>>(ins[s], S0, outs[s], L.Fx, L.Gy, D, P, gp.mech, dt, a + 6,
+      k_amr_update<NS, 3><<<L.nblk, AB2, 0, st>>>(ins[s], S0, outs[s], L.Fx, L.Gy, D, P, gp.mech, lc, gp.alpha, a + 6,
                                                   A->d_status);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && A->d.chemistry == JANC_CHEM_LIE) {
-    StepCtl ctl;
-    ctl.dt_fixed = dt;
-    ctl.cfl = 0.0;
-    ctl.hmin = 1.0;
-    ctl.chem_frac = 1.0;
-    ctl.source = 0;
-    e = launch_chem(NS, S0, layer_grid(A, i), gp.mech, ctl, a, a + 8, A->d_status, st);
-  }
+  if (e == cudaSuccess && A->d.chemistry == JANC_CHEM_LIE)
+    e = launch_chem(NS, S0, layer_grid(A, i), gp.mech, lc, gp.alpha, a + 8, A->d_status, st);
   return e;
 }
 
-cudaError_t solve_layer(janc_amr_s* A, int i, double dt) {
+cudaError_t solve_layer(janc_amr_s* A, int i, const StepCtl& lc) {
   if (A->L[i].nblk == 0) return cudaSuccess;
   switch (A->ns) {
-    case 1: return solve_layer_t<1>(A, i, dt);
-    case 3: return solve_layer_t<3>(A, i, dt);
-    case 9: return solve_layer_t<9>(A, i, dt);
+    case 1: return solve_layer_t<1>(A, i, lc);
+    case 3: return solve_layer_t<3>(A, i, lc);
+    case 9: return solve_layer_t<9>(A, i, lc);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int advance(janc_amr_s* A, int i, double dt) {
+// Step control of a layer whose dt is 2^-k times the given one: a fixed dt
+// halves, a CFL dt halves through the spacing (exact in floating point).
+StepCtl halved(StepCtl c, int k) {
+  if (c.dt_fixed > 0.0) c.dt_fixed = std::ldexp(c.dt_fixed, -k);
+  else c.hmin = std::ldexp(c.hmin, -k);
+  return c;
+}
+
+// Crossover advance of layer i and everything finer (Fig. 2a): two steps of
+// the next layer per step of this one. The base layer (i = 0) steps through
+// janc_step with the same dt (its CFL dt is computed the same way).
+int advance(janc_amr_s* A, int i, const StepCtl& c) {
   if (i < A->a.levels && A->L[i + 1].nblk > 0) {
-    int rc = advance(A, i + 1, 0.5 * dt);
-    if (rc == JANC_OK) rc = advance(A, i + 1, 0.5 * dt);
+    const StepCtl f = halved(c, 1);
+    int rc = advance(A, i + 1, f);
+    if (rc == JANC_OK) rc = advance(A, i + 1, f);
     if (rc != JANC_OK) return rc;
   }
-  if (i == 0) return janc_step(A->g0, 1, dt, 0.0, nullptr, nullptr);
-  cudaError_t e = solve_layer(A, i, dt);
+  if (i == 0) return janc_step(A->g0, 1, c.dt_fixed, c.dt_fixed > 0.0 ? 0.0 : c.cfl, nullptr, nullptr);
+  cudaError_t e = solve_layer(A, i, c);
   return e == cudaSuccess ? JANC_OK : afail_cuda(e, "AMR layer solve");
 }
 
@@ -561,17 +654,37 @@ cudaError_t f2c_t(janc_amr_s* A, int i) {
   return cudaGetLastError();
 }
 
-// New block list of a layer from the flags; neighbours (periodic wrap,
-// physical sides, external sides) and the position map (janc_host.h).
-void build_lists(const janc_amr_s* A, const std::vector<unsigned char>& flags, AmrLayer& N, std::vector<int>& nbr) {
-  janc::host::build_block_lists(flags.data(), N.nbx, N.nby, A->d.bc, N.pos, N.map, nbr);
-  N.nblk = (int)N.pos.size();
+// Enlarges a layer's state and flux buffers to hold at least `need` blocks
+// (about 1.25 x need, so that a slowly growing layer does not reallocate at
+// every regrid). S[0] keeps its data; the other buffers hold nothing yet.
+cudaError_t grow_layer(janc_amr_s* A, AmrLayer& L, int need) {
+  const int cap = std::max(need, need + need / 4);
+  const int np = A->nv + 4;
+  const size_t cells = (size_t)cap * AB2;
+  double* S0 = nullptr;
+  cudaError_t e = cudaMalloc(&S0, sizeof(double) * np * cells);
+  // S[0] holds the layer's current data: copy the nblk blocks into the new one
+  if (e == cudaSuccess && L.nblk > 0)
+    e = cudaMemcpyAsync(S0, L.S[0], sizeof(double) * np * (size_t)L.nblk * AB2, cudaMemcpyDeviceToDevice, A->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(A->stream);
+  if (e != cudaSuccess) {
+    if (S0) cudaFree(S0);
+    return e;
+  }
+  free_state_bufs(L);
+  L.S[0] = S0;
+  for (int k = 1; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&L.S[k], sizeof(double) * np * cells);
+  if (e == cudaSuccess) e = cudaMalloc(&L.spare, sizeof(double) * np * cells);
+  if (e == cudaSuccess) e = cudaMalloc(&L.Fx, sizeof(double) * A->nv * (size_t)cap * AB * (AB + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&L.Gy, sizeof(double) * A->nv * (size_t)cap * AB * (AB + 1));
+  if (e == cudaSuccess) L.cap = cap;
+  ++A->grow_events;
+  return e;
 }
 
 int regrid(janc_amr_s* A) {
   const GridParts gp = grid_parts(A->g0);
   cudaStream_t st = A->stream;
-  const int np = A->nv + 4;
   for (int i = 1; i <= A->a.levels; ++i) {
     AmrLayer& O = A->L[i];
     // mask of layer i-1 in its index space
@@ -593,73 +706,53 @@ int regrid(janc_amr_s* A) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return afail_cuda(e, "AMR mask");
     const int ncand = O.nbx * O.nby;
-    k_amr_flags<<<(ncand + 255) / 256, 256, 0, st>>>(A->d_mask, width, height, O.nbx, O.nby, A->a.n_buffer,
-                                                     i >= 2 ? A->L[i - 1].d_map : nullptr, A->L[i - 1].nbx,
-                                                     A->d_flags);
-    e = cudaGetLastError();
-    std::vector<unsigned char> flags((size_t)ncand);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(flags.data(), A->d_flags, (size_t)ncand, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return afail_cuda(e, "AMR flags");
-    if (i >= 2 && A->L[i - 1].nblk == 0) std::fill(flags.begin(), flags.end(), (unsigned char)0);
-
-    AmrLayer N;
-    N.nbx = O.nbx;
-    N.nby = O.nby;
-    N.alpha = O.alpha;
-    std::vector<int> nbr;
-    build_lists(A, flags, N, nbr);
-    std::vector<int> oldidx((size_t)N.nblk);
-    for (int b = 0; b < N.nblk; ++b) {
-      const int bx = N.pos[b] & 0xffff, by = N.pos[b] >> 16;
-      oldidx[b] = O.nblk ? O.map[(size_t)by * O.nbx + bx] : -1;
+    if (i >= 2 && A->L[i - 1].nblk == 0) {
+      e = cudaMemsetAsync(A->d_flags, 0, (size_t)ncand, st);  // no parent blocks: nothing can refine
+    } else {
+      k_amr_flags<<<(ncand + 255) / 256, 256, 0, st>>>(A->d_mask, width, height, O.nbx, O.nby, A->a.n_buffer,
+                                                       i >= 2 ? A->L[i - 1].d_map : nullptr, A->L[i - 1].nbx,
+                                                       A->d_flags);
+      e = cudaGetLastError();
     }
-    const size_t cells = (size_t)N.nblk * AB2;
-    e = cudaMalloc(&N.d_map, sizeof(int) * N.map.size());
+    // the new block list, from the flags, on the device; only the count comes back
+    const int nxt = O.cur ^ 1;
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(N.d_map, N.map.data(), sizeof(int) * N.map.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && N.nblk > 0) {
-      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&N.S[k], sizeof(double) * np * cells);
-      if (e == cudaSuccess) e = cudaMalloc(&N.Fx, sizeof(double) * A->nv * N.nblk * AB * (AB + 1));
-      if (e == cudaSuccess) e = cudaMalloc(&N.Gy, sizeof(double) * A->nv * N.nblk * AB * (AB + 1));
-      if (e == cudaSuccess) e = cudaMalloc(&N.d_pos, sizeof(int) * N.nblk);
-      if (e == cudaSuccess) e = cudaMalloc(&N.d_nbr, sizeof(int) * 4 * N.nblk);
-      if (e == cudaSuccess && (size_t)N.nblk > A->oldidx_count) {
-        if (A->d_oldidx) cudaFree(A->d_oldidx);
-        A->d_oldidx = nullptr;
-        e = cudaMalloc(&A->d_oldidx, sizeof(int) * N.nblk);
-        A->oldidx_count = e == cudaSuccess ? (size_t)N.nblk : 0;
+      k_amr_compact<<<1, AMR_SCAN, 0, st>>>(A->d_flags, ncand, O.nbx, O.nblk > 0 ? O.d_map : nullptr, O.d_mapv[nxt],
+                                           O.d_pos, O.d_oldidx, O.d_count);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    int nblk = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nblk, O.d_count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return afail_cuda(e, "AMR block list");
+    if (nblk > 0) {
+      if (nblk > O.cap) {
+        e = grow_layer(A, O, nblk);
+        if (e != cudaSuccess) return afail_cuda(e, "AMR layer buffers");
       }
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(N.d_pos, N.pos.data(), sizeof(int) * N.nblk, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(N.d_nbr, nbr.data(), sizeof(int) * 4 * N.nblk, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(A->d_oldidx, oldidx.data(), sizeof(int) * N.nblk, cudaMemcpyHostToDevice, st);
+      k_amr_neighbours<<<(4 * nblk + 255) / 256, 256, 0, st>>>(O.d_pos, O.d_mapv[nxt], nblk, O.nbx, O.nby, A->d.bc[0],
+                                                              A->d.bc[1], A->d.bc[2], A->d.bc[3], O.d_nbr);
+      e = cudaGetLastError();
+      // kept blocks copy their old cells, new ones their parent (into the spare state)
+      const int nblk_old = O.nblk;
+      O.nblk = nblk;
+      O.d_map = O.d_mapv[nxt];
+      const LayerDev D = layer_dev(A, i);
+      const ParentDev P = parent_dev(A, i);
+      const StateView Sold{O.S[0]};
+      const long long n_old = (long long)nblk_old * AB2;
       if (e == cudaSuccess) {
-        AmrLayer keep = A->L[i];
-        A->L[i] = N;  // layer_dev / parent_dev of the new list
-        const LayerDev D = layer_dev(A, i);
-        const ParentDev P = parent_dev(A, i);
-        const StateView Sold{keep.S[0]};
-        const long long n_old = (long long)keep.nblk * AB2;
-        if (A->ns == 9) k_amr_fill<9><<<N.nblk, AB2, 0, st>>>(StateView{N.S[0]}, D, A->d_oldidx, Sold, n_old, P);
-        else if (A->ns == 3) k_amr_fill<3><<<N.nblk, AB2, 0, st>>>(StateView{N.S[0]}, D, A->d_oldidx, Sold, n_old, P);
-        else k_amr_fill<1><<<N.nblk, AB2, 0, st>>>(StateView{N.S[0]}, D, A->d_oldidx, Sold, n_old, P);
+        if (A->ns == 9) k_amr_fill<9><<<nblk, AB2, 0, st>>>(StateView{O.spare}, D, O.d_oldidx, Sold, n_old, P);
+        else if (A->ns == 3) k_amr_fill<3><<<nblk, AB2, 0, st>>>(StateView{O.spare}, D, O.d_oldidx, Sold, n_old, P);
+        else k_amr_fill<1><<<nblk, AB2, 0, st>>>(StateView{O.spare}, D, O.d_oldidx, Sold, n_old, P);
         e = cudaGetLastError();
-        A->L[i] = keep;
       }
-      // the old buffers are read by the fill: wait before freeing them
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    } else if (e == cudaSuccess) {
-      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return afail_cuda(e, "AMR regrid");
+      std::swap(O.S[0], O.spare);
+    } else {
+      O.nblk = 0;
+      O.d_map = O.d_mapv[nxt];
     }
-    if (e != cudaSuccess) {
-      free_layer_bufs(N);
-      return afail_cuda(e, "AMR regrid");
-    }
-    free_layer_bufs(O);
-    A->L[i] = N;
+    O.cur = nxt;
   }
   return JANC_OK;
 }
@@ -694,10 +787,20 @@ int janc_amr_create(const janc_grid_desc* base, const janc_mechanism* m, const j
   A->L.resize(a->levels + 1);
   cudaError_t e = cudaSuccess;
   for (int i = 1; i <= a->levels; ++i) {
-    A->L[i].nbx = (base->nx << i) / AB;
-    A->L[i].nby = (base->ny << i) / AB;
-    A->L[i].map.assign((size_t)A->L[i].nbx * A->L[i].nby, -1);
-    if (e == cudaSuccess) e = cudaMalloc(&A->L[i].alpha, 12 * sizeof(unsigned long long));
+    AmrLayer& L = A->L[i];
+    L.nbx = (base->nx << i) / AB;
+    L.nby = (base->ny << i) / AB;
+    const size_t ncand = (size_t)L.nbx * L.nby;
+    if (e == cudaSuccess) e = cudaMalloc(&L.alpha, 12 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_pos, sizeof(int) * ncand);
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_nbr, sizeof(int) * 4 * ncand);
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_oldidx, sizeof(int) * ncand);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaMalloc(&L.d_mapv[k], sizeof(int) * ncand);
+      if (e == cudaSuccess) e = cudaMemsetAsync(L.d_mapv[k], 0xff, sizeof(int) * ncand, A->stream);  // -1
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_count, sizeof(int));
+    L.d_map = L.d_mapv[0];
     A->flags_bytes = std::max(A->flags_bytes, (size_t)A->L[i].nbx * A->L[i].nby);
     A->mask_bytes = std::max(A->mask_bytes, ((size_t)base->nx << (i - 1)) * ((size_t)base->ny << (i - 1)));
   }
@@ -718,14 +821,8 @@ int janc_amr_set_state_primitive(janc_amr_t A, const double* T, const double* p,
   if (!A) return afail(JANC_E_INVALID, "null AMR object");
   const int rc = janc_set_state_primitive(A->g0, T, p, u, v, Y, where);
   if (rc != JANC_OK) return rc;
-  for (int i = 1; i <= A->a.levels; ++i) {  // layers are rebuilt at the next step
-    free_layer_bufs(A->L[i]);
-    A->L[i].nblk = 0;
-    A->L[i].pos.clear();
-    A->L[i].map.assign((size_t)A->L[i].nbx * A->L[i].nby, -1);
-  }
+  for (int i = 1; i <= A->a.levels; ++i) A->L[i].nblk = 0;  // rebuilt at the next step (buffers kept)
   A->nstep = 0;
-  A->t = 0.0;
   return JANC_OK;
 }
 
@@ -734,34 +831,39 @@ int janc_amr_step(janc_amr_t A, int n_steps, double dt, double cfl, double* t_ou
   if ((dt > 0.0) == (cfl > 0.0)) return afail(JANC_E_INVALID, "give exactly one of dt > 0 or cfl > 0");
   const GridParts gp = grid_parts(A->g0);
   cudaStream_t st = A->stream;
-  const double t0 = A->t;
+  double t0 = 0.0;
+  if (t_out) {  // the base grid's clock advances by every base step's dt
+    janc_status_info si;
+    const int rc = janc_status(A->g0, &si);
+    if (rc != JANC_OK) return rc;
+    t0 = si.t;
+  }
+  // the base step's control: a fixed dt, or the CFL of the base layer's LF
+  // speeds at the step's start, computed on the device by every kernel
+  StepCtl c;
+  c.dt_fixed = dt > 0.0 ? dt : 0.0;
+  c.cfl = dt > 0.0 ? 0.0 : cfl;
+  c.hmin = A->d.dx < A->d.dy ? A->d.dx : A->d.dy;
+  c.chem_frac = 1.0;
+  c.source = 0;
   for (int s = 0; s < n_steps; ++s) {
     if (A->nstep % A->a.regrid_every == 0 && A->a.levels > 0) {
       const int rc = regrid(A);
       if (rc != JANC_OK) return rc;
     }
-    double h = dt;
-    if (!(h > 0.0)) {  // CFL of the base layer at the step's start
-      unsigned long long al[2];
-      cudaError_t e = cudaMemcpyAsync(al, gp.alpha, sizeof(al), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return afail_cuda(e, "AMR alpha read");
-      double ax, ay;
-      std::memcpy(&ax, &al[0], 8);
-      std::memcpy(&ay, &al[1], 8);
-      const double hmin = A->d.dx < A->d.dy ? A->d.dx : A->d.dy;
-      h = cfl * hmin / (ax > ay ? ax : ay);
-    }
     int rc = JANC_OK;
     if (A->a.synchronous) {  // Fig. 2b: every layer takes this dt, deepest first
-      if (!(dt > 0.0)) h = std::ldexp(h, -A->a.levels);
+      // a fixed dt as given; the CFL dt of the base layer over 2^levels
+      const StepCtl cs = c.dt_fixed > 0.0 ? c : halved(c, A->a.levels);
       for (int i = A->a.levels; i >= 1 && rc == JANC_OK; --i) {
-        cudaError_t e = solve_layer(A, i, h);
+        cudaError_t e = solve_layer(A, i, cs);
         if (e != cudaSuccess) rc = afail_cuda(e, "AMR layer solve");
       }
-      if (rc == JANC_OK) rc = janc_step(A->g0, 1, h, 0.0, nullptr, nullptr);
+      if (rc == JANC_OK)
+        rc = janc_step(A->g0, 1, cs.dt_fixed, cs.dt_fixed > 0.0 ? 0.0 : std::ldexp(cfl, -A->a.levels), nullptr,
+                       nullptr);
     } else {
-      rc = advance(A, 0, h);
+      rc = advance(A, 0, c);
     }
     if (rc != JANC_OK) return rc;
     cudaError_t e = cudaSuccess;
@@ -775,9 +877,52 @@ int janc_amr_step(janc_amr_t A, int n_steps, double dt, double cfl, double* t_ou
     for (int i = 1; i <= A->a.levels; ++i) up += ((long long)A->L[i].nblk * AB2) << (A->a.synchronous ? 0 : i);
     A->updates_last = up;
     A->nstep += 1;
-    A->t += h;
   }
-  if (t_out) *t_out = A->t - t0;
+  if (t_out) {
+    janc_status_info si;
+    const int rc = janc_status(A->g0, &si);
+    if (rc != JANC_OK) return rc;
+    *t_out = si.t - t0;
+  }
+  return JANC_OK;
+}
+
+int janc_amr_block_lists(const unsigned char* flags, int nbx, int nby, const int* bc, int* pos, int* map, int* nbr,
+                         int* nblk) {
+  if (!flags || !bc || !pos || !map || !nbr || !nblk || nbx < 1 || nby < 1 || nbx > 65535 || nby > 65535)
+    return afail(JANC_E_INVALID, "janc_amr_block_lists: bad argument");
+  const size_t nc = (size_t)nbx * nby;
+  unsigned char* d_flags = nullptr;
+  int *d_map = nullptr, *d_pos = nullptr, *d_old = nullptr, *d_nbr = nullptr, *d_count = nullptr;
+  cudaError_t e = cudaMalloc(&d_flags, nc);
+  if (e == cudaSuccess) e = cudaMalloc(&d_map, sizeof(int) * nc);
+  if (e == cudaSuccess) e = cudaMalloc(&d_pos, sizeof(int) * nc);
+  if (e == cudaSuccess) e = cudaMalloc(&d_old, sizeof(int) * nc);
+  if (e == cudaSuccess) e = cudaMalloc(&d_nbr, sizeof(int) * 4 * nc);
+  if (e == cudaSuccess) e = cudaMalloc(&d_count, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(d_flags, flags, nc, cudaMemcpyHostToDevice);
+  int n = 0;
+  if (e == cudaSuccess) {
+    k_amr_compact<<<1, AMR_SCAN>>>(d_flags, (int)nc, nbx, nullptr, d_map, d_pos, d_old, d_count);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&n, d_count, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && n > 0) {
+    k_amr_neighbours<<<(4 * n + 255) / 256, 256>>>(d_pos, d_map, n, nbx, nby, bc[0], bc[1], bc[2], bc[3], d_nbr);
+    e = cudaGetLastError();
+  }
+  std::vector<int> pk((size_t)n);
+  if (e == cudaSuccess && n > 0) e = cudaMemcpy(pk.data(), d_pos, sizeof(int) * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(map, d_map, sizeof(int) * nc, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && n > 0) e = cudaMemcpy(nbr, d_nbr, sizeof(int) * 4 * n, cudaMemcpyDeviceToHost);
+  for (void* p : {(void*)d_flags, (void*)d_map, (void*)d_pos, (void*)d_old, (void*)d_nbr, (void*)d_count})
+    if (p) cudaFree(p);
+  if (e != cudaSuccess) return afail_cuda(e, "janc_amr_block_lists");
+  for (int b = 0; b < n; ++b) {
+    pos[2 * b] = pk[b] & 0xffff;
+    pos[2 * b + 1] = pk[b] >> 16;
+  }
+  *nblk = n;
   return JANC_OK;
 }
 
@@ -790,11 +935,16 @@ int janc_amr_layer_blocks(janc_amr_t A, int level, int* nblk) {
 int janc_amr_get_layer(janc_amr_t A, int level, int* pos, double* U, double* T) {
   if (!A || level < 1 || level > A->a.levels) return afail(JANC_E_INVALID, "janc_amr_get_layer");
   const AmrLayer& L = A->L[level];
-  if (pos)
+  if (pos && L.nblk > 0) {
+    std::vector<int> pk((size_t)L.nblk);
+    cudaError_t e = cudaMemcpyAsync(pk.data(), L.d_pos, sizeof(int) * L.nblk, cudaMemcpyDeviceToHost, A->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(A->stream);
+    if (e != cudaSuccess) return afail_cuda(e, "janc_amr_get_layer");
     for (int b = 0; b < L.nblk; ++b) {
-      pos[2 * b] = L.pos[b] & 0xffff;
-      pos[2 * b + 1] = L.pos[b] >> 16;
+      pos[2 * b] = pk[b] & 0xffff;
+      pos[2 * b + 1] = pk[b] >> 16;
     }
+  }
   if (L.nblk == 0 || (!U && !T)) return JANC_OK;
   const size_t cells = (size_t)L.nblk * AB2;
   std::vector<double> h((size_t)(A->nv + 1) * cells);
@@ -844,7 +994,6 @@ void janc_amr_destroy(janc_amr_t A) {
   if (A->d_mask) cudaFree(A->d_mask);
   if (A->d_flags) cudaFree(A->d_flags);
   if (A->d_status) cudaFree(A->d_status);
-  if (A->d_oldidx) cudaFree(A->d_oldidx);
   if (A->g0) janc_destroy_grid(A->g0);
   delete A;
 }

@@ -953,13 +953,22 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
     if (r == cudaSuccess) r = cudaEventRecord(ev_rec[c % 2], s2);
     return r;
   };
+  // With recomputation the sweep runs on an internal stream of the highest
+  // priority and the recompute on one of the lowest: the sweep is the
+  // critical path, the recompute has a whole segment of slack.
+  cudaStream_t s1 = nullptr;
   if (e == cudaSuccess && L.ncp > 1 && n_steps > 0) {
-    e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, least);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev_rec[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_rev, cudaEventDisableTiming);
-    // s2 starts after everything enqueued on the grid's stream so far
+    // both start after everything enqueued on the grid's stream so far
     if (e == cudaSuccess) e = cudaEventRecord(ev_rev, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_rev, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, ev_rev, 0);
+    if (e == cudaSuccess) st = s1;
     if (e == cudaSuccess) e = recompute(L.ncp - 2);
   }
   for (int c = L.ncp - 1; c >= 0 && e == cudaSuccess && n_steps > 0; --c) {
@@ -1018,6 +1027,11 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
     const cudaError_t e2 = cudaStreamSynchronize(s2);  // nothing is left on it once st is done; a failure shows here
     if (e == cudaSuccess) e = e2;
     cudaStreamDestroy(s2);
+  }
+  if (s1) {
+    const cudaError_t e1 = cudaStreamSynchronize(s1);
+    if (e == cudaSuccess) e = e1;
+    cudaStreamDestroy(s1);
   }
   for (int k = 0; k < 2; ++k)
     if (ev_rec[k]) cudaEventDestroy(ev_rec[k]);

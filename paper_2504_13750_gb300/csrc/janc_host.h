@@ -5,10 +5,6 @@
 //    the server gives every admitted request its piece;
 //  * admission_pass: one pass of the server's admission over its FIFO queue
 //    (arrival order with skip-ahead, slot count, cell budget with aging);
-//  * build_block_lists: a refined layer's block list, position map and
-//    neighbour table from its refinement flags (Sec. 3: blocks at fixed
-//    positions, neighbours across periodic sides, physical and external
-//    sides marked).
 #pragma once
 
 #include <cstddef>
@@ -111,42 +107,6 @@ void admission_pass(std::deque<int>& queue, Pool& pool, int max_active, long lon
 constexpr int NB_EXTERNAL = -1;  // no block there: the layer's external boundary (Sec. 3.1.3)
 constexpr int NB_PHYSICAL = -2;  // the side lies on the domain's wall or zero-gradient boundary
 constexpr int BC_PERIODIC_CODE = 2;
-
-// Block list of a layer whose index space has nbx x nby candidate blocks,
-// from flags[by * nbx + bx] != 0. Outputs: pos (bx | by << 16, in (by, bx)
-// order), map ([nby][nbx] block number or -1) and nbr ([nblk][4]: north,
-// south, west, east). bc holds the domain's left, right, bottom and top
-// boundary codes; across a periodic side the neighbour wraps around.
-inline void build_block_lists(const unsigned char* flags, int nbx, int nby, const int bc[4], std::vector<int>& pos,
-                              std::vector<int>& map, std::vector<int>& nbr) {
-  pos.clear();
-  map.assign((size_t)nbx * nby, -1);
-  for (int by = 0; by < nby; ++by)
-    for (int bx = 0; bx < nbx; ++bx)
-      if (flags[(size_t)by * nbx + bx]) {
-        map[(size_t)by * nbx + bx] = (int)pos.size();
-        pos.push_back(bx | (by << 16));
-      }
-  const int nblk = (int)pos.size();
-  nbr.assign((size_t)4 * nblk, NB_EXTERNAL);
-  const int dxs[4] = {0, 0, -1, 1}, dys[4] = {1, -1, 0, 0}, side[4] = {3, 2, 0, 1};
-  for (int b = 0; b < nblk; ++b) {
-    const int bx = pos[b] & 0xffff, by = pos[b] >> 16;
-    for (int s = 0; s < 4; ++s) {
-      int qx = bx + dxs[s], qy = by + dys[s];
-      const bool inside = qx >= 0 && qx < nbx && qy >= 0 && qy < nby;
-      if (!inside) {
-        if (bc[side[s]] != BC_PERIODIC_CODE) {
-          nbr[(size_t)4 * b + s] = NB_PHYSICAL;
-          continue;
-        }
-        qx = (qx + nbx) % nbx;
-        qy = (qy + nby) % nby;
-      }
-      nbr[(size_t)4 * b + s] = map[(size_t)qy * nbx + qx];
-    }
-  }
-}
 
 }  // namespace host
 }  // namespace janc

@@ -118,6 +118,7 @@ def lib():
             L.janc_amr_get_base.argtypes = [p, p, p, i]
             L.janc_amr_status.argtypes = [p, ctypes.POINTER(i)]
             L.janc_amr_cell_updates.argtypes = [p, ctypes.POINTER(ctypes.c_longlong)]
+            L.janc_amr_block_lists.argtypes = [p, i, i, p, p, p, p, ctypes.POINTER(i)]
             L.janc_amr_destroy.argtypes = [p]
             L.janc_amr_destroy.restype = None
             sz = ctypes.c_size_t
@@ -682,6 +683,23 @@ def janc_amr_step(a, n_steps, dt=0.0, cfl=0.0):
     t = ctypes.c_double()
     _check(lib().janc_amr_step(a, int(n_steps), float(dt), float(cfl), ctypes.byref(t)))
     return t.value
+
+
+def janc_amr_block_lists(flags, bc):
+    """(pos [nblk, 2], map [nby, nbx], nbr [nblk, 4]) of the device block-list
+    builder for the refinement flags [nby, nbx] (see include/janc.h)."""
+    f = np.ascontiguousarray(flags, dtype=np.uint8)
+    nby, nbx = f.shape
+    b = np.ascontiguousarray(bc, dtype=np.int32)
+    pos = np.zeros(2 * nbx * nby, dtype=np.int32)
+    mp = np.zeros(nbx * nby, dtype=np.int32)
+    nbr = np.zeros(4 * nbx * nby, dtype=np.int32)
+    n = ctypes.c_int()
+    _check(lib().janc_amr_block_lists(f.ctypes.data_as(ctypes.c_void_p), nbx, nby, b.ctypes.data_as(ctypes.c_void_p),
+                                      pos.ctypes.data_as(ctypes.c_void_p), mp.ctypes.data_as(ctypes.c_void_p),
+                                      nbr.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))
+    k = n.value
+    return pos[:2 * k].reshape(k, 2), mp.reshape(nby, nbx), nbr[:4 * k].reshape(k, 4)
 
 
 def janc_amr_layer_blocks(a, level):

@@ -86,19 +86,5 @@ int hh_admission(int n, const long long* cells, const long long* fp, const doubl
   return na;
 }
 
-// Block lists of an nbx x nby layer from flags; bc = left, right, bottom,
-// top. pos gets (bx, by) pairs, map nbx * nby entries, nbr 4 per block
-// (north, south, west, east). Returns the number of blocks.
-int hh_block_lists(const unsigned char* flags, int nbx, int nby, const int* bc, int* pos, int* map, int* nbr) {
-  std::vector<int> p, m, b;
-  build_block_lists(flags, nbx, nby, bc, p, m, b);
-  for (size_t k = 0; k < p.size(); ++k) {
-    pos[2 * k] = p[k] & 0xffff;
-    pos[2 * k + 1] = p[k] >> 16;
-  }
-  std::memcpy(map, m.data(), sizeof(int) * m.size());
-  std::memcpy(nbr, b.data(), sizeof(int) * b.size());
-  return (int)p.size();
-}
 
 }  // extern "C"

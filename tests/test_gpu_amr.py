@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from amr import AMROracle
+from amr import EXTERNAL, PHYSICAL, AMROracle, Layer
 from paper_2504_13750_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -158,3 +158,40 @@ def test_full_layer_is_a_decomposed_fine_grid(J):
     assert a.status() == 0
     a.close()
     f.close()
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (2, 2, 0, 0), (1, 1, 2, 2), (2, 2, 2, 2), (0, 1, 1, 0)])
+def test_device_block_lists_match_the_oracle_layer(J, bc):
+    """The regrid's block lists, built on the device from refinement flags
+    (janc_amr_block_lists: the compaction and neighbour kernels of the
+    regrid), against the AMR oracle's definition: blocks in (by, bx) order,
+    the position map, and the neighbours across every side (periodic partner,
+    physical side, external side), for random flag patterns."""
+    rng = np.random.default_rng(sum(bc) + 7)
+    for nbx, nby in [(1, 1), (2, 3), (8, 4), (13, 5), (256, 64), (1024, 128)]:
+        for density in (0.0, 0.3, 0.7, 1.0):
+            flags = (rng.random((nby, nbx)) < density).astype(np.uint8)
+            pos, mp, nbr = J.janc_amr_block_lists(flags, bc)
+            opos = [(bx, by) for by in range(nby) for bx in range(nbx) if flags[by, bx]]
+            assert [tuple(p) for p in pos] == opos
+            want_map = -np.ones((nby, nbx), dtype=np.int32)
+            for k, (bx, by) in enumerate(opos):
+                want_map[by, bx] = k
+            assert np.array_equal(mp, want_map)
+            if nbx * nby <= 4096:  # the oracle's neighbour walk is plain Python
+                lay = Layer(1, opos, None, None, nbx, nby, bc)
+                for k in range(len(opos)):
+                    assert tuple(nbr[k]) == lay.neighbours(k), (nbx, nby, k)
+    assert EXTERNAL == -1 and PHYSICAL == -2   # the codes the kernels use
+
+
+def test_regrid_every_step_matches_the_oracle(J):
+    """A regrid before every base step of the reacting tube: each regrid
+    builds the lists on the device, refills the state into the layer's spare
+    buffer (growing the buffers only when the layer outgrows them) and swaps
+    it in; the layers and the base still match the AMR oracle step by step."""
+    st = inputs.tube(H2AIR, 64, 16, Lx=0.05 * 64 / 256, perturb_seed=3)
+    dx = st["grid"]["dx"]
+    a, o = _compare(J, H2AIR, st, True, levels=2, thr=100.0 / dx, nbuf=2, every=1, nsteps=6)
+    assert all(o.layers[i].pos for i in range(1, 3))
+    a.close()

@@ -6,10 +6,10 @@ driven on the CPU through tests/host_harness.cpp:
 * the admission pass of the continuous-batching server: arrival order with
   skip-ahead past requests the pool cannot hold, the slot limit, the cell
   budget (a request over it is admitted only into an empty active set; later
-  requests pass it until it has waited max_skip_s), failed admissions;
-* the AMR block lists and neighbour tables (Sec. 3: fixed block positions,
-  neighbours across periodic sides, physical and external sides), against
-  the AMR oracle's own neighbour definition (oracle/amr.py, Layer)."""
+  requests pass it until it has waited max_skip_s), failed admissions.
+
+(The AMR block lists are built on the device; tests/test_gpu_amr.py checks
+them against the AMR oracle's neighbour definition.)"""
 import ctypes
 import os
 import shutil
@@ -17,8 +17,6 @@ import subprocess
 
 import numpy as np
 import pytest
-
-from amr import EXTERNAL, PHYSICAL, Layer
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -39,8 +37,6 @@ def hh(tmp_path_factory):
     lib.hh_admission.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_longlong, ctypes.c_int, ctypes.c_longlong,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                  P, P, P, P]
-    lib.hh_block_lists.restype = ctypes.c_int
-    lib.hh_block_lists.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P]
     return lib
 
 
@@ -154,29 +150,3 @@ def test_failed_admission_leaves_the_queue_and_returns_its_piece(hh):
     reqs = [(10, 4096, 0.0), (10, 4096, 0.0), (10, 4096, 0.0)]
     adm, left, used = admission(hh, reqs, fail={1})
     assert adm == [0, 2] and left == [] and used == 2 * 4096
-
-
-@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (2, 2, 0, 0), (1, 1, 2, 2), (2, 2, 2, 2), (0, 1, 1, 0)])
-def test_block_lists_match_the_oracle_layer(hh, bc):
-    rng = np.random.default_rng(sum(bc) + 7)
-    for nbx, nby in [(1, 1), (2, 3), (8, 4), (13, 5)]:
-        for density in (0.0, 0.3, 0.7, 1.0):
-            flags = (rng.random((nby, nbx)) < density).astype(np.uint8)
-            pos = np.zeros(2 * nbx * nby, dtype=np.int32)
-            mp = np.zeros(nbx * nby, dtype=np.int32)
-            nbr = np.zeros(4 * nbx * nby, dtype=np.int32)
-            bca = np.array(bc, dtype=np.int32)
-            nb = hh.hh_block_lists(_ptr(np.ascontiguousarray(flags)), nbx, nby, _ptr(bca), _ptr(pos), _ptr(mp),
-                                   _ptr(nbr))
-            opos = [(bx, by) for by in range(nby) for bx in range(nbx) if flags[by, bx]]
-            assert nb == len(opos)
-            got = [tuple(pos[2 * k:2 * k + 2]) for k in range(nb)]
-            assert got == opos
-            lay = Layer(1, opos, None, None, nbx, nby, bc)
-            for k in range(nb):
-                assert tuple(nbr[4 * k:4 * k + 4]) == lay.neighbours(k), (nbx, nby, k)
-            want_map = -np.ones((nby, nbx), dtype=np.int32)
-            for k, (bx, by) in enumerate(opos):
-                want_map[by, bx] = k
-            assert np.array_equal(mp.reshape(nby, nbx), want_map)
-    assert EXTERNAL == -1 and PHYSICAL == -2   # the codes the host header uses
