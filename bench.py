@@ -417,9 +417,12 @@ def _amr_timed(janc, stream, mech, st, levels, every, sync, warm, steps):
     t0 = time.perf_counter()
     # chunks of one regrid period: the layers (and so the updates per step)
     # only change at a regrid, which opens each chunk; one host read per chunk
-    for _ in range(steps // every):
-        t_sim += a.step(every, cfl=0.5)
-        updates += a.cell_updates() * every
+    done = 0
+    while done < steps:  # the warm-up is a multiple of `every`, so every chunk opens with a regrid
+        k = min(every, steps - done)
+        t_sim += a.step(k, cfl=0.5)
+        updates += a.cell_updates() * k
+        done += k
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     status = a.status()
