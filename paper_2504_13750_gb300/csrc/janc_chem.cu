@@ -23,9 +23,11 @@
 // reaction's species, coefficients and third-body data from the run-time
 // table, FixRx<I> returns them as compile-time constants of the shipped H2-air
 // mechanism (janc_mech_fixed.cuh). Both run the same operations in the same
-// order, so they give the same bits; with FixRx every index of the per-cell
-// arrays (concentrations, exp(G_k), production rates, Jacobian) is a constant
-// and the arrays live in registers instead of local memory.
+// order (the compiler may still contract multiply-adds differently in the
+// two, so their results agree to rounding, each within the oracle's bars);
+// with FixRx every index of the per-cell arrays (concentrations, exp(G_k),
+// production rates, Jacobian) is a constant and the arrays live in registers
+// instead of local memory.
 #include <utility>
 
 #include "janc_device.cuh"

@@ -82,7 +82,7 @@ struct GridDev {
   const double* halo_lo;
   const double* halo_hi;
   // 1: the mechanism has the reaction structure compiled into the fixed
-  // chemistry kernels (same arithmetic, every index a constant)
+  // chemistry kernels (the same operations, every index a constant)
   int chem_fixed;
 };
 

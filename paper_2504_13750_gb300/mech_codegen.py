@@ -9,7 +9,7 @@ the per-cell rates, Jacobian and production arrays is a constant, so those
 arrays live in registers. The numbers (A, b, Ea, the coefficients' values, the
 thermodynamic fits) stay run-time data. A grid whose mechanism has this
 structure takes the compiled kernels; any other mechanism takes the generic
-ones, whose arithmetic is the same.
+ones, which run the same operations in the same order.
 
 Run by build.build() before compiling (it rewrites the header only when its
 text changes); `python -m paper_2504_13750_gb300.mech_codegen` prints it.
