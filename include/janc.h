@@ -224,13 +224,36 @@ int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
 #define JANC_LOSS_ENDWALL_P 0  /* L = sum_n dt * mean_j p(nx-1, j) of U^{n+1} */
 #define JANC_LOSS_SEEDED 1     /* L = <seed, U^N> (seed: nv planes) */
 
+/* How the reverse sweep gets the derivatives of the WENO5 reconstructions
+ * (Eq. 4.10) of every stage state. JANC_ADJ_RECOMPUTE (the default): the
+ * face pass of each RHS vector-Jacobian product recomputes them from the
+ * stage state. JANC_ADJ_STORE_FACES: the steps that fill a segment store
+ * (the forward's last segment, every recomputed segment) run a face-flux
+ * kernel that also stores, per face, variable and split sign, the four
+ * partials of the reconstruction with respect to its window's differences,
+ * and the reverse face pass only weights them by the cotangent. That moves
+ * about two thirds of the reverse face work into the recompute, which runs
+ * on its own stream beside the sweep, at a memory cost of
+ * 8 nv ((nx+1) ny + (ny+1) nx) doubles per RK stage: 3 ckpt_every stages per
+ * segment store (two stores when there is more than one segment). The face
+ * fluxes, the trajectory and the loss are the same bit for bit in both
+ * modes; the gradients agree to rounding. The mode is read when
+ * janc_adjoint_workspace_bytes and janc_adjoint_forward run; a pending
+ * forward keeps the mode it started with. JANC_E_INVALID for another mode.
+ * The paper has no counterpart: it is a memory-for-work trade of this
+ * implementation of the discrete adjoint. */
+#define JANC_ADJ_RECOMPUTE 0
+#define JANC_ADJ_STORE_FACES 1
+int janc_set_adjoint_mode(janc_grid_t g, int mode);
+
 /* Device bytes janc_step_adjoint needs as workspace: checkpoints every
  * ckpt_every steps, the stage states of one segment of ckpt_every steps (two
  * such stores when n_steps > ckpt_every), cotangent and face buffers. The
  * forward writes the last segment's stages directly, so the reverse
  * recomputes every segment but the last; with ckpt_every >= n_steps the
  * whole trajectory is kept and nothing is recomputed (about
- * (4 n_steps + 2) (nv + 4) nx ny doubles). */
+ * (4 n_steps + 2) (nv + 4) nx ny doubles, plus the face derivatives of
+ * 3 n_steps stage states in mode JANC_ADJ_STORE_FACES). */
 int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, size_t* bytes);
 
 /* From the grid's current state U^0 (set beforehand), run n_steps fixed-dt

@@ -41,21 +41,106 @@ namespace janc {
 // ---------------------------------------------------------------------------
 // Face pass, tiled like the forward face-flux kernel. A block takes
 // VLINES grid lines by VFACES (16, or 8 on small grids) consecutive faces
-// along them (x tiles first,
-// then y tiles), stages the cells with the 5-cell stencil margin (ghosts
-// mapped on the fly) and the cotangent mu of L, and every thread owns one
-// (variable, line): it slides the F+ and F- windows along its faces exactly
-// as the forward does, and at each face reverses both reconstructions for
-// phi = (mu_i - mu_{i-1}) / h (L_i = -(F_{i+1/2} - F_{i-1/2}) / h).
+// along them (x tiles first, then y tiles) and stages the cotangent mu of L
+// for them; every thread owns one (variable, line) and walks its faces. At
+// face t, L_i = -(F_{i+1/2} - F_{i-1/2}) / h gives the face value the
+// cotangent phi = (mu_i - mu_{i-1}) / h, and each of the two reconstructions
+// W (F+ and F-) passes it on as phi dW/dF_j to the five split-flux values of
+// its window.
 //
-// The cotangents of the split fluxes are summed per stencil position in
-// registers while the window passes, and each position is added once to
-// GF (zeroed) when the window leaves it or the tile ends: position e of a
-// line (e = -3 .. ncell + 2, ghosts included) holds (dL/dF+_e, dL/dF-_e).
-// GF layout: x faces [k][j][i + 3][2], y faces [k][j + 3][i][2]. A position
-// is touched by the faces of at most two tiles, so each slot receives at
-// most two additions onto zero, whose result does not depend on their order.
+// dW/dF_j comes from the partials with respect to the window differences
+// D_m = F_m - F_{m-1} (weno_face_dD) plus the centre F2's weight one. The
+// walk sums phi dW/dD_m per difference ("edge" q between positions q-1 and
+// q), and a position's sum is complete once the faces have passed both of
+// its edges: edge q minus edge q+1 plus the phi of the face whose window it
+// centres. Each complete position, ghost positions -3 .. ncell + 2 included,
+// is added to GF (zeroed beforehand): position e of a line holds
+// (dL/dF+_e, dL/dF-_e); GF layout x faces [k][j][i + 3][2], y faces
+// [k][j + 3][i][2]. A position is touched by the faces of at most two tiles,
+// so each slot receives at most two additions onto zero, whose result does
+// not depend on their order.
+//
+// Two forms: k_adj_faces recomputes the reconstructions from the staged
+// cells; k_adj_faces_lin reads the derivatives the forward stored
+// (launch_face_flux_lin) and only forms the sums.
 constexpr int VLINES = 8;
+
+// The per-position sums of one (variable, line) as its faces pass.
+struct EdgeSums {
+  double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;  // F+ edges t+1 .. t+4 at face t
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;  // F- edges t+2 .. t+5
+  double pp = 0.0, pm = 0.0;                      // the last completed F+ / F- edge (t, t+1)
+  double ph1 = 0.0, ph2 = 0.0;                    // phi of faces t-1 and t-2
+  // After face t's partials are in: positions t (F+) and t+1 (F-) are
+  // complete; add them to slot pair `s` (+0) and the next pair (+1).
+  __device__ __forceinline__ void finish_face(double phi, double* gs, long long pstride) {
+    atomicAdd(gs, (pp - p0) + ph2);
+    atomicAdd(gs + pstride + 1, (pm - m0) + ph2);
+    pp = p0; p0 = p1; p1 = p2; p2 = p3; p3 = 0.0;
+    pm = m0; m0 = m1; m1 = m2; m2 = m3; m3 = 0.0;
+    ph2 = ph1; ph1 = phi;
+  }
+  // After the tile's last face (nf faces): positions nf .. nf+3 (F+) and
+  // nf+1 .. nf+4 (F-), starting at slot pair `s` of position nf.
+  __device__ __forceinline__ void flush(double* gs, long long pstride) {
+    atomicAdd(gs, (pp - p0) + ph2);
+    atomicAdd(gs + pstride, (p0 - p1) + ph1);
+    atomicAdd(gs + 2 * pstride, p1 - p2);
+    atomicAdd(gs + 3 * pstride, p2);
+    atomicAdd(gs + pstride + 1, (pm - m0) + ph2);
+    atomicAdd(gs + 2 * pstride + 1, (m0 - m1) + ph1);
+    atomicAdd(gs + 3 * pstride + 1, m1 - m2);
+    atomicAdd(gs + 4 * pstride + 1, m2);
+  }
+};
+
+// Tile geometry shared by both face-pass forms.
+struct VjpTile {
+  bool xdir;
+  int f0, l0, nlines, nfaces, ncell, bc_lo, bc_hi, nmom;
+  __device__ __forceinline__ VjpTile(const GridDev& g, int blk, int nbx, int ntx_x, int ntx_y, int vfaces) {
+    xdir = blk < nbx;
+    const int tile = xdir ? blk : blk - nbx;
+    const int ntl = xdir ? ntx_x : ntx_y;
+    const int ta = tile % ntl, tb = tile / ntl;
+    f0 = xdir ? ta * vfaces : tb * vfaces;
+    l0 = xdir ? tb * VLINES : ta * VLINES;
+    nlines = xdir ? g.ny : g.nx;
+    nfaces = (xdir ? g.nx : g.ny) + 1;
+    ncell = xdir ? g.nx : g.ny;
+    bc_lo = xdir ? g.bc[0] : g.bc[2];
+    bc_hi = xdir ? g.bc[1] : g.bc[3];
+    nmom = xdir ? 1 : 2;
+  }
+};
+
+// Stages mu of cells f0-1 .. f0+VFACES-1 of the tile's lines (zero outside).
+template <int NV, int VFACES>
+__device__ __forceinline__ void stage_mu(const VjpTile& T, const double* __restrict__ mu, const GridDev& g,
+                                         double (*sMu)[VLINES][VFACES + 1]) {
+  const long long n = g.n;
+  for (int q = threadIdx.x; q < VLINES * (VFACES + 1); q += blockDim.x) {
+    int line, w;
+    if (T.xdir) { line = q / (VFACES + 1); w = q % (VFACES + 1); } else { w = q / VLINES; line = q % VLINES; }
+    const int lg = T.l0 + line;
+    const int c = T.f0 - 1 + w;
+    const bool in = lg < T.nlines && c >= 0 && c < T.ncell;
+    const long long idx = T.xdir ? (long long)lg * g.nx + c : (long long)c * g.nx + lg;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sMu[k][line][w] = in ? mu[(long long)k * n + idx] : 0.0;
+  }
+}
+
+// Slot pair of tile position 0 (cell f0 - 3) of (var, lg), and the pair stride.
+__device__ __forceinline__ double* gf_base(const VjpTile& T, double* GFx, double* GFy, const GridDev& g, int var,
+                                           int lg, long long& pstride) {
+  if (T.xdir) {
+    pstride = 2;
+    return GFx + (((long long)var * g.ny + lg) * (g.nx + 6) + T.f0) * 2;
+  }
+  pstride = 2LL * g.nx;
+  return GFy + (((long long)var * (g.ny + 6) + T.f0) * g.nx + lg) * 2;
+}
 
 template <int NV, int VFACES>
 __global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const double* __restrict__ alpha2,
@@ -66,36 +151,25 @@ __global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const do
   __shared__ double sU[NV][VLINES][VWIN];
   __shared__ double sLp[VLINES][VWIN], sLm[VLINES][VWIN], sHp[VLINES][VWIN], sHpu[VLINES][VWIN];
   __shared__ double sMu[NV][VLINES][VFACES + 1];
-  const int blk = blockIdx.x;
-  const bool xdir = blk < nbx;
-  const int tile = xdir ? blk : blk - nbx;
-  const int ntl = xdir ? ntx_x : ntx_y;
-  const int ta = tile % ntl, tb = tile / ntl;
+  const VjpTile T(g, blockIdx.x, nbx, ntx_x, ntx_y, VFACES);
   const long long n = g.n;
-  const int nx = g.nx, ny = g.ny;
-  const int f0 = xdir ? ta * VFACES : tb * VFACES;
-  const int l0 = xdir ? tb * VLINES : ta * VLINES;
-  const int nlines = xdir ? ny : nx;
-  const int nfaces = (xdir ? nx : ny) + 1;
-  const int ncell = xdir ? nx : ny;
-  const int bc_lo = xdir ? g.bc[0] : g.bc[2], bc_hi = xdir ? g.bc[1] : g.bc[3];
-  const int nmom = xdir ? 1 : 2;
-  const double ha = 0.5 * alpha2[xdir ? 0 : 1];
-  const double rh = xdir ? g.rdx : g.rdy;
-  const double* uplane = S.plane(xdir ? NV + 1 : NV + 2, n);
+  const int nx = g.nx;
+  const double ha = 0.5 * alpha2[T.xdir ? 0 : 1];
+  const double rh = T.xdir ? g.rdx : g.rdy;
+  const double* uplane = S.plane(T.xdir ? NV + 1 : NV + 2, n);
   const double* pplane = S.plane(NV + 3, n);
 
-  // ---- stage: cells f0-3 .. f0+VFACES+1 of every line, and mu at f0-1 .. f0+VFACES-1 ----
+  // ---- stage: cells f0-3 .. f0+VFACES+1 of every line, and mu ----
   for (int q = threadIdx.x; q < VLINES * VWIN; q += blockDim.x) {
     int line, w;
-    if (xdir) { line = q / VWIN; w = q % VWIN; } else { w = q / VLINES; line = q % VLINES; }
-    int lg = l0 + line;
-    if (lg >= nlines) lg = nlines - 1;  // inactive line: any valid cell
-    int cg = f0 - 3 + w;
-    if (cg > ncell + 2) cg = ncell + 2;
+    if (T.xdir) { line = q / VWIN; w = q % VWIN; } else { w = q / VLINES; line = q % VLINES; }
+    int lg = T.l0 + line;
+    if (lg >= T.nlines) lg = T.nlines - 1;  // inactive line: any valid cell
+    int cg = T.f0 - 3 + w;
+    if (cg > T.ncell + 2) cg = T.ncell + 2;
     bool flip;
-    const int src = ghost_src(cg, ncell, bc_lo, bc_hi, flip);
-    const long long idx = xdir ? (long long)lg * nx + src : (long long)src * nx + lg;
+    const int src = ghost_src(cg, T.ncell, T.bc_lo, T.bc_hi, flip);
+    const long long idx = T.xdir ? (long long)lg * nx + src : (long long)src * nx + lg;
     double un = uplane[idx];
     if (flip) un = -un;
     const double hp = 0.5 * pplane[idx];
@@ -106,78 +180,83 @@ __global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const do
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double v = S.plane(k, n)[idx];
-      if (flip && k == nmom) v = -v;
+      if (flip && k == T.nmom) v = -v;
       sU[k][line][w] = v;
     }
   }
-  for (int q = threadIdx.x; q < VLINES * (VFACES + 1); q += blockDim.x) {
-    int line, w;
-    if (xdir) { line = q / (VFACES + 1); w = q % (VFACES + 1); } else { w = q / VLINES; line = q % VLINES; }
-    const int lg = l0 + line;
-    const int c = f0 - 1 + w;
-    const bool in = lg < nlines && c >= 0 && c < ncell;
-    const long long idx = xdir ? (long long)lg * nx + c : (long long)c * nx + lg;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sMu[k][line][w] = in ? mu[(long long)k * n + idx] : 0.0;
-  }
+  stage_mu<NV, VFACES>(T, mu, g, sMu);
   __syncthreads();
 
   const int var = threadIdx.x / VLINES;
   const int line = threadIdx.x % VLINES;
-  const int lg = l0 + line;
-  if (lg >= nlines) return;
-  const int nf = min(VFACES, nfaces - f0);
+  const int lg = T.l0 + line;
+  if (lg >= T.nlines) return;
+  const int nf = min(VFACES, T.nfaces - T.f0);
   const double* Ul = sU[var][line];
   const double* lp = sLp[line];
   const double* lm = sLm[line];
-  const double* pt = (var == nmom) ? sHp[line] : (var == 3 ? sHpu[line] : nullptr);
+  const double* pt = (var == T.nmom) ? sHp[line] : (var == 3 ? sHpu[line] : nullptr);
   const double* ml = sMu[var][line];
   auto Fp = [&](int w) -> double { return pt ? fma(lp[w], Ul[w], pt[w]) : lp[w] * Ul[w]; };
   auto Fm = [&](int w) -> double { return pt ? fma(lm[w], Ul[w], pt[w]) : lm[w] * Ul[w]; };
-  // position w of the tile (cell f0 - 3 + w) -> its GF slot pair
-  double* gbase;
   long long pstride;
-  if (xdir) {
-    gbase = GFx + (((long long)var * ny + lg) * (nx + 6) + f0) * 2;
-    pstride = 2;
-  } else {
-    gbase = GFy + (((long long)var * (ny + 6) + f0) * nx + lg) * 2;
-    pstride = 2LL * nx;
-  }
+  double* gbase = gf_base(T, GFx, GFy, g, var, lg, pstride);
+  const double rh4 = 4.0 * rh;
   Win P, M;
   P.init(Fp(0), Fp(1), Fp(2), Fp(3), Fp(4), g.eps4);
   M.init(Fm(1), Fm(2), Fm(3), Fm(4), Fm(5), g.eps4);
-  // Ap[m]: dL/dF+ at position t + m, Am[m]: dL/dF- at position t + 1 + m (face t)
-  double Ap[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, Am[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  EdgeSums E;
   for (int t = 0; t < nf; ++t) {
-    const double phi = rh * (ml[t + 1] - ml[t]);
-    double gp[5], gm[5];
-    weno_face_vjp<false>(P.D1, P.D2, P.D3, P.D4, P.S1, P.S2, P.S3, P.T1, P.T2, P.T3, phi, gp);
-    weno_face_vjp<true>(M.D1, M.D2, M.D3, M.D4, M.S1, M.S2, M.S3, M.T1, M.T2, M.T3, phi, gm);
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      Ap[m] += gp[m];
-      Am[m] += gm[m];
-    }
-    atomicAdd(gbase + (long long)t * pstride, Ap[0]);
-    atomicAdd(gbase + (long long)(t + 1) * pstride + 1, Am[0]);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      Ap[m] = Ap[m + 1];
-      Am[m] = Am[m + 1];
-    }
-    Ap[4] = 0.0;
-    Am[4] = 0.0;
+    const double dmu = ml[t + 1] - ml[t];
+    weno_face_dD<false, true>(P, rh4 * dmu, nullptr, E.p0, E.p1, E.p2, E.p3);
+    weno_face_dD<true, true>(M, rh4 * dmu, nullptr, E.m0, E.m1, E.m2, E.m3);
+    E.finish_face(rh * dmu, gbase + (long long)t * pstride, pstride);
     if (t + 1 < nf) {
       P.push(Fp(t + 5), g.eps4);
       M.push(Fm(t + 6), g.eps4);
     }
   }
+  E.flush(gbase + (long long)nf * pstride, pstride);
+}
+
+template <int NV, int VFACES>
+__global__ void __launch_bounds__(VLINES * NV) k_adj_faces_lin(const double* __restrict__ lin,
+                                                               const double* __restrict__ mu, double* __restrict__ GFx,
+                                                               double* __restrict__ GFy, GridDev g, int nbx, int ntx_x,
+                                                               int ntx_y) {
+  __shared__ double sMu[NV][VLINES][VFACES + 1];
+  const VjpTile T(g, blockIdx.x, nbx, ntx_x, ntx_y, VFACES);
+  stage_mu<NV, VFACES>(T, mu, g, sMu);
+  __syncthreads();
+  const int var = threadIdx.x / VLINES;
+  const int line = threadIdx.x % VLINES;
+  const int lg = T.l0 + line;
+  if (lg >= T.nlines) return;
+  const int nf = min(VFACES, T.nfaces - T.f0);
+  const double rh = T.xdir ? g.rdx : g.rdy;
+  const double* ml = sMu[var][line];
+  // the store's layout (face_flux_tile<..., LIN>): x faces [8][NV][nx+1][ny], then y faces [8][NV][ny+1][nx]
+  const long long nfx = g.nx + 1, nfy = g.ny + 1;
+  const double* lb;
+  long long cstride;
+  if (T.xdir) { lb = lin + ((long long)var * nfx + T.f0) * g.ny + lg; cstride = (long long)NV * nfx * g.ny; }
+  else { lb = lin + 8LL * NV * nfx * g.ny + ((long long)var * nfy + T.f0) * g.nx + lg; cstride = (long long)NV * nfy * g.nx; }
+  const long long fstride = T.nlines;
+  long long pstride;
+  double* gbase = gf_base(T, GFx, GFy, g, var, lg, pstride);
+  EdgeSums E;
+#pragma unroll 4
+  for (int t = 0; t < nf; ++t) {
+    const double* l = lb + (long long)t * fstride;
+    double d[8];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    atomicAdd(gbase + (long long)(nf + m) * pstride, Ap[m]);
-    atomicAdd(gbase + (long long)(nf + 1 + m) * pstride + 1, Am[m]);
+    for (int c = 0; c < 8; ++c) d[c] = __ldg(l + c * cstride);
+    const double phi = rh * (ml[t + 1] - ml[t]);
+    E.p0 = fma(phi, d[0], E.p0); E.p1 = fma(phi, d[1], E.p1); E.p2 = fma(phi, d[2], E.p2); E.p3 = fma(phi, d[3], E.p3);
+    E.m0 = fma(phi, d[4], E.m0); E.m1 = fma(phi, d[5], E.m1); E.m2 = fma(phi, d[6], E.m2); E.m3 = fma(phi, d[7], E.m3);
+    E.finish_face(phi, gbase + (long long)t * pstride, pstride);
   }
+  E.flush(gbase + (long long)nf * pstride, pstride);
 }
 
 // Cell pass: cotangents of U, u_n and p of cell c from the per-position sums
@@ -1042,7 +1121,8 @@ size_t rhs_vjp_scratch_bytes(const GridDev& g) {
 
 template <int NS>
 static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const double* mu, double* nu, double* CFx,
-                             double* CFy, double* scratch, const GridDev& g, const MechDev* mech, cudaStream_t st) {
+                             double* CFy, double* scratch, const GridDev& g, const MechDev* mech, const double* lin,
+                             cudaStream_t st) {
   constexpr int NV = NS + 3;
   const int nb = adj_cell_blocks(g);
   double* adj_alpha = scratch;
@@ -1065,10 +1145,12 @@ static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const
   int nbx, ntx_x, ntx_y;
   int total = tiles(16, &nbx, &ntx_x, &ntx_y);
   if (total >= 8 * sms) {
-    k_adj_faces<NV, 16><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+    if (lin) k_adj_faces_lin<NV, 16><<<total, VLINES * NV, 0, st>>>(lin, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+    else k_adj_faces<NV, 16><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
   } else {
     total = tiles(8, &nbx, &ntx_x, &ntx_y);
-    k_adj_faces<NV, 8><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+    if (lin) k_adj_faces_lin<NV, 8><<<total, VLINES * NV, 0, st>>>(lin, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+    else k_adj_faces<NV, 8><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
   }
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
   k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, nu, adj_alpha, g, mech, part_mx, part_id);
@@ -1078,11 +1160,11 @@ static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const
 
 cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const double* mu, double* nu,
                            double* CFx, double* CFy, double* scratch, const GridDev& g, const MechDev* mech,
-                           cudaStream_t st) {
+                           const double* lin, cudaStream_t st) {
   switch (ns) {
-    case 1: return rhs_vjp_t<1>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, st);
-    case 3: return rhs_vjp_t<3>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, st);
-    case 9: return rhs_vjp_t<9>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, st);
+    case 1: return rhs_vjp_t<1>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, lin, st);
+    case 3: return rhs_vjp_t<3>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, lin, st);
+    case 9: return rhs_vjp_t<9>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, lin, st);
     default: return cudaErrorInvalidValue;
   }
 }

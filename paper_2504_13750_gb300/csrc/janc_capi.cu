@@ -653,12 +653,14 @@ int janc_status(janc_grid_t g, janc_status_info* s) {
 namespace {
 
 struct AdjLayout {
-  size_t state, ckpt, seg, alog, lam, cfx, cfy, small, total;
+  size_t state, ckpt, seg, alog, lin, lin_stage, lam, cfx, cfy, small, total;
   int ncp, seglen;
   int nstore;  // segment stores: 2 when segments are recomputed (the next one while the current is reversed)
 };
 
-AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every) {
+// mode: JANC_ADJ_STORE_FACES adds to each segment store the face derivatives
+// of its 3 ckpt_every stage states (lin_stage doubles each).
+AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every, int mode) {
   AdjLayout L;
   const size_t n = (size_t)g->n;
   const int nv = g->nv;
@@ -669,11 +671,13 @@ AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every) {
   L.nstore = L.ncp > 1 ? 2 : 1;
   L.seg = (size_t)(4 * ckpt_every + 1) * L.state;        // S0[0..len], S1, S2, S* per step (one store)
   L.alog = align256(sizeof(unsigned long long) * 10 * ckpt_every);
+  L.lin_stage = mode == JANC_ADJ_STORE_FACES ? face_lin_doubles(nv, g->gd) : 0;
+  L.lin = align256(sizeof(double) * L.lin_stage * 3 * (size_t)ckpt_every);
   L.lam = 7 * align256(sizeof(double) * (size_t)nv * n);
   L.cfx = align256(sizeof(double) * (size_t)nv * g->gd.ny * (g->gd.nx + 1) * 10);
   L.cfy = align256(sizeof(double) * (size_t)nv * (g->gd.ny + 1) * g->gd.nx * 10);
   L.small = 256 + rhs_vjp_scratch_bytes(g->gd);  // [0] loss, then the RHS-VJP scratch at +256
-  L.total = L.ckpt + L.nstore * (L.seg + L.alog) + L.lam + L.cfx + L.cfy + L.small;
+  L.total = L.ckpt + L.nstore * (L.seg + L.alog + L.lin) + L.lam + L.cfx + L.cfy + L.small;
   return L;
 }
 
@@ -683,7 +687,14 @@ extern "C" {
 
 int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, size_t* bytes) {
   if (!g || !bytes || n_steps < 0 || ckpt_every <= 0) return fail(JANC_E_INVALID, "bad argument");
-  *bytes = adj_layout(g, n_steps, ckpt_every).total;
+  *bytes = adj_layout(g, n_steps, ckpt_every, g->adj_mode).total;
+  return JANC_OK;
+}
+
+int janc_set_adjoint_mode(janc_grid_t g, int mode) {
+  if (!g) return fail(JANC_E_INVALID, "null grid");
+  if (mode != JANC_ADJ_RECOMPUTE && mode != JANC_ADJ_STORE_FACES) return fail(JANC_E_INVALID, "adjoint mode");
+  g->adj_mode = mode;
   return JANC_OK;
 }
 
@@ -713,7 +724,7 @@ int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, s
                                   where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream);
   if (e == cudaSuccess)
     e = launch_rhs_vjp(g->ns, sv(g, 0), (const double*)g->alpha, dmu, dnu, cfx, cfy, scratch, g->gd, g->mech,
-                       g->stream);
+                       nullptr, g->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(nu, dnu, sizeof(double) * nvn,
                         where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream);
@@ -727,10 +738,12 @@ int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, s
 
 namespace {
 
-// One segment store: the states of a segment and their alpha log.
+// One segment store: the states of a segment, their alpha log and (mode
+// JANC_ADJ_STORE_FACES) the face derivatives of every stage state.
 struct SegStore {
   char* seg;
   unsigned long long* alog;
+  double* lin;  // null in mode JANC_ADJ_RECOMPUTE
 };
 
 // Pointers into an adjoint workspace (see adj_layout).
@@ -751,6 +764,7 @@ AdjPtrs adj_ptrs(const janc_grid_s* g, const AdjLayout& L, char* ws) {
   for (int k = 0; k < L.nstore; ++k) {
     q.store[k].seg = p; p += L.seg;
     q.store[k].alog = (unsigned long long*)p; p += L.alog;
+    q.store[k].lin = L.lin_stage ? (double*)p : nullptr; p += L.lin;
   }
   if (L.nstore == 1) q.store[1] = q.store[0];
   for (int k = 0; k < 7; ++k) { q.lam[k] = (double*)p; p += lamb; }
@@ -783,6 +797,10 @@ StateView seg_S0(const SegStore& q, const AdjLayout& L, int m) {
 StateView seg_S(const SegStore& q, const AdjLayout& L, int m, int which) {  // which: 1 = S1, 2 = S2, 3 = S*
   return StateView{(double*)(q.seg + (size_t)(L.seglen + 1 + 3 * m + which - 1) * L.state)};
 }
+// Face derivatives of RK stage s (0: U^n, 1: U1, 2: U2) of step m, or null.
+const double* seg_lin(const SegStore& q, const AdjLayout& L, int m, int s) {
+  return q.lin ? q.lin + (size_t)(3 * m + s) * L.lin_stage : nullptr;
+}
 
 // `len` fixed-dt steps of the Lie (or explicit-source) order from segment
 // slot 0, whose alpha pair is in alog[0..1], keeping every stage state in
@@ -797,19 +815,24 @@ cudaError_t adj_segment(janc_grid_s* g, const AdjLayout& L, const SegStore& q, i
   const int nv = g->nv;
   const bool chem = g->d.chemistry == JANC_CHEM_LIE;
   unsigned long long* alog = q.alog;
+  // the face fluxes of stage s of step m, with its derivatives when the store keeps them
+  auto flux = [&](const StateView& Sin, const unsigned long long* a, int m, int s) {
+    if (!q.lin) return launch_face_flux(nv, Sin, a, g->Fx, g->Gy, g->gd, st);
+    return launch_face_flux_lin(nv, Sin, a, g->Fx, g->Gy, q.lin + (size_t)(3 * m + s) * L.lin_stage, g->gd, st);
+  };
   cudaError_t e = cudaSuccess;
   for (int m = 0; m < len && e == cudaSuccess; ++m) {
     unsigned long long* a = alog + 10 * m;
     if (m > 0) e = cudaMemcpyAsync(a, alog + 10 * (m - 1) + 8, 16, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = launch_face_flux(nv, seg_S0(q, L, m), a, g->Fx, g->Gy, g->gd, st);
+    if (e == cudaSuccess) e = flux(seg_S0(q, L, m), a, m, 0);
     if (e == cudaSuccess)
       e = launch_rk_update(g->ns, 1, seg_S0(q, L, m), seg_S0(q, L, m), seg_S(q, L, m, 1), g->Fx, g->Gy, g->gd,
                            g->mech, ctl, a, a + 2, g->status, clock, st);
-    if (e == cudaSuccess) e = launch_face_flux(nv, seg_S(q, L, m, 1), a + 2, g->Fx, g->Gy, g->gd, st);
+    if (e == cudaSuccess) e = flux(seg_S(q, L, m, 1), a + 2, m, 1);
     if (e == cudaSuccess)
       e = launch_rk_update(g->ns, 2, seg_S(q, L, m, 1), seg_S0(q, L, m), seg_S(q, L, m, 2), g->Fx, g->Gy, g->gd,
                            g->mech, ctl, a, a + 4, g->status, nullptr, st);
-    if (e == cudaSuccess) e = launch_face_flux(nv, seg_S(q, L, m, 2), a + 4, g->Fx, g->Gy, g->gd, st);
+    if (e == cudaSuccess) e = flux(seg_S(q, L, m, 2), a + 4, m, 2);
     if (e == cudaSuccess)
       e = launch_rk_update(g->ns, 3, seg_S(q, L, m, 2), seg_S0(q, L, m), seg_S(q, L, m, 3), g->Fx, g->Gy, g->gd,
                            g->mech, ctl, a, chem ? a + 6 : a + 8, g->status, nullptr, st);
@@ -833,7 +856,8 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
   if (g->d.chemistry == JANC_CHEM_STRANG) return fail(JANC_E_UNSUPPORTED, "the adjoint reverses the Lie order only");
   if (g->halo_side[0] || g->halo_side[1]) return fail(JANC_E_UNSUPPORTED, "the adjoint runs on whole grids, not x-slabs");
   adj_release(g);
-  const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
+  const int mode = g->adj_mode;
+  const AdjLayout L = adj_layout(g, n_steps, ckpt_every, mode);
   char* ws = (char*)workspace;
   bool own = false;
   if (!ws) {
@@ -894,6 +918,7 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
   g->adj.n_steps = n_steps;
   g->adj.ckpt_every = ckpt_every;
   g->adj.loss_kind = loss_kind;
+  g->adj.mode = mode;
   g->adj.dt = dt;
   g->adj.ws = ws;
   g->adj.own = own;
@@ -906,7 +931,7 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
   if (!g->adj.valid) return fail(JANC_E_INVALID, "janc_adjoint_reverse: no pending janc_adjoint_forward");
   const int n_steps = g->adj.n_steps, ckpt_every = g->adj.ckpt_every, loss_kind = g->adj.loss_kind;
   const double dt = g->adj.dt;
-  const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
+  const AdjLayout L = adj_layout(g, n_steps, ckpt_every, g->adj.mode);
   const AdjPtrs q = adj_ptrs(g, L, g->adj.ws);
   cudaStream_t st = g->stream;
   const size_t n = (size_t)g->n;
@@ -992,7 +1017,7 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 2.0 / 3.0 * dt, lamS, 0.0, nullptr, false, st);
       if (e == cudaSuccess)
         e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), mu, nu, cfx, cfy, small + 32, g->gd, g->mech,
-                           st);
+                           seg_lin(sq, L, m, 2), st);
       if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, mu, nu, st);
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam2, 2.0 / 3.0, lamS, 1.0, nu, false, st);
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0 / 3.0, lamS, 0.0, nullptr, false, st);
@@ -1000,14 +1025,15 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 0.25 * dt, lam2, 0.0, nullptr, false, st);
       if (e == cudaSuccess)
         e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), mu, nu, cfx, cfy, small + 32, g->gd, g->mech,
-                           st);
+                           seg_lin(sq, L, m, 1), st);
       if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, mu, nu, st);
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam1, 0.25, lam2, 1.0, nu, false, st);
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 0.75, lam2, 0.0, nullptr, true, st);
       // stage 1: U1 = U^n + dt L(U^n)
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, dt, lam1, 0.0, nullptr, false, st);
       if (e == cudaSuccess)
-        e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 32, g->gd, g->mech, st);
+        e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 32, g->gd, g->mech,
+                           seg_lin(sq, L, m, 0), st);
       if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, mu, nu, st);
       if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0, lam1, 1.0, nu, true, st);
       std::swap(lamN, lam0);
@@ -1051,7 +1077,7 @@ int janc_step_adjoint(janc_grid_t g, int n_steps, double dt, int ckpt_every, int
   int rc = janc_adjoint_forward(g, n_steps, dt, ckpt_every, loss_kind, &loss, workspace, workspace_bytes);
   if (rc) return rc;
   if (loss_kind == JANC_LOSS_SEEDED) {  // loss = <seed, U^N>
-    const AdjLayout L = adj_layout(g, n_steps, ckpt_every);
+    const AdjLayout L = adj_layout(g, n_steps, ckpt_every, g->adj.mode);
     const AdjPtrs q = adj_ptrs(g, L, g->adj.ws);
     const size_t nvn = (size_t)g->nv * (size_t)g->n;
     double* dseed = q.lam[6];

@@ -31,10 +31,14 @@ constexpr int FACES = 32;  // faces per tile of the batched launch and of large 
 // index in the launch (x tiles first). Shared by the single-grid and the
 // batched kernels. HALO: the grid is a slab of an x-slab decomposition and
 // the ghost columns of its BC_HALO sides come from the halo buffers.
-template <int NV, int FC = FACES, bool HALO = false>
+// LIN: also store the reconstructions' derivatives (slide_line2_lin) in
+// `lin`: x faces [8][NV][nx + 1][ny], then y faces [8][NV][ny + 1][nx]
+// (line index fastest, so a warp's stores are contiguous per variable).
+template <int NV, int FC = FACES, bool HALO = false, bool LIN = false>
 __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigned long long* __restrict__ alpha,
                                                double* __restrict__ Fx, double* __restrict__ Gy, const GridDev& g,
-                                               int blk, int nbx, int ntx_x, int ntx_y, double* smem) {
+                                               int blk, int nbx, int ntx_x, int ntx_y, double* smem,
+                                               double* __restrict__ lin = nullptr) {
   constexpr int WIN = FC + 5;
   double* sU = smem;                       // [NV][LINES][WIN]
   double* sLp = sU + NV * LINES * WIN;     // lambda+ = (u_n + alpha) / 2
@@ -114,7 +118,16 @@ __device__ __forceinline__ void face_flux_tile(const StateView& S, const unsigne
     long long stride;
     if (xdir) { out = Fx + ((long long)var * ny + lg) * (nx + 1) + f0; stride = 1; }
     else { out = Gy + ((long long)var * (ny + 1) + f0) * nx + lg; stride = nx; }
-    slide_line2(Ul, sLp + line * WIN, sLm + line * WIN, pt, g.eps4, nf, out, stride);
+    if (LIN) {
+      const long long nfx = nx + 1, nfy = ny + 1;
+      double* lb;
+      long long cstride;
+      if (xdir) { lb = lin + ((long long)var * nfx + f0) * ny + lg; cstride = (long long)NV * nfx * ny; }
+      else { lb = lin + 8LL * NV * nfx * ny + ((long long)var * nfy + f0) * nx + lg; cstride = (long long)NV * nfy * nx; }
+      slide_line2_lin(Ul, sLp + line * WIN, sLm + line * WIN, pt, g.eps4, nf, out, stride, lb, nlines, cstride);
+    } else {
+      slide_line2(Ul, sLp + line * WIN, sLm + line * WIN, pt, g.eps4, nf, out, stride);
+    }
   }
 }
 
@@ -124,6 +137,18 @@ __global__ void __launch_bounds__(LINES * NV) k_face_flux(StateView S, const uns
                                                           GridDev g, int nbx, int ntx_x, int ntx_y) {
   extern __shared__ double smem[];
   face_flux_tile<NV, FC, HALO>(S, alpha, Fx, Gy, g, blockIdx.x, nbx, ntx_x, ntx_y, smem);
+}
+
+// The same face fluxes, bit for bit, plus the derivatives of every
+// reconstruction with respect to its window differences in `lin` (the
+// discrete adjoint's face-derivative store).
+template <int NV, int FC>
+__global__ void __launch_bounds__(LINES * NV) k_face_flux_lin(StateView S, const unsigned long long* __restrict__ alpha,
+                                                              double* __restrict__ Fx, double* __restrict__ Gy,
+                                                              double* __restrict__ lin, GridDev g, int nbx, int ntx_x,
+                                                              int ntx_y) {
+  extern __shared__ double smem[];
+  face_flux_tile<NV, FC, false, true>(S, alpha, Fx, Gy, g, blockIdx.x, nbx, ntx_x, ntx_y, smem, lin);
 }
 
 // Batched form: a persistent grid walks the flattened (request, tile) list;
@@ -228,6 +253,45 @@ static cudaError_t launch_face_flux_t(const StateView& S, const unsigned long lo
                                       const GridDev& g, cudaStream_t st) {
   if (g.bc[0] == BC_HALO || g.bc[1] == BC_HALO) return launch_face_flux_h<NV, true>(S, alpha, Fx, Gy, g, st);
   return launch_face_flux_h<NV, false>(S, alpha, Fx, Gy, g, st);
+}
+
+template <int NV, int FC>
+static cudaError_t launch_face_flux_lin_fc(const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
+                                           double* lin, const GridDev& g, cudaStream_t st) {
+  int nbx, ntx_x, ntx_y, total;
+  tiles_of(g, FC, &nbx, &ntx_x, &ntx_y, &total);
+  const size_t smem = flux_smem_bytes<NV, FC>();
+  static std::atomic<unsigned long long> attr_done{0};
+  cudaError_t e = set_attr_once((const void*)k_face_flux_lin<NV, FC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem, &attr_done);
+  if (e != cudaSuccess) return e;
+  k_face_flux_lin<NV, FC><<<total, LINES * NV, smem, st>>>(S, alpha, Fx, Gy, lin, g, nbx, ntx_x, ntx_y);
+  return cudaGetLastError();
+}
+
+template <int NV>
+static cudaError_t launch_face_flux_lin_t(const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
+                                          double* lin, const GridDev& g, cudaStream_t st) {
+  switch (flux_tile_faces(g)) {
+    case 32: return launch_face_flux_lin_fc<NV, 32>(S, alpha, Fx, Gy, lin, g, st);
+    case 16: return launch_face_flux_lin_fc<NV, 16>(S, alpha, Fx, Gy, lin, g, st);
+    default: return launch_face_flux_lin_fc<NV, 8>(S, alpha, Fx, Gy, lin, g, st);
+  }
+}
+
+size_t face_lin_doubles(int nv, const GridDev& g) {
+  return 8 * (size_t)nv * ((size_t)(g.nx + 1) * g.ny + (size_t)(g.ny + 1) * g.nx);
+}
+
+cudaError_t launch_face_flux_lin(int nv, const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
+                                 double* lin, const GridDev& g, cudaStream_t st) {
+  if (g.bc[0] == BC_HALO || g.bc[1] == BC_HALO) return cudaErrorInvalidValue;  // whole grids only
+  switch (nv) {
+    case 4: return launch_face_flux_lin_t<4>(S, alpha, Fx, Gy, lin, g, st);
+    case 6: return launch_face_flux_lin_t<6>(S, alpha, Fx, Gy, lin, g, st);
+    case 12: return launch_face_flux_lin_t<12>(S, alpha, Fx, Gy, lin, g, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 void face_flux_tiles(const GridDev& g, int* nbx, int* ntx_x, int* ntx_y, int* total) {

@@ -65,9 +65,10 @@ struct janc_grid_s {
   janc::Exchanger* ex = nullptr;  // owned by the grid
   bool alpha_shared = false;
   // trajectory of the last janc_adjoint_forward, for janc_adjoint_reverse
+  int adj_mode = 0;  // JANC_ADJ_RECOMPUTE or JANC_ADJ_STORE_FACES (janc_set_adjoint_mode)
   struct AdjPending {
     bool valid = false;
-    int n_steps = 0, ckpt_every = 1, loss_kind = 0;
+    int n_steps = 0, ckpt_every = 1, loss_kind = 0, mode = 0;
     double dt = 0.0;
     char* ws = nullptr;
     bool own = false;

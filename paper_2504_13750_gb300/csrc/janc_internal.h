@@ -33,6 +33,13 @@ GridParts grid_parts(janc_grid_t g);
 cudaError_t launch_face_flux(int nv, const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
                              const GridDev& g, cudaStream_t st);
 
+// The same face fluxes plus the derivatives of every WENO5 reconstruction
+// with respect to its window differences, face_lin_doubles(nv, g) doubles
+// at `lin` (janc_flux.cu; whole grids only).
+cudaError_t launch_face_flux_lin(int nv, const StateView& S, const unsigned long long* alpha, double* Fx, double* Gy,
+                                 double* lin, const GridDev& g, cudaStream_t st);
+size_t face_lin_doubles(int nv, const GridDev& g);
+
 // RK3 stage `stage` (1..3): Sout = combination of S0 and Sin + dt L(Sin), then
 // Newton T warm-started from Sin's T, aux planes, and the alpha max of Sout
 // into alpha_out (janc_update.cu). alpha_step holds the step's starting alpha.
@@ -80,9 +87,11 @@ int sm_count();
 // Scratch of one launch_rhs_vjp: the two alpha cotangents and the per-block
 // arg-max partials of the LF speeds (256-byte aligned start).
 size_t rhs_vjp_scratch_bytes(const GridDev& g);
+// lin: the state's face-derivative store (launch_face_flux_lin), or null to
+// recompute the reconstructions.
 cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const double* mu, double* nu,
                            double* CFx, double* CFy, double* scratch, const GridDev& g, const MechDev* mech,
-                           cudaStream_t st);
+                           const double* lin, cudaStream_t st);
 cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, const MechDev* mech, double dt,
                             const double* lam, double* out, cudaStream_t st);
 cudaError_t launch_lincomb(long long count, double* out, double a, const double* x, double b, const double* y,

@@ -102,6 +102,7 @@ def lib():
             L.janc_server_destroy.argtypes = [p]
             L.janc_server_destroy.restype = None
             L.janc_adjoint_workspace_bytes.argtypes = [p, i, i, ctypes.POINTER(ctypes.c_size_t)]
+            L.janc_set_adjoint_mode.argtypes = [p, i]
             L.janc_step_adjoint.argtypes = [p, i, d, i, i, p, p, p, p, ctypes.c_size_t, i]
             L.janc_adjoint_forward.argtypes = [p, i, d, i, i, p, p, ctypes.c_size_t]
             L.janc_adjoint_reverse.argtypes = [p, p, p, i]
@@ -298,6 +299,13 @@ def janc_rhs_static(desc, mech: Mechanism, U, T, L, alpha=None, stream=None):
 
 
 LOSS_ENDWALL_P, LOSS_SEEDED = 0, 1
+ADJ_RECOMPUTE, ADJ_STORE_FACES = 0, 1
+
+
+def janc_set_adjoint_mode(g, mode):
+    """ADJ_RECOMPUTE (default) or ADJ_STORE_FACES (face derivatives kept in
+    the segment stores); read by the next workspace query and forward."""
+    _check(lib().janc_set_adjoint_mode(g, int(mode)))
 
 
 def janc_adjoint_workspace_bytes(g, n_steps, ckpt_every) -> int:
