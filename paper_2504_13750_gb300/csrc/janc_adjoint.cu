@@ -144,9 +144,9 @@ __device__ __forceinline__ double* gf_base(const VjpTile& T, double* GFx, double
 
 template <int NV, int VFACES>
 __global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const double* __restrict__ alpha2,
-                                                           const double* __restrict__ mu, double* __restrict__ GFx,
-                                                           double* __restrict__ GFy, GridDev g, int nbx, int ntx_x,
-                                                           int ntx_y) {
+                                                           const double* __restrict__ mu, double mu_scale,
+                                                           double* __restrict__ GFx, double* __restrict__ GFy,
+                                                           GridDev g, int nbx, int ntx_x, int ntx_y) {
   constexpr int VWIN = VFACES + 5;
   __shared__ double sU[NV][VLINES][VWIN];
   __shared__ double sLp[VLINES][VWIN], sLm[VLINES][VWIN], sHp[VLINES][VWIN], sHpu[VLINES][VWIN];
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const do
   const long long n = g.n;
   const int nx = g.nx;
   const double ha = 0.5 * alpha2[T.xdir ? 0 : 1];
-  const double rh = T.xdir ? g.rdx : g.rdy;
+  const double rh = (T.xdir ? g.rdx : g.rdy) * mu_scale;
   const double* uplane = S.plane(T.xdir ? NV + 1 : NV + 2, n);
   const double* pplane = S.plane(NV + 3, n);
 
@@ -221,9 +221,9 @@ __global__ void __launch_bounds__(VLINES * NV) k_adj_faces(StateView S, const do
 
 template <int NV, int VFACES>
 __global__ void __launch_bounds__(VLINES * NV) k_adj_faces_lin(const double* __restrict__ lin,
-                                                               const double* __restrict__ mu, double* __restrict__ GFx,
-                                                               double* __restrict__ GFy, GridDev g, int nbx, int ntx_x,
-                                                               int ntx_y) {
+                                                               const double* __restrict__ mu, double mu_scale,
+                                                               double* __restrict__ GFx, double* __restrict__ GFy,
+                                                               GridDev g, int nbx, int ntx_x, int ntx_y) {
   __shared__ double sMu[NV][VLINES][VFACES + 1];
   const VjpTile T(g, blockIdx.x, nbx, ntx_x, ntx_y, VFACES);
   stage_mu<NV, VFACES>(T, mu, g, sMu);
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(VLINES * NV) k_adj_faces_lin(const double* __r
   const int lg = T.l0 + line;
   if (lg >= T.nlines) return;
   const int nf = min(VFACES, T.nfaces - T.f0);
-  const double rh = T.xdir ? g.rdx : g.rdy;
+  const double rh = (T.xdir ? g.rdx : g.rdy) * mu_scale;
   const double* ml = sMu[var][line];
   // the store's layout (face_flux_tile<..., LIN>): x faces [8][NV][nx+1][ny], then y faces [8][NV][ny+1][nx]
   const long long nfx = g.nx + 1, nfy = g.ny + 1;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(VLINES * NV) k_adj_faces_lin(const double* __r
 // of k_adj_faces, with the ghost positions that copy cell c folded back.
 // Returns via references.
 template <int NV>
-__device__ __forceinline__ void gather_dir(const StateView& S, const double* __restrict__ GF, const GridDev& g,
+__device__ __forceinline__ void gather_dir(const StateView& S, double* __restrict__ GF, const GridDev& g,
                                            double ha, int xdir, int i, int j, double* aU, double& a_un, double& a_p,
                                            double& a_alpha) {
   const long long n = g.n;
@@ -301,9 +301,11 @@ __device__ __forceinline__ void gather_dir(const StateView& S, const double* __r
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const double U = (flip && k == nmom) ? -Uc[k] : Uc[k];
-      const double* gf = GF + 2 * (xdir ? ((long long)k * ny + line) * (nx + 6) + (e + 3)
-                                        : ((long long)k * (ny + 6) + (e + 3)) * nx + line);
+      double* gf = GF + 2 * (xdir ? ((long long)k * ny + line) * (nx + 6) + (e + 3)
+                                  : ((long long)k * (ny + 6) + (e + 3)) * nx + line);
       const double fp = gf[0], fm = gf[1];
+      gf[0] = 0.0;  // each slot is read by exactly one cell: leave the sums zero for the next face pass
+      gf[1] = 0.0;
       const double aUk = lp * fp + lm * fm;
       aU[k] += (flip && k == nmom) ? -aUk : aUk;
       aLp = fma(U, fp, aLp);
@@ -330,8 +332,8 @@ __device__ __forceinline__ void argmax_merge(unsigned long long& m, int& i, unsi
 // (atomically added) and the arg-max of |u|+c and |v|+c over its cells in
 // part_mx / part_id [2 * block + direction].
 template <int NS>
-__global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, const double* __restrict__ GFx,
-                            const double* __restrict__ GFy, double* __restrict__ nu, double* adj_alpha, GridDev g,
+__global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, double* __restrict__ GFx,
+                            double* __restrict__ GFy, VjpIO io, double* adj_alpha, GridDev g,
                             const MechDev* __restrict__ mech, unsigned long long* __restrict__ part_mx,
                             int* __restrict__ part_id) {
   constexpr int NV = NS + 3;
@@ -363,7 +365,17 @@ __global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, cons
     aU[1] += a_u * rrho;
     aU[2] += a_v * rrho;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) nu[(long long)k * n + idx] = fma(dp[k], a_p, aU[k]);
+    for (int k = 0; k < NV; ++k) {
+      const long long kq = (long long)k * n + idx;
+      double va = fma(dp[k], a_p, aU[k]);  // nu
+      if (io.acc_a) va += io.a[kq];
+      if (io.xa) va = fma(io.ca, io.xa[kq], va);
+      io.a[kq] = va;
+      if (io.b) {
+        const double vb = io.cb * io.xb[kq];
+        io.b[kq] = io.acc_b ? io.b[kq] + vb : vb;
+      }
+    }
     // the LF speeds of this cell, as the forward's alpha max formed them
     const double c = sound_speed<NS>(u, T, *mech);
     const double rr = rcp(u[0]);
@@ -410,7 +422,7 @@ __global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, cons
 template <int NS>
 __global__ void k_adj_alpha(StateView S, GridDev g, const MechDev* __restrict__ mech,
                             const unsigned long long* __restrict__ part_mx, const int* __restrict__ part_id, int nb,
-                            const double* adj_alpha, double* nu) {
+                            double* adj_alpha, double* nu) {
   constexpr int NV = NS + 3;
   __shared__ unsigned long long mx[2][256];
   __shared__ int id[2][256];
@@ -493,6 +505,12 @@ __global__ void k_adj_alpha(StateView S, GridDev g, const MechDev* __restrict__ 
     const int cx = id[0][0], cyi = id[1][0];
     if (cx >= 0 && cx < g.n) nu[(long long)k * n + cx] += contrib;
     if (cyi >= 0 && cyi < g.n) nu[(long long)k * n + cyi] += cy;
+  }
+  // the cotangents are consumed: leave them zero for the next cell pass
+  __syncwarp();
+  if (tid == 0) {
+    adj_alpha[0] = 0.0;
+    adj_alpha[1] = 0.0;
   }
 }
 
@@ -918,7 +936,8 @@ __global__ void __launch_bounds__(128) k_adj_chem_rev(StateView Sstar, GridDev g
 // X(U) and the implicit dT/dU.
 template <int NS>
 __global__ void __launch_bounds__(128) k_src_vjp(StateView S, GridDev g, const MechDev* __restrict__ mech,
-                                                 const double* __restrict__ mu, double* __restrict__ nu) {
+                                                 const double* __restrict__ lam, double mu_scale,
+                                                 double* __restrict__ nu) {
   constexpr int NSP = NS - 1;
   constexpr int NV = NS + 3;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -929,7 +948,7 @@ __global__ void __launch_bounds__(128) k_src_vjp(StateView S, GridDev g, const M
 #pragma unroll
   for (int k = 0; k < NV; ++k) u[k] = S.plane(k, n)[q];
 #pragma unroll
-  for (int k = 0; k < NSP; ++k) w[k] = m.M[k] * mu[(long long)(4 + k) * n + q];
+  for (int k = 0; k < NSP; ++k) w[k] = m.M[k] * (mu_scale * lam[(long long)(4 + k) * n + q]);
   const double T = S.plane(NV, n)[q];
   double X[NS];
   double rest = u[0];
@@ -1120,20 +1139,24 @@ size_t rhs_vjp_scratch_bytes(const GridDev& g) {
 }
 
 template <int NS>
-static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const double* mu, double* nu, double* CFx,
-                             double* CFy, double* scratch, const GridDev& g, const MechDev* mech, const double* lin,
+static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const VjpIO& io, double* CFx, double* CFy,
+                             double* scratch, const GridDev& g, const MechDev* mech, const double* lin, bool fresh,
                              cudaStream_t st) {
   constexpr int NV = NS + 3;
   const int nb = adj_cell_blocks(g);
   double* adj_alpha = scratch;
   unsigned long long* part_mx = (unsigned long long*)((char*)scratch + 256);
   int* part_id = (int*)(part_mx + 2 * nb);
-  cudaError_t e = cudaMemsetAsync(adj_alpha, 0, 2 * sizeof(double), st);
-  if (e != cudaSuccess) return e;
-  // CFx / CFy hold the per-position sums (GF of k_adj_faces)
-  e = cudaMemsetAsync(CFx, 0, sizeof(double) * 2 * (size_t)NV * g.ny * (g.nx + 6), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(CFy, 0, sizeof(double) * 2 * (size_t)NV * (g.ny + 6) * g.nx, st);
-  if (e != cudaSuccess) return e;
+  const double* mu = io.lam;
+  const double ms = io.mu_scale;
+  if (fresh) {
+    // CFx / CFy hold the per-position sums (GF of k_adj_faces); the cell
+    // pass and k_adj_alpha leave them and the alpha cotangents zero
+    cudaError_t e = cudaMemsetAsync(adj_alpha, 0, 2 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(CFx, 0, sizeof(double) * 2 * (size_t)NV * g.ny * (g.nx + 6), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(CFy, 0, sizeof(double) * 2 * (size_t)NV * (g.ny + 6) * g.nx, st);
+    if (e != cudaSuccess) return e;
+  }
   // tiles of 16 faces while that gives at least 8 blocks per SM, else 8
   const int sms = sm_count();
   auto tiles = [&](int vf, int* nbx, int* ntx_x, int* ntx_y) {
@@ -1145,26 +1168,26 @@ static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const
   int nbx, ntx_x, ntx_y;
   int total = tiles(16, &nbx, &ntx_x, &ntx_y);
   if (total >= 8 * sms) {
-    if (lin) k_adj_faces_lin<NV, 16><<<total, VLINES * NV, 0, st>>>(lin, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
-    else k_adj_faces<NV, 16><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+    if (lin) k_adj_faces_lin<NV, 16><<<total, VLINES * NV, 0, st>>>(lin, mu, ms, CFx, CFy, g, nbx, ntx_x, ntx_y);
+    else k_adj_faces<NV, 16><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, ms, CFx, CFy, g, nbx, ntx_x, ntx_y);
   } else {
     total = tiles(8, &nbx, &ntx_x, &ntx_y);
-    if (lin) k_adj_faces_lin<NV, 8><<<total, VLINES * NV, 0, st>>>(lin, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
-    else k_adj_faces<NV, 8><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, CFx, CFy, g, nbx, ntx_x, ntx_y);
+    if (lin) k_adj_faces_lin<NV, 8><<<total, VLINES * NV, 0, st>>>(lin, mu, ms, CFx, CFy, g, nbx, ntx_x, ntx_y);
+    else k_adj_faces<NV, 8><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, ms, CFx, CFy, g, nbx, ntx_x, ntx_y);
   }
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-  k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, nu, adj_alpha, g, mech, part_mx, part_id);
-  k_adj_alpha<NS><<<1, 256, 0, st>>>(S, g, mech, part_mx, part_id, nb, adj_alpha, nu);
+  k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, io, adj_alpha, g, mech, part_mx, part_id);
+  k_adj_alpha<NS><<<1, 256, 0, st>>>(S, g, mech, part_mx, part_id, nb, adj_alpha, io.a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const double* mu, double* nu,
-                           double* CFx, double* CFy, double* scratch, const GridDev& g, const MechDev* mech,
-                           const double* lin, cudaStream_t st) {
+cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const VjpIO& io, double* CFx,
+                           double* CFy, double* scratch, const GridDev& g, const MechDev* mech, const double* lin,
+                           bool fresh, cudaStream_t st) {
   switch (ns) {
-    case 1: return rhs_vjp_t<1>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, lin, st);
-    case 3: return rhs_vjp_t<3>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, lin, st);
-    case 9: return rhs_vjp_t<9>(S, alpha2_dev, mu, nu, CFx, CFy, scratch, g, mech, lin, st);
+    case 1: return rhs_vjp_t<1>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, st);
+    case 3: return rhs_vjp_t<3>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, st);
+    case 9: return rhs_vjp_t<9>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1190,11 +1213,11 @@ cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const double* mu,
-                              double* nu, cudaStream_t st) {
+cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const VjpIO& io,
+                              cudaStream_t st) {
   switch (ns) {
-    case 3: k_src_vjp<3><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, mu, nu); break;
-    case 9: k_src_vjp<9><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, mu, nu); break;
+    case 3: k_src_vjp<3><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, io.lam, io.mu_scale, io.a); break;
+    case 9: k_src_vjp<9><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, io.lam, io.mu_scale, io.a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

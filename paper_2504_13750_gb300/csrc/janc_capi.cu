@@ -723,8 +723,9 @@ int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, s
   cudaError_t e = cudaMemcpyAsync(dmu, mu, sizeof(double) * nvn,
                                   where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream);
   if (e == cudaSuccess)
-    e = launch_rhs_vjp(g->ns, sv(g, 0), (const double*)g->alpha, dmu, dnu, cfx, cfy, scratch, g->gd, g->mech,
-                       nullptr, g->stream);
+    e = launch_rhs_vjp(g->ns, sv(g, 0), (const double*)g->alpha,
+                       VjpIO{dmu, 1.0, dnu, nullptr, 0.0, 0, nullptr, nullptr, 0.0, 0}, cfx, cfy, scratch, g->gd,
+                       g->mech, nullptr, true, g->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(nu, dnu, sizeof(double) * nvn,
                         where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream);
@@ -951,12 +952,15 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
   double* lam2 = q.lam[2];
   double* lam1 = q.lam[3];
   double* lam0 = q.lam[4];
-  double* mu = q.lam[5];
-  double* nu = q.lam[6];
   cudaError_t e = cudaSuccess;
   if (seed) e = cudaMemcpyAsync(lamN, seed, sizeof(double) * nvn,
                                 where == JANC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
   else e = cudaMemsetAsync(lamN, 0, sizeof(double) * nvn, st);
+  // the RHS VJPs of the sweep find the per-position sums and the alpha
+  // cotangents zero and leave them zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(cfx, 0, L.cfx, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cfy, 0, L.cfy, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(small + 32, 0, 2 * sizeof(double), st);
   // Segments other than the last are recomputed from their checkpoints on a
   // second stream into the other segment store, one segment ahead of the
   // reverse sweep: segment c - 1 is recomputed while segment c is reversed.
@@ -1013,29 +1017,27 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
         if (chem) e = launch_chem_vjp(g->ns, segS(m, 3), g->gd, g->mech, dt, lamN, lamS, st);
         else e = cudaMemcpyAsync(lamS, lamN, sizeof(double) * nvn, cudaMemcpyDeviceToDevice, st);
       }
-      // stage 3: U* = U^n/3 + 2/3 (U2 + dt L(U2))
-      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 2.0 / 3.0 * dt, lamS, 0.0, nullptr, false, st);
+      // Each stage's RHS VJP takes mu = c dt lam directly and writes the
+      // stage's combinations itself (VjpIO); the explicit-source VJP adds
+      // to the same output.
+      // stage 3: U* = U^n/3 + 2/3 (U2 + dt L(U2)): lam2 = 2/3 lamS + L^T mu, lam0 = lamS / 3
+      const VjpIO io3{lamS, 2.0 / 3.0 * dt, lam2, lamS, 2.0 / 3.0, 0, lam0, lamS, 1.0 / 3.0, 0};
       if (e == cudaSuccess)
-        e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), mu, nu, cfx, cfy, small + 32, g->gd, g->mech,
-                           seg_lin(sq, L, m, 2), st);
-      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, mu, nu, st);
-      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam2, 2.0 / 3.0, lamS, 1.0, nu, false, st);
-      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0 / 3.0, lamS, 0.0, nullptr, false, st);
-      // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
-      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, 0.25 * dt, lam2, 0.0, nullptr, false, st);
+        e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), io3, cfx, cfy, small + 32, g->gd, g->mech,
+                           seg_lin(sq, L, m, 2), false, st);
+      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, io3, st);
+      // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1)): lam1 = lam2 / 4 + L^T mu, lam0 += 3/4 lam2
+      const VjpIO io2{lam2, 0.25 * dt, lam1, lam2, 0.25, 0, lam0, lam2, 0.75, 1};
       if (e == cudaSuccess)
-        e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), mu, nu, cfx, cfy, small + 32, g->gd, g->mech,
-                           seg_lin(sq, L, m, 1), st);
-      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, mu, nu, st);
-      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam1, 0.25, lam2, 1.0, nu, false, st);
-      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 0.75, lam2, 0.0, nullptr, true, st);
-      // stage 1: U1 = U^n + dt L(U^n)
-      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, mu, dt, lam1, 0.0, nullptr, false, st);
+        e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), io2, cfx, cfy, small + 32, g->gd, g->mech,
+                           seg_lin(sq, L, m, 1), false, st);
+      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, io2, st);
+      // stage 1: U1 = U^n + dt L(U^n): lam0 += lam1 + L^T mu
+      const VjpIO io1{lam1, dt, lam0, lam1, 1.0, 1, nullptr, nullptr, 0.0, 0};
       if (e == cudaSuccess)
-        e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, mu, nu, cfx, cfy, small + 32, g->gd, g->mech,
-                           seg_lin(sq, L, m, 0), st);
-      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, mu, nu, st);
-      if (e == cudaSuccess) e = launch_lincomb((long long)nvn, lam0, 1.0, lam1, 1.0, nu, true, st);
+        e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, io1, cfx, cfy, small + 32, g->gd, g->mech,
+                           seg_lin(sq, L, m, 0), false, st);
+      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, io1, st);
       std::swap(lamN, lam0);
     }
     // segment c's store is free once its reverse is done: refill it with c - 2

@@ -48,10 +48,12 @@ cudaError_t launch_rk_update(int ns, int stage, const StateView& Sin, const Stat
                              const StepCtl& ctl, const unsigned long long* alpha_step, unsigned long long* alpha_out,
                              int* status, double* clock2, cudaStream_t st);
 
-// nu += (dS/dU)^T mu for the explicit source S(U) (production rates of the
-// carried species at the stored T) at state S (janc_adjoint.cu).
-cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const double* mu,
-                              double* nu, cudaStream_t st);
+// io.a += (dS/dU)^T mu, mu = io.mu_scale io.lam, for the explicit source S(U)
+// (production rates of the carried species at the stored T) at state S
+// (janc_adjoint.cu).
+struct VjpIO;
+cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const VjpIO& io,
+                              cudaStream_t st);
 
 // Point-implicit chemistry in place on S (janc_chem.cu).
 cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
@@ -87,11 +89,30 @@ int sm_count();
 // Scratch of one launch_rhs_vjp: the two alpha cotangents and the per-block
 // arg-max partials of the LF speeds (256-byte aligned start).
 size_t rhs_vjp_scratch_bytes(const GridDev& g);
+// Input and outputs of one RHS vector-Jacobian product nu = (dL/dU)^T mu
+// with mu = mu_scale lam, fused with the linear combinations of an RK stage
+// of the reverse sweep ([nv][ny][nx] arrays):
+//   a = (acc_a ? a : 0) + ca xa + nu        (xa may be null)
+//   b = (acc_b ? b : 0) + cb xb             (b may be null)
+struct VjpIO {
+  const double* lam;
+  double mu_scale;
+  double* a;
+  const double* xa;
+  double ca;
+  int acc_a;
+  double* b;
+  const double* xb;
+  double cb;
+  int acc_b;
+};
 // lin: the state's face-derivative store (launch_face_flux_lin), or null to
-// recompute the reconstructions.
-cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const double* mu, double* nu,
-                           double* CFx, double* CFy, double* scratch, const GridDev& g, const MechDev* mech,
-                           const double* lin, cudaStream_t st);
+// recompute the reconstructions. fresh: zero the per-position sums and the
+// alpha cotangents first; otherwise they must be zero on entry (every call
+// leaves them zero).
+cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const VjpIO& io, double* CFx,
+                           double* CFy, double* scratch, const GridDev& g, const MechDev* mech, const double* lin,
+                           bool fresh, cudaStream_t st);
 cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, const MechDev* mech, double dt,
                             const double* lam, double* out, cudaStream_t st);
 cudaError_t launch_lincomb(long long count, double* out, double a, const double* x, double b, const double* y,
