@@ -298,14 +298,26 @@ __device__ __forceinline__ void gather_dir(const StateView& S, double* __restric
     const double un = flip ? -un0 : un0;
     const double lp = fma(0.5, un, ha), lm = fma(0.5, un, -ha);
     double aLp = 0.0, aLm = 0.0, a_hp = 0.0, a_hpu = 0.0;
+    // all loads first, then the zeroing (each slot is read by exactly one
+    // cell: the sums are left zero for the next face pass), so the loads are
+    // not held behind the stores
+    double* gf0 = GF + 2 * (xdir ? ((long long)line) * (nx + 6) + (e + 3) : ((long long)(e + 3)) * nx + line);
+    const long long kstride = 2 * (xdir ? (long long)ny * (nx + 6) : (long long)(ny + 6) * nx);
+    double fpk[NV], fmk[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      fpk[k] = gf0[k * kstride];
+      fmk[k] = gf0[k * kstride + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      gf0[k * kstride] = 0.0;
+      gf0[k * kstride + 1] = 0.0;
+    }
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const double U = (flip && k == nmom) ? -Uc[k] : Uc[k];
-      double* gf = GF + 2 * (xdir ? ((long long)k * ny + line) * (nx + 6) + (e + 3)
-                                  : ((long long)k * (ny + 6) + (e + 3)) * nx + line);
-      const double fp = gf[0], fm = gf[1];
-      gf[0] = 0.0;  // each slot is read by exactly one cell: leave the sums zero for the next face pass
-      gf[1] = 0.0;
+      const double fp = fpk[k], fm = fmk[k];
       const double aUk = lp * fp + lm * fm;
       aU[k] += (flip && k == nmom) ? -aUk : aUk;
       aLp = fma(U, fp, aLp);
@@ -597,8 +609,10 @@ struct LocalRateCache {
   }
   __device__ __forceinline__ double k_f(int i) const { return kf[i]; }
   __device__ __forceinline__ double k_b(int i) const { return kb[i]; }
-  __device__ __forceinline__ double dk_f(int i) const { return dkf[i]; }
-  __device__ __forceinline__ double dk_b(int i) const { return dkb[i]; }
+  template <class Rx>
+  __device__ __forceinline__ double dk_f(const Rx& R) const { return dkf[R.idx()]; }
+  template <class Rx>
+  __device__ __forceinline__ double dk_b(const Rx& R) const { return dkb[R.idx()]; }
 };
 struct SharedRateCache {
   double* col;  // this thread's column: entry q at col[q * stride]
@@ -611,9 +625,122 @@ struct SharedRateCache {
   }
   __device__ __forceinline__ double k_f(int i) const { return col[(4 * i) * stride]; }
   __device__ __forceinline__ double k_b(int i) const { return col[(4 * i + 1) * stride]; }
-  __device__ __forceinline__ double dk_f(int i) const { return col[(4 * i + 2) * stride]; }
-  __device__ __forceinline__ double dk_b(int i) const { return col[(4 * i + 3) * stride]; }
+  template <class Rx>
+  __device__ __forceinline__ double dk_f(const Rx& R) const { return col[(4 * R.idx() + 2) * stride]; }
+  template <class Rx>
+  __device__ __forceinline__ double dk_b(const Rx& R) const { return col[(4 * R.idx() + 3) * stride]; }
 };
+// The rate constants the segment recompute's chemistry kept (k_chem_lin:
+// k_f, k_b of reaction i at entries 2i, 2i+1 of cell q) and their log-T
+// derivatives formed here, as the forward pass of chem_vjp_rev forms them:
+// d ln k_f/dT = b/T + Ea/(R T^2), d ln k_b/dT = d ln k_f/dT + sum over the
+// reactants of dG - sum over the products of dG + dnu/T.
+template <int NS>
+struct StoredRateCache {
+  const double* clin;
+  long long n, q;
+  double rT, rT2;
+  const double* dG;
+  const MechDev& m;
+  __device__ __forceinline__ double k_f(int i) const { return __ldg(clin + (2LL * i) * n + q); }
+  __device__ __forceinline__ double k_b(int i) const { return __ldg(clin + (2LL * i + 1) * n + q); }
+  template <class Rx>
+  __device__ __forceinline__ double dk_f(const Rx& R) const {
+    const int i = R.idx();
+    return fma(m.b[i], rT, m.EaR[i] * rT2);
+  }
+  template <class Rx>
+  __device__ __forceinline__ double dk_b(const Rx& R) const {
+    double d = dk_f(R);
+#pragma unroll
+    for (int r = 0; r < R.nre(); ++r)
+#pragma unroll
+      for (int k = 0; k < R.rnu(r); ++k) d += dG[R.rsp(r)];
+#pragma unroll
+    for (int r = 0; r < R.npr(); ++r)
+#pragma unroll
+      for (int k = 0; k < R.pnu(r); ++k) d -= dG[R.psp(r)];
+    return fma((double)R.dnu(), rT, d);
+  }
+};
+
+// Reverse pass over the reactions (shared by both chemistry VJPs): the
+// gradient (gT, gX) of psi = dt sum_i m_i (q_i + Dq_i[x_eff]) in (T, X),
+// m_i = sum_k nu_ki mu_k, with the rate constants and their log-T
+// derivatives from `cache`.
+template <int NS, bool FIXED, class Cache>
+__device__ __forceinline__ void chem_reverse_reactions(const MechDev& m, const double* X, const double* xe, double Ctot,
+                                                       const double* mu, double dt, const Cache& cache, double& gT_out,
+                                                       double* gX) {
+  constexpr int NSP = NS - 1;
+  double gT = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) gX[k] = 0.0;
+  for_reactions<FIXED>(m, [&](auto R) {
+    const int i = R.idx();
+    const int nre = R.nre(), npr = R.npr();
+    double mi = 0.0;
+#pragma unroll
+    for (int r = 0; r < nre; ++r)
+      if (R.rsp(r) < NSP) mi = fma(-R.rnud(r), mu[R.rsp(r)], mi);
+#pragma unroll
+    for (int r = 0; r < npr; ++r)
+      if (R.psp(r) < NSP) mi = fma(R.pnud(r), mu[R.psp(r)], mi);
+    const double w = dt * mi;
+    const double kf = cache.k_f(i), kb = cache.k_b(i);
+    double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
+    monomial(X, [&](int s_) { return R.rsp(s_); }, [&](int s_) { return R.rnu(s_); }, nre, xe, F, gF, DF, hF);
+    monomial(X, [&](int s_) { return R.psp(s_); }, [&](int s_) { return R.pnu(s_); }, npr, xe, B, gB, DB, hB);
+    const double net = fma(kf, F, -kb * B);
+    const double Dnet = fma(kf, DF, -kb * DB);
+    double Mi = 1.0, DMi = 0.0;
+    if (R.tb()) {
+      Mi = Ctot;
+#pragma unroll
+      for (int e = 0; e < R.neff(); ++e) Mi = fma(m.effv[i][e], X[R.effsp(e)], Mi);
+#pragma unroll
+      for (int j = 0; j < NS; ++j) DMi = fma(1.0 + m.effm1[i][j], xe[j], DMi);
+    }
+    const double MD = Mi + DMi;
+    const double kfp = kf * cache.dk_f(R), kbp = kb * cache.dk_b(R);
+    gT = fma(w, fma(MD, fma(kfp, F, -kbp * B), Mi * fma(kfp, DF, -kbp * DB)), gT);
+#pragma unroll
+    for (int r = 0; r < nre; ++r) {
+      const int j = R.rsp(r);
+      gX[j] = fma(w * kf, fma(MD, gF[r], Mi * hF[r]), gX[j]);
+    }
+#pragma unroll
+    for (int r = 0; r < npr; ++r) {
+      const int j = R.psp(r);
+      gX[j] = fma(-w * kb, fma(MD, gB[r], Mi * hB[r]), gX[j]);
+    }
+    if (R.tb()) {
+      const double v = w * (net + Dnet);
+#pragma unroll
+      for (int j = 0; j < NS; ++j) gX[j] = fma(1.0 + m.effm1[i][j], v, gX[j]);
+    }
+  });
+  gT_out = gT;
+}
+
+// Chain of the chemistry VJP to U*: X(U*) and the implicit dT/dU* of the
+// Newton recovery; out = lam + (d(T, X)/dU*)^T (gT, gX).
+template <int NS>
+__device__ __forceinline__ void chem_vjp_out(const double* u, double T, const MechDev& m, const double* lam, double gT,
+                                             const double* gX, double* out) {
+  constexpr int NSP = NS - 1;
+  constexpr int NV = NS + 3;
+  CellThermo<NS> ct;
+  cell_thermo<NS>(u, T, m, ct);
+  double dT[NV], dp[NV];
+  dT_dp_dU<NS>(u, T, m, ct, dT, dp);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = fma(gT, dT[q], lam[q]);
+  const double gN = gX[NSP] * m.invM[NSP];
+  out[0] += gN;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) out[4 + k] += fma(gX[k], m.invM[k], -gN);
+}
 
 template <int NS, bool FIXED, class Cache>
 __device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double dt, const double* lam, double* out,
@@ -844,64 +971,97 @@ __device__ void chem_vjp_rev(const double* u, double T, const MechDev& m, double
   xe[NSP] = xN;
 
   // ---- reverse: gradient of psi in (T, X) ----
-  double gT = 0.0, gX[NS];
+  double gT, gX[NS];
+  chem_reverse_reactions<NS, FIXED>(m, X, xe, Ctot, mu, dt, cache, gT, gX);
+  chem_vjp_out<NS>(u, T, m, lam, gT, gX, out);
+}
+
+// Chemistry VJP from the factors the segment recompute kept (k_chem_lin):
+// no rates, Jacobian or factorisation are formed again. The transposed solve
+// A^T mu = r runs on the LU factors in elimination order: with
+// A = P_1 L_1 P_2 L_2 ... P_{n-1} L_{n-1} U (P_c the row swap of step c, L_c
+// the multipliers of step c in the rows' positions at that step),
+// mu = P_1 L_1^{-T} ... P_{n-1} L_{n-1}^{-T} U^{-T} r.
+template <int NS, bool FIXED>
+__device__ void chem_vjp_stored(const double* u, double T, const MechDev& m, double dt, const double* lam, double* out,
+                                const double* __restrict__ clin, long long n, long long q) {
+  constexpr int NSP = NS - 1;
+  double X[NS];
+  double rest = u[0];
 #pragma unroll
-  for (int k = 0; k < NS; ++k) gX[k] = 0.0;
-  for_reactions<FIXED>(m, [&](auto R) {
-    const int i = R.idx();
-    const int nre = R.nre(), npr = R.npr();
-    double mi = 0.0;
+  for (int k = 0; k < NSP; ++k) {
+    X[k] = u[4 + k] * m.invM[k];
+    rest -= u[4 + k];
+  }
+  X[NSP] = rest * m.invM[NSP];
+  double Ctot = X[0];
 #pragma unroll
-    for (int r = 0; r < nre; ++r)
-      if (R.rsp(r) < NSP) mi = fma(-R.rnud(r), mu[R.rsp(r)], mi);
+  for (int k = 1; k < NS; ++k) Ctot += X[k];
+  const double rT = rcp(T);
+  const double rT2 = rT * rT;
+  double dG[NS];
 #pragma unroll
-    for (int r = 0; r < npr; ++r)
-      if (R.psp(r) < NSP) mi = fma(R.pnud(r), mu[R.psp(r)], mi);
-    const double w = dt * mi;
-    const double kf = cache.k_f(i), kb = cache.k_b(i);
-    double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
-    monomial(X, [&](int s_) { return R.rsp(s_); }, [&](int s_) { return R.rnu(s_); }, nre, xe, F, gF, DF, hF);
-    monomial(X, [&](int s_) { return R.psp(s_); }, [&](int s_) { return R.pnu(s_); }, npr, xe, B, gB, DB, hB);
-    const double net = fma(kf, F, -kb * B);
-    const double Dnet = fma(kf, DF, -kb * DB);
-    double Mi = 1.0, DMi = 0.0;
-    if (R.tb()) {
-      Mi = Ctot;
+  for (int k = 0; k < NS; ++k) {
+    const double* c = m.gc[k];
+    dG[k] = fma(c[0], rT, fma(-c[5], rT2, fma(T, fma(T, fma(T, 4.0 * c[4], 3.0 * c[3]), 2.0 * c[2]), c[1])));
+  }
+  const long long lu0 = 2LL * m.nr;
+  auto LU = [&](int r, int k) { return __ldg(clin + (lu0 + r * NSP + k) * n + q); };
+  double xe[NS];
+  double xN = 0.0;
 #pragma unroll
-      for (int e = 0; e < R.neff(); ++e) Mi = fma(m.effv[i][e], X[R.effsp(e)], Mi);
+  for (int l = 0; l < NSP; ++l) {
+    xe[l] = __ldg(clin + (lu0 + NSP * NSP + 1 + l) * n + q);
+    xN = fma(-m.mratio[l], xe[l], xN);
+  }
+  xe[NSP] = xN;
+  const unsigned long long pivs = __ldg(reinterpret_cast<const unsigned long long*>(clin) + (lu0 + NSP * NSP) * n + q);
+  // U^T z = r, r_k = M_k lam_{4+k} (the diagonal entries hold 1/U_kk)
+  double mu[NSP];
 #pragma unroll
-      for (int j = 0; j < NS; ++j) DMi = fma(1.0 + m.effm1[i][j], xe[j], DMi);
-    }
-    const double MD = Mi + DMi;
-    const double kfp = kf * cache.dk_f(i), kbp = kb * cache.dk_b(i);
-    gT = fma(w, fma(MD, fma(kfp, F, -kbp * B), Mi * fma(kfp, DF, -kbp * DB)), gT);
+  for (int c = 0; c < NSP; ++c) {
+    double s = m.M[c] * lam[4 + c];
 #pragma unroll
-    for (int r = 0; r < nre; ++r) {
-      const int j = R.rsp(r);
-      gX[j] = fma(w * kf, fma(MD, gF[r], Mi * hF[r]), gX[j]);
-    }
+    for (int k = 0; k < c; ++k) s = fma(-LU(k, c), mu[k], s);
+    mu[c] = s * LU(c, c);
+  }
+  // then, from the last step to the first: L_c^{-T}, then the swap P_c
 #pragma unroll
-    for (int r = 0; r < npr; ++r) {
-      const int j = R.psp(r);
-      gX[j] = fma(-w * kb, fma(MD, gB[r], Mi * hB[r]), gX[j]);
-    }
-    if (R.tb()) {
-      const double v = w * (net + Dnet);
+  for (int c = NSP - 1; c >= 0; --c) {
+    double s = mu[c];
 #pragma unroll
-      for (int j = 0; j < NS; ++j) gX[j] = fma(1.0 + m.effm1[i][j], v, gX[j]);
-    }
-  });
-  // chain to U*: X(U*) and the implicit dT/dU* of the Newton recovery
-  CellThermo<NS> ct;
-  cell_thermo<NS>(u, T, m, ct);
-  double dT[NV], dp[NV];
-  dT_dp_dU<NS>(u, T, m, ct, dT, dp);
+    for (int r = c + 1; r < NSP; ++r) s = fma(-LU(r, c), mu[r], s);
+    const int p = (int)((pivs >> (4 * c)) & 15ull);
+    double v = s;
 #pragma unroll
-  for (int q = 0; q < NV; ++q) out[q] = fma(gT, dT[q], lam[q]);
-  const double gN = gX[NSP] * m.invM[NSP];
-  out[0] += gN;
+    for (int r = c + 1; r < NSP; ++r) v = (p == r) ? mu[r] : v;
 #pragma unroll
-  for (int k = 0; k < NSP; ++k) out[4 + k] += fma(gX[k], m.invM[k], -gN);
+    for (int r = c + 1; r < NSP; ++r) mu[r] = (p == r) ? s : mu[r];
+    mu[c] = v;
+  }
+  const StoredRateCache<NS> cache{clin, n, q, rT, rT2, dG, m};
+  double gT, gX[NS];
+  chem_reverse_reactions<NS, FIXED>(m, X, xe, Ctot, mu, dt, cache, gT, gX);
+  chem_vjp_out<NS>(u, T, m, lam, gT, gX, out);
+}
+
+template <int NS, bool FIXED>
+__global__ void __launch_bounds__(128) k_adj_chem_lin(StateView Sstar, GridDev g, const MechDev* __restrict__ mech,
+                                                      double dt, const double* __restrict__ lam,
+                                                      double* __restrict__ out, const double* __restrict__ clin) {
+  constexpr int NV = NS + 3;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= g.n) return;
+  const long long n = g.n;
+  double u[NV], l[NV], o[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    u[k] = Sstar.plane(k, n)[q];
+    l[k] = lam[(long long)k * n + q];
+  }
+  chem_vjp_stored<NS, FIXED>(u, Sstar.plane(NV, n)[q], *mech, dt, l, o, clin, n, q);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[(long long)k * n + q] = o[k];
 }
 
 template <int NS, bool FIXED>
@@ -1193,7 +1353,18 @@ cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev,
 }
 
 cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, const MechDev* mech, double dt,
-                            const double* lam, double* out, cudaStream_t st) {
+                            const double* lam, double* out, const double* clin, cudaStream_t st) {
+  if (clin) {
+    switch (ns) {
+      case 3: k_adj_chem_lin<3, false><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out, clin); break;
+      case 9:
+        if (g.chem_fixed) k_adj_chem_lin<9, true><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out, clin);
+        else k_adj_chem_lin<9, false><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out, clin);
+        break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   switch (ns) {
     case 3: k_adj_chem_rev<3, false><<<nblk(g.n, 128), 128, 0, st>>>(Sstar, g, mech, dt, lam, out); break;
     case 9:

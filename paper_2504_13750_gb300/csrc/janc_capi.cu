@@ -236,6 +236,7 @@ int janc::create_grid(const janc_grid_desc* d, const janc_mechanism* m, void* wo
   if (g->d.newton_maxit <= 0) g->d.newton_maxit = 50;
   g->ns = m->ns;
   g->nv = m->ns + 3;
+  g->nr = m->nr;
   g->n = (long long)d->nx * d->ny;
   const bool own_halos = so && ((so->halo_lo && !so->halo_ext[0]) || (so->halo_hi && !so->halo_ext[1]));
   g->L = layout_of(d->nx, d->ny, g->nv, own_halos);
@@ -653,13 +654,15 @@ int janc_status(janc_grid_t g, janc_status_info* s) {
 namespace {
 
 struct AdjLayout {
-  size_t state, ckpt, seg, alog, lin, lin_stage, lam, cfx, cfy, small, total;
+  size_t state, ckpt, seg, alog, lin, lin_stage, clin, clin_step, lam, cfx, cfy, small, total;
   int ncp, seglen;
   int nstore;  // segment stores: 2 when segments are recomputed (the next one while the current is reversed)
 };
 
 // mode: JANC_ADJ_STORE_FACES adds to each segment store the face derivatives
-// of its 3 ckpt_every stage states (lin_stage doubles each).
+// of its 3 ckpt_every stage states (lin_stage doubles each) and, with
+// point-implicit chemistry, the chemistry factors of its ckpt_every steps
+// (clin_step doubles each).
 AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every, int mode) {
   AdjLayout L;
   const size_t n = (size_t)g->n;
@@ -673,11 +676,14 @@ AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every, int mode
   L.alog = align256(sizeof(unsigned long long) * 10 * ckpt_every);
   L.lin_stage = mode == JANC_ADJ_STORE_FACES ? face_lin_doubles(nv, g->gd) : 0;
   L.lin = align256(sizeof(double) * L.lin_stage * 3 * (size_t)ckpt_every);
+  L.clin_step = (mode == JANC_ADJ_STORE_FACES && g->d.chemistry == JANC_CHEM_LIE)
+                    ? chem_lin_entries(g->ns, g->nr) * n : 0;
+  L.clin = align256(sizeof(double) * L.clin_step * (size_t)ckpt_every);
   L.lam = 7 * align256(sizeof(double) * (size_t)nv * n);
   L.cfx = align256(sizeof(double) * (size_t)nv * g->gd.ny * (g->gd.nx + 1) * 10);
   L.cfy = align256(sizeof(double) * (size_t)nv * (g->gd.ny + 1) * g->gd.nx * 10);
   L.small = 256 + rhs_vjp_scratch_bytes(g->gd);  // [0] loss, then the RHS-VJP scratch at +256
-  L.total = L.ckpt + L.nstore * (L.seg + L.alog + L.lin) + L.lam + L.cfx + L.cfy + L.small;
+  L.total = L.ckpt + L.nstore * (L.seg + L.alog + L.lin + L.clin) + L.lam + L.cfx + L.cfy + L.small;
   return L;
 }
 
@@ -744,7 +750,8 @@ namespace {
 struct SegStore {
   char* seg;
   unsigned long long* alog;
-  double* lin;  // null in mode JANC_ADJ_RECOMPUTE
+  double* lin;   // null in mode JANC_ADJ_RECOMPUTE
+  double* clin;  // chemistry factors; null in mode JANC_ADJ_RECOMPUTE or without point-implicit chemistry
 };
 
 // Pointers into an adjoint workspace (see adj_layout).
@@ -766,6 +773,7 @@ AdjPtrs adj_ptrs(const janc_grid_s* g, const AdjLayout& L, char* ws) {
     q.store[k].seg = p; p += L.seg;
     q.store[k].alog = (unsigned long long*)p; p += L.alog;
     q.store[k].lin = L.lin_stage ? (double*)p : nullptr; p += L.lin;
+    q.store[k].clin = L.clin_step ? (double*)p : nullptr; p += L.clin;
   }
   if (L.nstore == 1) q.store[1] = q.store[0];
   for (int k = 0; k < 7; ++k) { q.lam[k] = (double*)p; p += lamb; }
@@ -801,6 +809,10 @@ StateView seg_S(const SegStore& q, const AdjLayout& L, int m, int which) {  // w
 // Face derivatives of RK stage s (0: U^n, 1: U1, 2: U2) of step m, or null.
 const double* seg_lin(const SegStore& q, const AdjLayout& L, int m, int s) {
   return q.lin ? q.lin + (size_t)(3 * m + s) * L.lin_stage : nullptr;
+}
+// Chemistry factors of step m, or null.
+double* seg_clin(const SegStore& q, const AdjLayout& L, int m) {
+  return q.clin ? q.clin + (size_t)m * L.clin_step : nullptr;
 }
 
 // `len` fixed-dt steps of the Lie (or explicit-source) order from segment
@@ -839,8 +851,13 @@ cudaError_t adj_segment(janc_grid_s* g, const AdjLayout& L, const SegStore& q, i
                            g->mech, ctl, a, chem ? a + 6 : a + 8, g->status, nullptr, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(seg_S0(q, L, m + 1).base, seg_S(q, L, m, 3).base, L.state, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && chem)
-      e = launch_chem(g->ns, seg_S0(q, L, m + 1), g->gd, g->mech, ctl, a, a + 8, g->status, st);
+    if (e == cudaSuccess && chem) {
+      if (q.clin)
+        e = launch_chem_lin(g->ns, seg_S0(q, L, m + 1), g->gd, g->mech, ctl, a, a + 8, g->status, seg_clin(q, L, m),
+                            st);
+      else
+        e = launch_chem(g->ns, seg_S0(q, L, m + 1), g->gd, g->mech, ctl, a, a + 8, g->status, st);
+    }
     if (e == cudaSuccess && loss) e = launch_loss_endwall(g->ns, seg_S0(q, L, m + 1), g->gd, w_loss, loss, st);
   }
   return e;
@@ -1014,7 +1031,7 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
       if (loss_kind == JANC_LOSS_ENDWALL_P)
         e = launch_seed_endwall(g->ns, segS0(m + 1), g->gd, g->mech, w_loss, lamN, st);
       if (e == cudaSuccess) {
-        if (chem) e = launch_chem_vjp(g->ns, segS(m, 3), g->gd, g->mech, dt, lamN, lamS, st);
+        if (chem) e = launch_chem_vjp(g->ns, segS(m, 3), g->gd, g->mech, dt, lamN, lamS, seg_clin(sq, L, m), st);
         else e = cudaMemcpyAsync(lamS, lamN, sizeof(double) * nvn, cudaMemcpyDeviceToDevice, st);
       }
       // Each stage's RHS VJP takes mu = c dt lam directly and writes the

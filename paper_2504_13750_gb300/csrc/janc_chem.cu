@@ -40,11 +40,18 @@ namespace janc {
 constexpr int CHEM_THREADS = 128;
 
 // One CHEM_THREADS block `blk` of cells; shared by the single-grid and the
-// batched kernels.
-template <int NS, bool FIXED>
+// batched kernels. STORE (the discrete adjoint's segment recompute): also
+// keep, per cell, what the chemistry VJP reuses (chem_lin_entries doubles,
+// entry e of cell q at clin[e * n + q]): k_f and k_b of every reaction
+// (2i, 2i+1), then at 2 nr the LU factors of A = I - dt J'' in elimination
+// order (row r, column k at 2 nr + r (ns-1) + k: the multiplier of row r at
+// elimination step k for r > k, U for r < k, 1/U_kk on the diagonal), the
+// pivot row of every step (4 bits each, one 64-bit word) and the solution x.
+template <int NS, bool FIXED, bool STORE = false>
 __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g, const MechDev* __restrict__ mech,
                                            const StepCtl& ctl, const unsigned long long* __restrict__ alpha_step,
-                                           unsigned long long* alpha_out, int* status, long long blk) {
+                                           unsigned long long* alpha_out, int* status, long long blk,
+                                           double* __restrict__ clin = nullptr) {
   constexpr int NSP = NS - 1;
   constexpr int NV = NS + 3;
   const MechDev& m = *mech;
@@ -114,6 +121,10 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
       for (int q = 0; q < dn; ++q) kb *= rcref;
 #pragma unroll
       for (int q = 0; q < -dn; ++q) kb *= cref;
+      if (STORE) {
+        clin[(2LL * i) * n + idx] = kf;
+        clin[(2LL * i + 1) * n + idx] = kb;
+      }
       // law of mass action and its derivatives with respect to each participant
       double xr[MAX_SIDE], xp[MAX_SIDE];
       double fwd = kf, bwd = kb;
@@ -214,6 +225,8 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
       for (int l = 0; l < NSP; ++l) A[k][l] = fma(-dt, J[k][l], k == l ? 1.0 : 0.0);
     }
     bool singular = false;
+    const long long lu0 = 2LL * m.nr;  // STORE: first LU entry
+    unsigned long long pivs = 0;
 #pragma unroll
     for (int c = 0; c < NSP; ++c) {
       int piv = c;
@@ -248,13 +261,24 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
       }
       if (best == 0ull) singular = true;
       ip[c] = rcp(A[c][c]);
+      if (STORE) pivs |= (unsigned long long)piv << (4 * c);
 #pragma unroll
       for (int r = c + 1; r < NSP; ++r) {
         const double f = A[r][c] * ip[c];
+        if (STORE) clin[(lu0 + r * NSP + c) * n + idx] = f;
 #pragma unroll
         for (int k = c + 1; k < NSP; ++k) A[r][k] = fma(-f, A[c][k], A[r][k]);
         b[r] = fma(-f, b[c], b[r]);
       }
+    }
+    if (STORE) {
+#pragma unroll
+      for (int r = 0; r < NSP; ++r) {
+        clin[(lu0 + r * NSP + r) * n + idx] = ip[r];
+#pragma unroll
+        for (int k = r + 1; k < NSP; ++k) clin[(lu0 + r * NSP + k) * n + idx] = A[r][k];
+      }
+      reinterpret_cast<unsigned long long*>(clin)[(lu0 + NSP * NSP) * n + idx] = pivs;
     }
 #pragma unroll
     for (int r = NSP - 1; r >= 0; --r) {
@@ -262,6 +286,10 @@ __device__ __forceinline__ void chem_block(const StateView& S, const GridDev& g,
 #pragma unroll
       for (int k = r + 1; k < NSP; ++k) s = fma(-A[r][k], b[k], s);
       b[r] = s * ip[r];
+    }
+    if (STORE) {
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) clin[(lu0 + NSP * NSP + 1 + k) * n + idx] = b[k];
     }
     if (singular) {
       st |= ST_SINGULAR;
@@ -289,6 +317,16 @@ __global__ void __launch_bounds__(CHEM_THREADS) k_chem(StateView S, GridDev g, c
                                                        StepCtl ctl, const unsigned long long* __restrict__ alpha_step,
                                                        unsigned long long* alpha_out, int* status) {
   chem_block<NS, FIXED>(S, g, mech, ctl, alpha_step, alpha_out, status, blockIdx.x);
+}
+
+// k_chem that also keeps the chemistry VJP's factors (chem_block, STORE).
+template <int NS, bool FIXED>
+__global__ void __launch_bounds__(CHEM_THREADS) k_chem_lin(StateView S, GridDev g, const MechDev* __restrict__ mech,
+                                                           StepCtl ctl,
+                                                           const unsigned long long* __restrict__ alpha_step,
+                                                           unsigned long long* alpha_out, int* status,
+                                                           double* __restrict__ clin) {
+  chem_block<NS, FIXED, true>(S, g, mech, ctl, alpha_step, alpha_out, status, blockIdx.x, clin);
 }
 
 // Batched chemistry over the flattened (request, block) list: in place on
@@ -357,6 +395,26 @@ cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const Mech
     case 9:
       if (g.chem_fixed) k_chem<9, true><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status);
       else k_chem<9, false><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+size_t chem_lin_entries(int ns, int nr) { return 2 * (size_t)nr + (size_t)(ns - 1) * (ns - 1) + 1 + (ns - 1); }
+
+cudaError_t launch_chem_lin(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
+                            const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,
+                            double* clin, cudaStream_t st) {
+  const int thr = chem_threads(g.n);
+  const unsigned blocks = (unsigned)((g.n + thr - 1) / thr);
+  switch (ns) {
+    case 3: k_chem_lin<3, false><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status, clin); break;
+    case 9:
+      if (g.chem_fixed)
+        k_chem_lin<9, true><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status, clin);
+      else
+        k_chem_lin<9, false><<<blocks, thr, 0, st>>>(S, g, mech, ctl, alpha_step, alpha_out, status, clin);
       break;
     default: return cudaErrorInvalidValue;
   }

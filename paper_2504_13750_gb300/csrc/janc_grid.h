@@ -40,7 +40,7 @@ struct Exchanger {
 
 struct janc_grid_s {
   janc_grid_desc d;
-  int ns, nv;
+  int ns, nv, nr;
   long long n;
   janc::GridDev gd;
   janc::Layout L;

@@ -60,6 +60,14 @@ cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const Mech
                         const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,
                         cudaStream_t st);
 
+// Point-implicit chemistry that also keeps the factors the chemistry VJP
+// reuses: chem_lin_entries(ns, nr) doubles per cell at clin, entry-major
+// (janc_chem.cu).
+cudaError_t launch_chem_lin(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
+                            const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,
+                            double* clin, cudaStream_t st);
+size_t chem_lin_entries(int ns, int nr);
+
 // State set-up kernels (janc_update.cu).
 cudaError_t launch_set_primitive(int ns, const StateView& S, const double* T, const double* p, const double* u,
                                  const double* v, const double* Y, const GridDev& g, const MechDev* mech,
@@ -113,8 +121,10 @@ struct VjpIO {
 cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const VjpIO& io, double* CFx,
                            double* CFy, double* scratch, const GridDev& g, const MechDev* mech, const double* lin,
                            bool fresh, cudaStream_t st);
+// clin: the factors the segment recompute kept (launch_chem_lin), or null to
+// form them again.
 cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, const MechDev* mech, double dt,
-                            const double* lam, double* out, cudaStream_t st);
+                            const double* lam, double* out, const double* clin, cudaStream_t st);
 cudaError_t launch_lincomb(long long count, double* out, double a, const double* x, double b, const double* y,
                            bool accumulate, cudaStream_t st);
 cudaError_t launch_loss_endwall(int ns, const StateView& S, const GridDev& g, double w, double* loss,
