@@ -485,19 +485,26 @@ def run_inverse(janc, iters=15):
     """Inverse-problem leg (the synthetic form of Sec. 6.2): 1000 x 400
     periodic channel, one-step global reaction as an explicit source, loss of
     Eq. 6.6 after 100 fixed-dt steps; Adam iterations per second, each one a
-    forward of 100 steps with the whole trajectory kept on the device (20.5 GB),
-    the reverse sweep over them and the two state set-ups of dU_0/dtheta."""
+    forward of 100 steps with the whole trajectory and its face derivatives
+    kept on the device, the reverse sweep over them and the two state set-ups
+    of dU_0/dtheta."""
     from paper_2504_13750_gb300 import inverse
 
+    import torch
+
     t0 = time.perf_counter()
-    P = inverse.ChannelInverse(nx=1000, ny=400, n_steps=100, dev_steps=400)
+    P = inverse.ChannelInverse(nx=1000, ny=400, n_steps=100, dev_steps=400, store_faces=True)
     setup = time.perf_counter() - t0
     P.loss_and_grad(0.8)  # warm-up
     hist, wall = P.optimize(0.8, iters=iters, lr=0.01)
+    nbytes = P.nbytes
     P.close()
+    del P
+    torch.cuda.empty_cache()
     return {"workload": "channel_1000x400_global_h2o2_g129_explicit_100steps_adam_lr0.01",
             "iterations": iters, "iterations_per_s": iters / wall, "setup_s": setup,
             "theta_start": hist[0][0], "theta_end": hist[-1][0], "loss_start": hist[0][1], "loss_end": hist[-1][1],
+            "adjoint_mode": "store_faces", "workspace_bytes": nbytes,
             "note": "paper (A100, JAX): 1.20 iterations/s on its 1000 x 400 RDC case with 100 steps per iteration"}
 
 

@@ -224,20 +224,26 @@ int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
 #define JANC_LOSS_ENDWALL_P 0  /* L = sum_n dt * mean_j p(nx-1, j) of U^{n+1} */
 #define JANC_LOSS_SEEDED 1     /* L = <seed, U^N> (seed: nv planes) */
 
-/* How the reverse sweep gets the derivatives of the WENO5 reconstructions
- * (Eq. 4.10) of every stage state. JANC_ADJ_RECOMPUTE (the default): the
- * face pass of each RHS vector-Jacobian product recomputes them from the
- * stage state. JANC_ADJ_STORE_FACES: the steps that fill a segment store
- * (the forward's last segment, every recomputed segment) run a face-flux
- * kernel that also stores, per face, variable and split sign, the four
- * partials of the reconstruction with respect to its window's differences,
- * and the reverse face pass only weights them by the cotangent. That moves
- * about two thirds of the reverse face work into the recompute, which runs
- * on its own stream beside the sweep, at a memory cost of
- * 8 nv ((nx+1) ny + (ny+1) nx) doubles per RK stage: 3 ckpt_every stages per
- * segment store (two stores when there is more than one segment). The face
- * fluxes, the trajectory and the loss are the same bit for bit in both
- * modes; the gradients agree to rounding. The mode is read when
+/* How the reverse sweep gets the linearisation of the forward operators.
+ * JANC_ADJ_RECOMPUTE (the default): the face pass of each RHS
+ * vector-Jacobian product recomputes the derivatives of the WENO5
+ * reconstructions (Eq. 4.10) from the stage state, and the chemistry VJP
+ * forms the rates, J'' and the LU factors of Eq. 4.13 again.
+ * JANC_ADJ_STORE_FACES: the steps that fill a segment store (the forward's
+ * last segment, every recomputed segment) run a face-flux kernel that also
+ * stores, per face, variable and split sign, the four partials of the
+ * reconstruction with respect to its window's differences, and (with
+ * JANC_CHEM_LIE) a chemistry kernel that also keeps, per cell, the rate
+ * constants k_f and k_b, the LU factors, the pivots and the solution; the
+ * reverse face pass then only weights the partials by the cotangent, and the
+ * chemistry VJP starts from the kept factors. That moves most of the reverse
+ * work into the recompute, which runs on its own stream beside the sweep,
+ * at a memory cost per step of a segment store of
+ * 3 x 8 nv ((nx+1) ny + (ny+1) nx) doubles (faces) plus
+ * (2 nr + (ns-1)^2 + ns) nx ny doubles (chemistry), ckpt_every steps per
+ * store, two stores when there is more than one segment. The face fluxes,
+ * the trajectory and the loss are the same bit for bit in both modes; the
+ * gradients agree to rounding. The mode is read when
  * janc_adjoint_workspace_bytes and janc_adjoint_forward run; a pending
  * forward keeps the mode it started with. JANC_E_INVALID for another mode.
  * The paper has no counterpart: it is a memory-for-work trade of this
@@ -252,8 +258,8 @@ int janc_set_adjoint_mode(janc_grid_t g, int mode);
  * forward writes the last segment's stages directly, so the reverse
  * recomputes every segment but the last; with ckpt_every >= n_steps the
  * whole trajectory is kept and nothing is recomputed (about
- * (4 n_steps + 2) (nv + 4) nx ny doubles, plus the face derivatives of
- * 3 n_steps stage states in mode JANC_ADJ_STORE_FACES). */
+ * (4 n_steps + 2) (nv + 4) nx ny doubles, plus the face derivatives and
+ * chemistry factors of n_steps steps in mode JANC_ADJ_STORE_FACES). */
 int janc_adjoint_workspace_bytes(janc_grid_t g, int n_steps, int ckpt_every, size_t* bytes);
 
 /* From the grid's current state U^0 (set beforehand), run n_steps fixed-dt

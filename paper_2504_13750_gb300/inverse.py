@@ -38,10 +38,14 @@ def _h2o2_Y(mech, phi):
 
 
 class ChannelInverse:
-    def __init__(self, nx=250, ny=100, Lx=0.10, Ly=0.04, n_steps=100, dev_steps=400, ckpt_every=None, seed=0):
+    def __init__(self, nx=250, ny=100, Lx=0.10, Ly=0.04, n_steps=100, dev_steps=400, ckpt_every=None, seed=0,
+                 store_faces=True):
         """ckpt_every=None keeps the whole trajectory on the device (one
         segment: the reverse sweep recomputes nothing); about
-        (4 n_steps + 2) x 16 x nx x ny x 8 bytes."""
+        (4 n_steps + 2) x 16 x nx x ny x 8 bytes. store_faces also keeps the
+        face derivatives of every stage (janc_set_adjoint_mode
+        ADJ_STORE_FACES): 24 nv ((nx+1) ny + (ny+1) nx) x 8 bytes more per
+        step, and a reverse sweep that does not recompute them."""
         import torch
 
         self.torch = torch
@@ -85,6 +89,7 @@ class ChannelInverse:
         self.set_theta(1.0)
         self.target = self._forward()
         self.tnorm = float(self.torch.linalg.vector_norm(self.target))
+        janc.janc_set_adjoint_mode(self.g.handle, janc.ADJ_STORE_FACES if store_faces else janc.ADJ_RECOMPUTE)
         nbytes = janc.janc_adjoint_workspace_bytes(self.g.handle, n_steps, ckpt_every)
         self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         self.wp = (self.ws.data_ptr() + 255) & ~255
@@ -148,3 +153,4 @@ class ChannelInverse:
 
     def close(self):
         self.g.close()
+        self.ws = None
