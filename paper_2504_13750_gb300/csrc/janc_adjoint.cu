@@ -245,16 +245,18 @@ __global__ void __launch_bounds__(VLINES * NV) k_adj_faces_lin(const double* __r
   long long pstride;
   double* gbase = gf_base(T, GFx, GFy, g, var, lg, pstride);
   EdgeSums E;
+  const double rh4 = 4.0 * rh;  // the store holds a quarter of each partial
 #pragma unroll 4
   for (int t = 0; t < nf; ++t) {
     const double* l = lb + (long long)t * fstride;
     double d[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) d[c] = __ldg(l + c * cstride);
-    const double phi = rh * (ml[t + 1] - ml[t]);
-    E.p0 = fma(phi, d[0], E.p0); E.p1 = fma(phi, d[1], E.p1); E.p2 = fma(phi, d[2], E.p2); E.p3 = fma(phi, d[3], E.p3);
-    E.m0 = fma(phi, d[4], E.m0); E.m1 = fma(phi, d[5], E.m1); E.m2 = fma(phi, d[6], E.m2); E.m3 = fma(phi, d[7], E.m3);
-    E.finish_face(phi, gbase + (long long)t * pstride, pstride);
+    const double dmu = ml[t + 1] - ml[t];
+    const double p4 = rh4 * dmu;
+    E.p0 = fma(p4, d[0], E.p0); E.p1 = fma(p4, d[1], E.p1); E.p2 = fma(p4, d[2], E.p2); E.p3 = fma(p4, d[3], E.p3);
+    E.m0 = fma(p4, d[4], E.m0); E.m1 = fma(p4, d[5], E.m1); E.m2 = fma(p4, d[6], E.m2); E.m3 = fma(p4, d[7], E.m3);
+    E.finish_face(rh * dmu, gbase + (long long)t * pstride, pstride);
   }
   E.flush(gbase + (long long)nf * pstride, pstride);
 }
@@ -367,7 +369,7 @@ __global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, doub
 #pragma unroll
     for (int k = 0; k < NV; ++k) u[k] = S.plane(k, n)[idx];
     const double T = S.plane(NV, n)[idx];
-    const double rrho = 1.0 / u[0];
+    const double rrho = rcp(u[0]);
     const double vx = u[1] * rrho, vy = u[2] * rrho;
     CellThermo<NS> ct;
     cell_thermo<NS>(u, T, *mech, ct);

@@ -122,11 +122,11 @@ __device__ __forceinline__ void weno_face_dD(const Win& w, double scale4, double
   const double e0 = q0s - r;
   const double e1 = fma(-6.0, r, q1);
   const double e2 = fma(-3.0, r, q2h);
-  const double a4s0 = a4 * s0;
-  const double gs0 = a4 * fma(s2, e1, s1 * e2);
-  const double gs1 = fma(a4s0, e2, (a4 * s2) * e0);
-  const double gs2 = fma(a4s0, e1, (a4 * s1) * e0);
-  const double gq0 = a4 * P12, gq1 = a4s0 * s2, gq2 = a4s0 * s1;
+  const double A0 = a4 * s0, A1 = a4 * s1, A2 = a4 * s2;
+  const double gs0 = fma(A2, e1, A1 * e2);
+  const double gs1 = fma(A0, e2, A2 * e0);
+  const double gs2 = fma(A0, e1, A1 * e0);
+  const double gq0 = A1 * s2, gq1 = A0 * s2, gq2 = A0 * s1;
   double hA, hC;
   const double hB = bB * gs1;
   if (!MINUS) { hA = bA * gs0; hC = bC * gs2; } else { hA = bA * gs2; hC = bC * gs0; }
@@ -181,10 +181,10 @@ __device__ __forceinline__ void slide_line2(const double* __restrict__ Ul, const
 }
 
 // slide_line2 that also stores, per face, the derivatives of both
-// reconstructions with respect to their window differences (weno_face_dD):
-// component c (0..3: F+ window D1..D4, 4..7: F- window) of face t at
-// lin[c * cstride + t * fstride]. The face values are slide_line2's bit for
-// bit.
+// reconstructions with respect to their window differences (weno_face_dD),
+// a quarter of each: component c (0..3: F+ window D1..D4, 4..7: F- window)
+// of face t at lin[c * cstride + t * fstride]. The face values are
+// slide_line2's bit for bit.
 __device__ __forceinline__ void slide_line2_lin(const double* __restrict__ Ul, const double* __restrict__ lp,
                                                 const double* __restrict__ lm, const double* __restrict__ pt,
                                                 double eps4, int nf, double* __restrict__ out, long long stride,
@@ -196,8 +196,8 @@ __device__ __forceinline__ void slide_line2_lin(const double* __restrict__ Ul, c
   M.init(Fm(1), Fm(2), Fm(3), Fm(4), Fm(5), eps4);
   for (int t = 0; t < nf; ++t) {
     double rp, rm, g[8];
-    weno_face_dD<false, false>(P, 4.0, &rp, g[0], g[1], g[2], g[3]);
-    weno_face_dD<true, false>(M, 4.0, &rm, g[4], g[5], g[6], g[7]);
+    weno_face_dD<false, false>(P, 1.0, &rp, g[0], g[1], g[2], g[3]);
+    weno_face_dD<true, false>(M, 1.0, &rm, g[4], g[5], g[6], g[7]);
     out[(long long)t * stride] = rp + rm;
     double* l = lin + (long long)t * fstride;
 #pragma unroll
