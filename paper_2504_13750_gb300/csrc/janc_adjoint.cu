@@ -4,12 +4,13 @@
 // checkpoint-and-recompute over the trajectory.
 //
 //  * Right-hand side L(U) (Eq. 4.10-4.11, WENO5, ghost layers): the
-//    vector-Jacobian product reverses the reconstruction formula of both
-//    split signs face by face, in tiles that slide along grid lines like the
-//    forward kernel, and sums the split-flux cotangents per stencil position
-//    (ghost positions included); each cell then reads the sums of its own
-//    position and of the ghost images that copy it, folded back with the
-//    wall flips. The chain through u, v and p(T(U)) uses the implicit
+//    vector-Jacobian product takes the derivative of both split signs'
+//    reconstructions with respect to their window differences face by face
+//    (formed here, or kept by the forward in the face-derivative store), in
+//    tiles that slide along grid lines like the forward kernel, and sums the
+//    split-flux cotangents per stencil position (ghost positions included);
+//    each cell then reads the sums of its own position and of the ghost
+//    images that copy it, folded back with the wall flips. The chain through u, v and p(T(U)) uses the implicit
 //    derivative of the Newton T recovery. The global LF speeds alpha
 //    (Eq. 4.11) receive the summed cotangent, which flows to the cell that
 //    attains the maximum (ties: lowest linear index).
@@ -17,8 +18,9 @@
 //    LU factors of the forward system, then the gradient of a scalar
 //    (sum over reactions of the weighted rate and its derivative along the
 //    solution) in reverse mode, chained through T* = T(U*) (see
-//    chem_vjp_rev).
-//  * TVD-RK3: the Shu-Osher stages reversed.
+//    chem_vjp_rev; chem_vjp_stored starts from the factors the forward kept).
+//  * TVD-RK3: the Shu-Osher stages reversed; each stage's RHS VJP writes the
+//    stage's linear combinations of the cotangents itself.
 // No atomics touch state cotangents: every cell gathers its own. (The
 // per-position split-flux sums take at most two atomic additions per slot
 // onto zero, whose result does not depend on their order.)
