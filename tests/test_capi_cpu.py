@@ -184,3 +184,12 @@ def test_fixed_structure_header_is_generated_from_the_mechanism():
     for i, r in enumerate(rx):
         assert r["nuf"] == list(m["nuf"][i]) and r["nub"] == list(m["nub"][i]) and r["tb"] == int(m["tb"][i])
         assert r["eff_ne1"] == [k for k in range(m["ns"]) if m["tb"][i] and m["eff"][i][k] != 1.0]
+
+
+def test_adjoint_mode_refuses_a_null_grid(libjanc):
+    from paper_2504_13750_gb300 import janc
+
+    for mode in (janc.ADJ_RECOMPUTE, janc.ADJ_STORE_FACES, 7):
+        with pytest.raises(janc.JancError) as e:
+            janc.janc_set_adjoint_mode(None, mode)
+        assert e.value.rc == -1

@@ -415,3 +415,28 @@ def test_checkpoint_interval_leaves_trajectory_and_gradient_unchanged(J, chem):
             s = max(np.max(np.abs(grads[0][k])), 1e-300)
             assert np.max(np.abs(gr[k] - grads[0][k])) <= tol * s, (i, k)
     g.close()
+
+
+def test_store_mode_workspace_matches_the_documented_size(J):
+    """janc_adjoint_workspace_bytes grows in mode ADJ_STORE_FACES by the size
+    include/janc.h states: per step of a segment store 3 x 8 nv
+    ((nx+1) ny + (ny+1) nx) doubles of face derivatives and
+    (2 nr + (ns-1)^2 + ns) nx ny doubles of chemistry factors, ckpt_every steps
+    per store, two stores with more than one segment (each part 256-byte
+    aligned). An unknown mode is refused and leaves the mode as it was."""
+    st, U = _state(40, 24, 41)
+    g = J.Grid.from_grid_dict(H2AIR, st["grid"])
+    nx, ny, nv, ns, nr = 40, 24, 12, 9, H2AIR["nr"]
+    al = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    for n_steps, ck, nstore in ((30, 7, 2), (12, 12, 1)):
+        _mode(J, g, False)
+        base = J.janc_adjoint_workspace_bytes(g.handle, n_steps, ck)
+        _mode(J, g, True)
+        store = J.janc_adjoint_workspace_bytes(g.handle, n_steps, ck)
+        faces = al(8 * 3 * ck * 8 * nv * ((nx + 1) * ny + (ny + 1) * nx))
+        chem = al(8 * ck * (2 * nr + (ns - 1) ** 2 + ns) * nx * ny)
+        assert store - base == nstore * (faces + chem), (n_steps, ck, store - base)
+        with pytest.raises(J.JancError):
+            J.janc_set_adjoint_mode(g.handle, 2)
+        assert J.janc_adjoint_workspace_bytes(g.handle, n_steps, ck) == store
+    g.close()
