@@ -7,6 +7,9 @@ backward receives dL/dU^N from whatever loss follows and runs
 janc_adjoint_reverse, so any torch expression of U^N is differentiable with
 respect to U^0. One rollout may be pending per grid at a time.
 
+Both take ``store_faces`` to choose the adjoint mode (the forward's
+linearisation kept in the segment stores, or recomputed in the reverse).
+
 ``trajectory_loss(grid, T0, p, u, v, Y, n_steps, dt, ckpt_every)`` loads the
 initial state from primitive fields (device tensors) with the temperature
 field T0 as the differentiable input, runs n fixed-dt steps and returns the
@@ -47,7 +50,16 @@ class JancTrajectory(torch.autograd.Function):
         return g * dLdT, None, None, None, None, None, None, None, None
 
 
-def trajectory_loss(grid, T0, p, u, v, Y, n_steps, dt, ckpt_every=50):
+def _set_mode(grid, store_faces):
+    if store_faces is not None:
+        janc.janc_set_adjoint_mode(grid.handle, janc.ADJ_STORE_FACES if store_faces else janc.ADJ_RECOMPUTE)
+
+
+def trajectory_loss(grid, T0, p, u, v, Y, n_steps, dt, ckpt_every=50, store_faces=None):
+    """store_faces: True / False sets the grid's adjoint mode
+    (janc_set_adjoint_mode: keep the forward's linearisation in the segment
+    stores, or recompute it); None leaves the grid's mode as it is."""
+    _set_mode(grid, store_faces)
     return JancTrajectory.apply(T0, grid, p, u, v, Y, n_steps, dt, ckpt_every)
 
 
@@ -70,5 +82,7 @@ class JancRollout(torch.autograd.Function):
         return gU0, None, None, None, None
 
 
-def rollout(grid, U0, n_steps, dt, ckpt_every=50):
+def rollout(grid, U0, n_steps, dt, ckpt_every=50, store_faces=None):
+    """store_faces: as for trajectory_loss."""
+    _set_mode(grid, store_faces)
     return JancRollout.apply(U0, grid, n_steps, dt, ckpt_every)

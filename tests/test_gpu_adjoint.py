@@ -170,7 +170,7 @@ def test_rollout_autograd_and_split_adjoint(J):
     dt, n = 1e-8, 9
     g = J.Grid.from_grid_dict(H2AIR, st["grid"])
     U0 = torch.from_numpy(np.ascontiguousarray(U)).cuda().requires_grad_(True)
-    UN = rollout(g, U0, n, dt, 4)
+    UN = rollout(g, U0, n, dt, 4, store_faces=True)  # the store mode through autograd
     w = torch.from_numpy(np.random.default_rng(22).normal(size=U.shape)).cuda()
     scale = UN.detach().abs().amax(dim=(1, 2), keepdim=True).clamp_min(1e-12)
     L = torch.sum(w * (UN / scale) ** 2)
