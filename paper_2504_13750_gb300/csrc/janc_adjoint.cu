@@ -343,16 +343,12 @@ __device__ __forceinline__ void argmax_merge(unsigned long long& m, int& i, unsi
   if (m2 > m || (m2 == m && i2 < i)) { m = m2; i = i2; }
 }
 
-// Cell pass of the RHS VJP: blocks of CELL_BX x CELL_BY cells. At the 166
-// registers the 9-species pass needs, three such blocks fit an SM (one of 256
-// threads would), and a 512 x 64 grid spreads over every SM. Besides the gathered
+// Cell pass of the RHS VJP (256 threads per block). Besides the gathered
 // cotangents it leaves, per block, the block sums of the alpha cotangents
 // (atomically added) and the arg-max of |u|+c and |v|+c over its cells in
 // part_mx / part_id [2 * block + direction].
-constexpr int CELL_BX = 32, CELL_BY = 4, CELL_THREADS = CELL_BX * CELL_BY;
-
 template <int NS>
-__global__ void __launch_bounds__(CELL_THREADS) k_adj_cells(StateView S, const double* __restrict__ alpha2, double* __restrict__ GFx,
+__global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, double* __restrict__ GFx,
                             double* __restrict__ GFy, VjpIO io, double* adj_alpha, GridDev g,
                             const MechDev* __restrict__ mech, unsigned long long* __restrict__ part_mx,
                             int* __restrict__ part_id) {
@@ -404,9 +400,9 @@ __global__ void __launch_bounds__(CELL_THREADS) k_adj_cells(StateView S, const d
     cid = (int)idx;
   }
   // block sums of the alpha cotangents and block arg-max of the speeds
-  __shared__ double rx[CELL_THREADS], ry[CELL_THREADS];
-  __shared__ unsigned long long mx[2][CELL_THREADS];
-  __shared__ int id[2][CELL_THREADS];
+  __shared__ double rx[256], ry[256];
+  __shared__ unsigned long long mx[2][256];
+  __shared__ int id[2][256];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   rx[tid] = ax;
   ry[tid] = ay;
@@ -1299,8 +1295,8 @@ __global__ void k_prim_T_vjp(const double* __restrict__ T, const double* __restr
 // ---------------------------------------------------------------------------
 static unsigned nblk(long long count, int thr) { return (unsigned)((count + thr - 1) / thr); }
 
-// Cell-pass blocks (CELL_BX x CELL_BY cells).
-static int adj_cell_blocks(const GridDev& g) { return ((g.nx + CELL_BX - 1) / CELL_BX) * ((g.ny + CELL_BY - 1) / CELL_BY); }
+// Cell-pass blocks of 32 x 8 cells.
+static int adj_cell_blocks(const GridDev& g) { return ((g.nx + 31) / 32) * ((g.ny + 7) / 8); }
 
 size_t rhs_vjp_scratch_bytes(const GridDev& g) {
   return 256 + (((size_t)adj_cell_blocks(g) * 2 * (sizeof(unsigned long long) + sizeof(int)) + 255) & ~(size_t)255);
@@ -1343,7 +1339,7 @@ static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const
     if (lin) k_adj_faces_lin<NV, 8><<<total, VLINES * NV, 0, st>>>(lin, mu, ms, CFx, CFy, g, nbx, ntx_x, ntx_y);
     else k_adj_faces<NV, 8><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, ms, CFx, CFy, g, nbx, ntx_x, ntx_y);
   }
-  dim3 blk(CELL_BX, CELL_BY), grd((g.nx + CELL_BX - 1) / CELL_BX, (g.ny + CELL_BY - 1) / CELL_BY);
+  dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
   k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, io, adj_alpha, g, mech, part_mx, part_id);
   k_adj_alpha<NS><<<1, 256, 0, st>>>(S, g, mech, part_mx, part_id, nb, adj_alpha, io.a);
   return cudaGetLastError();
