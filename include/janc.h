@@ -234,14 +234,16 @@ int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
  * stores, per face, variable and split sign, the four partials of the
  * reconstruction with respect to its window's differences, and (with
  * JANC_CHEM_LIE) a chemistry kernel that also keeps, per cell, the rate
- * constants k_f and k_b, the LU factors, the pivots and the solution; the
- * reverse face pass then only weights the partials by the cotangent, and the
- * chemistry VJP starts from the kept factors. That moves most of the reverse
- * work into the recompute, which runs on its own stream beside the sweep,
- * at a memory cost per step of a segment store of
- * 3 x 8 nv ((nx+1) ny + (ny+1) nx) doubles (faces) plus
- * (2 nr + (ns-1)^2 + ns) nx ny doubles (chemistry), ckpt_every steps per
- * store, two stores when there is more than one segment. The face fluxes,
+ * constants k_f and k_b, the LU factors, the pivots and the solution, or
+ * (with JANC_CHEM_EXPLICIT) stage updates that keep k_f and k_b of the
+ * explicit source at each stage input; the reverse face pass then only
+ * weights the partials by the cotangent, and the chemistry or source VJP
+ * starts from the kept values. That moves most of the reverse work into the
+ * recompute, which runs on its own stream beside the sweep, at a memory cost
+ * per step of a segment store of 3 x 8 nv ((nx+1) ny + (ny+1) nx) doubles
+ * (faces) plus (2 nr + (ns-1)^2 + ns) nx ny doubles (JANC_CHEM_LIE) or
+ * 6 nr nx ny doubles (JANC_CHEM_EXPLICIT), ckpt_every steps per store, two
+ * stores when there is more than one segment. The face fluxes,
  * the trajectory and the loss are the same bit for bit in both modes; the
  * gradients agree to rounding. The mode is read when
  * janc_adjoint_workspace_bytes and janc_adjoint_forward run; a pending

@@ -1101,7 +1101,7 @@ __global__ void __launch_bounds__(128) k_adj_chem_rev(StateView Sstar, GridDev g
 template <int NS>
 __global__ void __launch_bounds__(128) k_src_vjp(StateView S, GridDev g, const MechDev* __restrict__ mech,
                                                  const double* __restrict__ lam, double mu_scale,
-                                                 double* __restrict__ nu) {
+                                                 double* __restrict__ nu, const double* __restrict__ keep) {
   constexpr int NSP = NS - 1;
   constexpr int NV = NS + 3;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1125,15 +1125,18 @@ __global__ void __launch_bounds__(128) k_src_vjp(StateView S, GridDev g, const M
   double Ctot = X[0];
 #pragma unroll
   for (int k = 1; k < NS; ++k) Ctot += X[k];
-  const double lnT = log(T);
   const double rT = rcp(T);
   const double rT2 = rT * rT;
+  // with `keep` the forward's k_f and k_b are read back and exp(G_k) is not needed
+  const double lnT = keep ? 0.0 : log(T);
   double eG[NS], reG[NS], dG[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     const double* c = m.gc[k];
-    eG[k] = exp_t(fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6]))));
-    reG[k] = rcp(eG[k]);
+    if (!keep) {
+      eG[k] = exp_t(fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6]))));
+      reG[k] = rcp(eG[k]);
+    }
     dG[k] = fma(c[0], rT, fma(-c[5], rT2, fma(T, fma(T, fma(T, 4.0 * c[4], 3.0 * c[3]), 2.0 * c[2]), c[1])));
   }
   const double cref = (P_REF / RU) * rT;
@@ -1151,17 +1154,27 @@ __global__ void __launch_bounds__(128) k_src_vjp(StateView S, GridDev g, const M
       if (m.rsp[i][r] < NSP) mi = fma(-m.rnud[i][r], w[m.rsp[i][r]], mi);
     for (int r = 0; r < npr; ++r)
       if (m.psp[i][r] < NSP) mi = fma(m.pnud[i][r], w[m.psp[i][r]], mi);
-    const double kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
     const double dlkf = fma(m.b[i], rT, m.EaR[i] * rT2);
-    double kb = kf, dlkb = dlkf;
+    double kf, kb, dlkb = dlkf;
     for (int r = 0; r < nre; ++r)
-      for (int qq = 0; qq < m.rnu[i][r]; ++qq) { kb *= eG[m.rsp[i][r]]; dlkb += dG[m.rsp[i][r]]; }
+      for (int qq = 0; qq < m.rnu[i][r]; ++qq) dlkb += dG[m.rsp[i][r]];
     for (int r = 0; r < npr; ++r)
-      for (int qq = 0; qq < m.pnu[i][r]; ++qq) { kb *= reG[m.psp[i][r]]; dlkb -= dG[m.psp[i][r]]; }
+      for (int qq = 0; qq < m.pnu[i][r]; ++qq) dlkb -= dG[m.psp[i][r]];
     const int dn = m.dnu[i];
-    for (int qq = 0; qq < dn; ++qq) kb *= rcref;
-    for (int qq = 0; qq < -dn; ++qq) kb *= cref;
     dlkb = fma((double)dn, rT, dlkb);
+    if (keep) {
+      kf = __ldg(keep + (2LL * i) * n + q);
+      kb = __ldg(keep + (2LL * i + 1) * n + q);
+    } else {
+      kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
+      kb = kf;
+      for (int r = 0; r < nre; ++r)
+        for (int qq = 0; qq < m.rnu[i][r]; ++qq) kb *= eG[m.rsp[i][r]];
+      for (int r = 0; r < npr; ++r)
+        for (int qq = 0; qq < m.pnu[i][r]; ++qq) kb *= reG[m.psp[i][r]];
+      for (int qq = 0; qq < dn; ++qq) kb *= rcref;
+      for (int qq = 0; qq < -dn; ++qq) kb *= cref;
+    }
     double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
     monomial(X, [&](int s_) { return m.rsp[i][s_]; }, [&](int s_) { return m.rnu[i][s_]; }, nre, zero, F, gF, DF, hF);
     monomial(X, [&](int s_) { return m.psp[i][s_]; }, [&](int s_) { return m.pnu[i][s_]; }, npr, zero, B, gB, DB, hB);
@@ -1389,10 +1402,10 @@ cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, co
 }
 
 cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const VjpIO& io,
-                              cudaStream_t st) {
+                              const double* keep, cudaStream_t st) {
   switch (ns) {
-    case 3: k_src_vjp<3><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, io.lam, io.mu_scale, io.a); break;
-    case 9: k_src_vjp<9><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, io.lam, io.mu_scale, io.a); break;
+    case 3: k_src_vjp<3><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, io.lam, io.mu_scale, io.a, keep); break;
+    case 9: k_src_vjp<9><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, io.lam, io.mu_scale, io.a, keep); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -660,9 +660,9 @@ struct AdjLayout {
 };
 
 // mode: JANC_ADJ_STORE_FACES adds to each segment store the face derivatives
-// of its 3 ckpt_every stage states (lin_stage doubles each) and, with
-// point-implicit chemistry, the chemistry factors of its ckpt_every steps
-// (clin_step doubles each).
+// of its 3 ckpt_every stage states (lin_stage doubles each) and, per step
+// (clin_step doubles), the chemistry factors of point-implicit chemistry or
+// the rate constants of the explicit source at its three stage inputs.
 AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every, int mode) {
   AdjLayout L;
   const size_t n = (size_t)g->n;
@@ -676,8 +676,10 @@ AdjLayout adj_layout(const janc_grid_s* g, int n_steps, int ckpt_every, int mode
   L.alog = align256(sizeof(unsigned long long) * 10 * ckpt_every);
   L.lin_stage = mode == JANC_ADJ_STORE_FACES ? face_lin_doubles(nv, g->gd) : 0;
   L.lin = align256(sizeof(double) * L.lin_stage * 3 * (size_t)ckpt_every);
-  L.clin_step = (mode == JANC_ADJ_STORE_FACES && g->d.chemistry == JANC_CHEM_LIE)
-                    ? chem_lin_entries(g->ns, g->nr) * n : 0;
+  L.clin_step = 0;
+  if (mode == JANC_ADJ_STORE_FACES && g->d.chemistry == JANC_CHEM_LIE) L.clin_step = chem_lin_entries(g->ns, g->nr) * n;
+  if (mode == JANC_ADJ_STORE_FACES && g->d.chemistry == JANC_CHEM_EXPLICIT && g->ns > 1)
+    L.clin_step = 3 * 2 * (size_t)g->nr * n;
   L.clin = align256(sizeof(double) * L.clin_step * (size_t)ckpt_every);
   L.lam = 7 * align256(sizeof(double) * (size_t)nv * n);
   L.cfx = align256(sizeof(double) * (size_t)nv * g->gd.ny * (g->gd.nx + 1) * 10);
@@ -814,6 +816,10 @@ const double* seg_lin(const SegStore& q, const AdjLayout& L, int m, int s) {
 double* seg_clin(const SegStore& q, const AdjLayout& L, int m) {
   return q.clin ? q.clin + (size_t)m * L.clin_step : nullptr;
 }
+// Explicit source: the rate constants at the input of RK stage s (0..2) of step m, or null.
+double* seg_src(const SegStore& q, const AdjLayout& L, int m, int s) {
+  return q.clin ? q.clin + (size_t)m * L.clin_step + (size_t)s * (L.clin_step / 3) : nullptr;
+}
 
 // `len` fixed-dt steps of the Lie (or explicit-source) order from segment
 // slot 0, whose alpha pair is in alog[0..1], keeping every stage state in
@@ -827,7 +833,10 @@ cudaError_t adj_segment(janc_grid_s* g, const AdjLayout& L, const SegStore& q, i
                         double* clock, double* loss, double w_loss, cudaStream_t st) {
   const int nv = g->nv;
   const bool chem = g->d.chemistry == JANC_CHEM_LIE;
+  const bool src = g->d.chemistry == JANC_CHEM_EXPLICIT;
   unsigned long long* alog = q.alog;
+  // the explicit source's rate constants at stage s's input, when the store keeps them
+  auto keep = [&](int m, int s) { return src ? seg_src(q, L, m, s) : nullptr; };
   // the face fluxes of stage s of step m, with its derivatives when the store keeps them
   auto flux = [&](const StateView& Sin, const unsigned long long* a, int m, int s) {
     if (!q.lin) return launch_face_flux(nv, Sin, a, g->Fx, g->Gy, g->gd, st);
@@ -840,15 +849,15 @@ cudaError_t adj_segment(janc_grid_s* g, const AdjLayout& L, const SegStore& q, i
     if (e == cudaSuccess) e = flux(seg_S0(q, L, m), a, m, 0);
     if (e == cudaSuccess)
       e = launch_rk_update(g->ns, 1, seg_S0(q, L, m), seg_S0(q, L, m), seg_S(q, L, m, 1), g->Fx, g->Gy, g->gd,
-                           g->mech, ctl, a, a + 2, g->status, clock, st);
+                           g->mech, ctl, a, a + 2, g->status, clock, st, keep(m, 0));
     if (e == cudaSuccess) e = flux(seg_S(q, L, m, 1), a + 2, m, 1);
     if (e == cudaSuccess)
       e = launch_rk_update(g->ns, 2, seg_S(q, L, m, 1), seg_S0(q, L, m), seg_S(q, L, m, 2), g->Fx, g->Gy, g->gd,
-                           g->mech, ctl, a, a + 4, g->status, nullptr, st);
+                           g->mech, ctl, a, a + 4, g->status, nullptr, st, keep(m, 1));
     if (e == cudaSuccess) e = flux(seg_S(q, L, m, 2), a + 4, m, 2);
     if (e == cudaSuccess)
       e = launch_rk_update(g->ns, 3, seg_S(q, L, m, 2), seg_S0(q, L, m), seg_S(q, L, m, 3), g->Fx, g->Gy, g->gd,
-                           g->mech, ctl, a, chem ? a + 6 : a + 8, g->status, nullptr, st);
+                           g->mech, ctl, a, chem ? a + 6 : a + 8, g->status, nullptr, st, keep(m, 2));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(seg_S0(q, L, m + 1).base, seg_S(q, L, m, 3).base, L.state, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && chem) {
@@ -1042,19 +1051,22 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
       if (e == cudaSuccess)
         e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), io3, cfx, cfy, small + 32, g->gd, g->mech,
                            seg_lin(sq, L, m, 2), false, st);
-      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, io3, st);
+      if (e == cudaSuccess && src)
+        e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, io3, seg_src(sq, L, m, 2), st);
       // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1)): lam1 = lam2 / 4 + L^T mu, lam0 += 3/4 lam2
       const VjpIO io2{lam2, 0.25 * dt, lam1, lam2, 0.25, 0, lam0, lam2, 0.75, 1};
       if (e == cudaSuccess)
         e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), io2, cfx, cfy, small + 32, g->gd, g->mech,
                            seg_lin(sq, L, m, 1), false, st);
-      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, io2, st);
+      if (e == cudaSuccess && src)
+        e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, io2, seg_src(sq, L, m, 1), st);
       // stage 1: U1 = U^n + dt L(U^n): lam0 += lam1 + L^T mu
       const VjpIO io1{lam1, dt, lam0, lam1, 1.0, 1, nullptr, nullptr, 0.0, 0};
       if (e == cudaSuccess)
         e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, io1, cfx, cfy, small + 32, g->gd, g->mech,
                            seg_lin(sq, L, m, 0), false, st);
-      if (e == cudaSuccess && src) e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, io1, st);
+      if (e == cudaSuccess && src)
+        e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, io1, seg_src(sq, L, m, 0), st);
       std::swap(lamN, lam0);
     }
     // segment c's store is free once its reverse is done: refill it with c - 2

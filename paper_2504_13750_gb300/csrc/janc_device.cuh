@@ -234,7 +234,11 @@ __device__ __forceinline__ double sound_speed(const double* u, double t, const M
 // Molar production rates (Eq. 4.7-4.9) of the carried species k < ns - 1 at
 // (T, X(u)), for the explicit source-term form of the step.
 template <int NS>
-__device__ __forceinline__ void carried_rates(const double* u, double T, const MechDev& m, double* wd) {
+// keep (the discrete adjoint's store): k_f and k_b of reaction i go to
+// keep[2i n + idx] and keep[(2i+1) n + idx].
+__device__ __forceinline__ void carried_rates(const double* u, double T, const MechDev& m, double* wd,
+                                              double* __restrict__ keep = nullptr, long long n = 0,
+                                              long long idx = 0) {
   constexpr int NSP = NS - 1;
   double X[NS];
   double rest = u[0];
@@ -269,6 +273,10 @@ __device__ __forceinline__ void carried_rates(const double* u, double T, const M
       for (int q = 0; q < m.pnu[i][r]; ++q) kb *= reG[m.psp[i][r]];
     for (int q = 0; q < m.dnu[i]; ++q) kb *= rcref;
     for (int q = 0; q < -m.dnu[i]; ++q) kb *= cref;
+    if (keep) {
+      keep[(2LL * i) * n + idx] = kf;
+      keep[(2LL * i + 1) * n + idx] = kb;
+    }
     double fwd = kf, bwd = kb;
     for (int r = 0; r < nre; ++r)
       for (int q = 0; q < m.rnu[i][r]; ++q) fwd *= X[m.rsp[i][r]];

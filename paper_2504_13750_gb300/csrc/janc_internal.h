@@ -43,17 +43,21 @@ size_t face_lin_doubles(int nv, const GridDev& g);
 // RK3 stage `stage` (1..3): Sout = combination of S0 and Sin + dt L(Sin), then
 // Newton T warm-started from Sin's T, aux planes, and the alpha max of Sout
 // into alpha_out (janc_update.cu). alpha_step holds the step's starting alpha.
+// src_keep (explicit source only, may be null): k_f and k_b of every reaction
+// at the stage input, 2 nr doubles per cell entry-major (carried_rates).
 cudaError_t launch_rk_update(int ns, int stage, const StateView& Sin, const StateView& S0, const StateView& Sout,
                              const double* Fx, const double* Gy, const GridDev& g, const MechDev* mech,
                              const StepCtl& ctl, const unsigned long long* alpha_step, unsigned long long* alpha_out,
-                             int* status, double* clock2, cudaStream_t st);
+                             int* status, double* clock2, cudaStream_t st, double* src_keep = nullptr);
 
 // io.a += (dS/dU)^T mu, mu = io.mu_scale io.lam, for the explicit source S(U)
 // (production rates of the carried species at the stored T) at state S
 // (janc_adjoint.cu).
+// keep: the stage's rate constants kept by launch_rk_update, or null to form
+// them again.
 struct VjpIO;
 cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const VjpIO& io,
-                              cudaStream_t st);
+                              const double* keep, cudaStream_t st);
 
 // Point-implicit chemistry in place on S (janc_chem.cu).
 cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,

@@ -33,7 +33,7 @@ __device__ __forceinline__ void rk_update_block(const StateView& Sin, const Stat
                                                 const GridDev& g, const MechDev* __restrict__ mech,
                                                 const StepCtl& ctl, const unsigned long long* __restrict__ alpha_step,
                                                 unsigned long long* alpha_out, int* status, double* clock2, int bx,
-                                                int by) {
+                                                int by, double* __restrict__ src_keep = nullptr) {
   constexpr int NV = NS + 3;
   const int i = bx * blockDim.x + threadIdx.x;
   const int j = by * blockDim.y + threadIdx.y;
@@ -55,7 +55,7 @@ __device__ __forceinline__ void rk_update_block(const StateView& Sin, const Stat
       double uin[NV];
 #pragma unroll
       for (int k = 0; k < NV; ++k) uin[k] = Sin.plane(k, n)[idx];
-      carried_rates<NS>(uin, Sin.plane(NV, n)[idx], *mech, src);
+      carried_rates<NS>(uin, Sin.plane(NV, n)[idx], *mech, src, src_keep, n, idx);
 #pragma unroll
       for (int k = 0; k < NS - 1; ++k) src[k] *= mech->M[k];
     }
@@ -91,9 +91,9 @@ __global__ void __launch_bounds__(UPD_BX* UPD_BY) k_rk_update(StateView Sin, Sta
                                                               const MechDev* __restrict__ mech, StepCtl ctl,
                                                               const unsigned long long* __restrict__ alpha_step,
                                                               unsigned long long* alpha_out, int* status,
-                                                              double* clock2) {
+                                                              double* clock2, double* src_keep) {
   rk_update_block<NS, STAGE, SRC>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, alpha_step, alpha_out, status, clock2,
-                                  blockIdx.x, blockIdx.y);
+                                  blockIdx.x, blockIdx.y, src_keep);
 }
 
 // Batched stage update over the flattened (request, block) list. Stage s
@@ -170,7 +170,7 @@ template <int NS>
 static cudaError_t launch_rk_update_t(int stage, const StateView& Sin, const StateView& S0, const StateView& Sout,
                                       const double* Fx, const double* Gy, const GridDev& g, const MechDev* mech,
                                       const StepCtl& ctl, const unsigned long long* a_step, unsigned long long* a_out,
-                                      int* status, double* clock2, cudaStream_t st) {
+                                      int* status, double* clock2, cudaStream_t st, double* keep) {
   // UPD_BX x UPD_BY blocks while that gives at least 4 blocks per SM; on
   // smaller grids shorter blocks (UPD_BX x 4, 2, 1) spread the cells over
   // all SMs.
@@ -181,18 +181,18 @@ static cudaError_t launch_rk_update_t(int stage, const StateView& Sin, const Sta
   dim3 blk(UPD_BX, by), grd((unsigned)bxs, (g.ny + by - 1) / by);
   if (ctl.source && NS > 1) {
     if (stage == 1)
-      k_rk_update<NS, 1, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+      k_rk_update<NS, 1, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, keep);
     else if (stage == 2)
-      k_rk_update<NS, 2, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+      k_rk_update<NS, 2, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, keep);
     else
-      k_rk_update<NS, 3, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+      k_rk_update<NS, 3, true><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, keep);
   } else {
     if (stage == 1)
-      k_rk_update<NS, 1, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+      k_rk_update<NS, 1, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, keep);
     else if (stage == 2)
-      k_rk_update<NS, 2, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+      k_rk_update<NS, 2, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, keep);
     else
-      k_rk_update<NS, 3, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2);
+      k_rk_update<NS, 3, false><<<grd, blk, 0, st>>>(Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, keep);
   }
   return cudaGetLastError();
 }
@@ -200,11 +200,14 @@ static cudaError_t launch_rk_update_t(int stage, const StateView& Sin, const Sta
 cudaError_t launch_rk_update(int ns, int stage, const StateView& Sin, const StateView& S0, const StateView& Sout,
                              const double* Fx, const double* Gy, const GridDev& g, const MechDev* mech,
                              const StepCtl& ctl, const unsigned long long* a_step, unsigned long long* a_out,
-                             int* status, double* clock2, cudaStream_t st) {
+                             int* status, double* clock2, cudaStream_t st, double* src_keep) {
   switch (ns) {
-    case 1: return launch_rk_update_t<1>(stage, Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, st);
-    case 3: return launch_rk_update_t<3>(stage, Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, st);
-    case 9: return launch_rk_update_t<9>(stage, Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, st);
+    case 1: return launch_rk_update_t<1>(stage, Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, st,
+                                         src_keep);
+    case 3: return launch_rk_update_t<3>(stage, Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, st,
+                                         src_keep);
+    case 9: return launch_rk_update_t<9>(stage, Sin, S0, Sout, Fx, Gy, g, mech, ctl, a_step, a_out, status, clock2, st,
+                                         src_keep);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -83,6 +83,11 @@ class ChannelInverse:
         self.v0 = U[2] / rho
         self.Y0 = Yall
         self.fresh = Yall[-1] < 1e-3
+        # the snapshot's fields stay on the device; only Y(theta) changes
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+        self._dT0, self._dp0, self._du0, self._dv0 = (dev(a) for a in (self.T0, self.p0, self.u0, self.v0))
+        self._dY0 = dev(Yall)
+        self._dfresh = dev(self.fresh)
         # fixed dt: the CFL dt of the snapshot
         self.set_theta(1.0)
         _, self.dt = self.g.step(1, cfl=0.5, want_time=True)
@@ -95,13 +100,12 @@ class ChannelInverse:
         self.wp = (self.ws.data_ptr() + 255) & ~255
         self.nbytes = nbytes
 
-    def _Y(self, theta):
-        Y = self.Y0.copy()
-        Y[:, self.fresh] = _h2o2_Y(self.mech, theta)[:, None]
-        return np.ascontiguousarray(Y)
-
     def set_theta(self, theta):
-        self.g.set_primitive(self.T0, self.p0, self.u0, self.v0, self._Y(theta))
+        """Loads U_0(theta): the snapshot with the fresh-gas cells at
+        equivalence ratio theta (fields on the device, no host copies)."""
+        Yth = self.torch.from_numpy(_h2o2_Y(self.mech, theta)).cuda()
+        Y = self.torch.where(self._dfresh[None], Yth[:, None, None], self._dY0).contiguous()
+        janc.janc_set_state_primitive(self.g.handle, self._dT0, self._dp0, self._du0, self._dv0, Y)
 
     def state(self):
         U = self.torch.empty((self.nv, self.ny, self.nx), dtype=self.torch.float64, device="cuda")

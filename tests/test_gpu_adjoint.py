@@ -440,3 +440,16 @@ def test_store_mode_workspace_matches_the_documented_size(J):
             J.janc_set_adjoint_mode(g.handle, 2)
         assert J.janc_adjoint_workspace_bytes(g.handle, n_steps, ck) == store
     g.close()
+    # explicit source: the rate constants of the three stage inputs, 6 nr doubles per cell and step
+    glob = inputs.load_mechanism("global_h2o2_g129")
+    Y = inputs.premix_Y(glob, {"H2": 4.032, "O2": 31.998})
+    st = inputs.tube(glob, nx, ny, Lx=0.025 * nx / 128, Y=Y, perturb_seed=4)
+    g = J.Grid.from_grid_dict(glob, st["grid"], chemistry=J.CHEM_EXPLICIT)
+    nv, nr = 6, glob["nr"]
+    _mode(J, g, False)
+    base = J.janc_adjoint_workspace_bytes(g.handle, 30, 7)
+    _mode(J, g, True)
+    store = J.janc_adjoint_workspace_bytes(g.handle, 30, 7)
+    faces = al(8 * 3 * 7 * 8 * nv * ((nx + 1) * ny + (ny + 1) * nx))
+    assert store - base == 2 * (faces + al(8 * 7 * 6 * nr * nx * ny))
+    g.close()
