@@ -337,6 +337,151 @@ __device__ __forceinline__ void gather_dir(const StateView& S, double* __restric
   }
 }
 
+// A mass-action monomial prod_s X_{sp(s)}^{a(s)} over n <= MAX_SIDE distinct
+// species (sp, a: accessors of the reaction side): the value, the gradient
+// g_s, the derivative along e (D), and the gradient of D
+// (h_s = sum_t e_t d2/dX_t dX_s).
+template <class SP, class A>
+__device__ __forceinline__ void monomial(const double* X, SP sp, A a, int n, const double* e, double& val, double* g,
+                                         double& D, double* h) {
+  double P[MAX_SIDE], P1[MAX_SIDE], P2[MAX_SIDE];
+#pragma unroll
+  for (int s = 0; s < n; ++s) {
+    const double x = X[sp(s)];
+    double pw = 1.0;
+#pragma unroll
+    for (int q = 0; q < a(s) - 2; ++q) pw *= x;  // x^(a-2)
+    P2[s] = a(s) >= 2 ? a(s) * (a(s) - 1) * pw : 0.0;
+    const double pw1 = a(s) >= 2 ? pw * x : 1.0;  // x^(a-1)
+    P1[s] = a(s) * pw1;
+    P[s] = pw1 * x;
+  }
+  val = 1.0;
+#pragma unroll
+  for (int s = 0; s < n; ++s) val *= P[s];
+  D = 0.0;
+#pragma unroll
+  for (int s = 0; s < n; ++s) {
+    double ex = P1[s];
+#pragma unroll
+    for (int t = 0; t < n; ++t)
+      if (t != s) ex *= P[t];
+    g[s] = ex;
+    D = fma(e[sp(s)], ex, D);
+  }
+#pragma unroll
+  for (int s = 0; s < n; ++s) {
+    double hs = 0.0;
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+      double v;
+      if (t == s) {
+        v = P2[s];
+#pragma unroll
+        for (int w = 0; w < n; ++w)
+          if (w != s) v *= P[w];
+      } else {
+        v = P1[s] * P1[t];
+#pragma unroll
+        for (int w = 0; w < n; ++w)
+          if (w != s && w != t) v *= P[w];
+      }
+      hs = fma(e[sp(t)], v, hs);
+    }
+    h[s] = hs;
+  }
+}
+
+// Explicit source S(U): rho Y_k rows receive M_k wdot_k(T(U), X(U)). Its VJP
+// (dS/dU)^T mu is the gradient of g = sum_i m_i q_i with
+// m_i = sum_k nu_ki w_k, w_k = M_k mu_{4+k}, in (T, X) per reaction; the cell
+// pass chains it through X(U) and the implicit dT/dU. keep: k_f and k_b of
+// the stage input kept by the forward (entries 2i, 2i+1 of cell q), or null
+// to form them again.
+template <int NS>
+__device__ __forceinline__ void src_grad(const double* u, double T, const MechDev& m, const double* w,
+                                         const double* __restrict__ keep, long long n, long long q, double& gT_out,
+                                         double* gX) {
+  constexpr int NSP = NS - 1;
+  double X[NS];
+  double rest = u[0];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    X[k] = u[4 + k] * m.invM[k];
+    rest -= u[4 + k];
+  }
+  X[NSP] = rest * m.invM[NSP];
+  double Ctot = X[0];
+#pragma unroll
+  for (int k = 1; k < NS; ++k) Ctot += X[k];
+  const double rT = rcp(T);
+  const double rT2 = rT * rT;
+  // with `keep` the forward's k_f and k_b are read back and exp(G_k) is not needed
+  const double lnT = keep ? 0.0 : log(T);
+  double eG[NS], reG[NS], dG[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double* c = m.gc[k];
+    if (!keep) {
+      eG[k] = exp_t(fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6]))));
+      reG[k] = rcp(eG[k]);
+    }
+    dG[k] = fma(c[0], rT, fma(-c[5], rT2, fma(T, fma(T, fma(T, 4.0 * c[4], 3.0 * c[3]), 2.0 * c[2]), c[1])));
+  }
+  const double cref = (P_REF / RU) * rT;
+  const double rcref = (RU / P_REF) * T;
+  double zero[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) zero[k] = 0.0;
+  double gT = 0.0;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) gX[k] = 0.0;
+  for (int i = 0; i < m.nr; ++i) {
+    const int nre = m.nre[i], npr = m.npr[i];
+    double mi = 0.0;
+    for (int r = 0; r < nre; ++r)
+      if (m.rsp[i][r] < NSP) mi = fma(-m.rnud[i][r], w[m.rsp[i][r]], mi);
+    for (int r = 0; r < npr; ++r)
+      if (m.psp[i][r] < NSP) mi = fma(m.pnud[i][r], w[m.psp[i][r]], mi);
+    const double dlkf = fma(m.b[i], rT, m.EaR[i] * rT2);
+    double kf, kb, dlkb = dlkf;
+    for (int r = 0; r < nre; ++r)
+      for (int qq = 0; qq < m.rnu[i][r]; ++qq) dlkb += dG[m.rsp[i][r]];
+    for (int r = 0; r < npr; ++r)
+      for (int qq = 0; qq < m.pnu[i][r]; ++qq) dlkb -= dG[m.psp[i][r]];
+    const int dn = m.dnu[i];
+    dlkb = fma((double)dn, rT, dlkb);
+    if (keep) {
+      kf = __ldg(keep + (2LL * i) * n + q);
+      kb = __ldg(keep + (2LL * i + 1) * n + q);
+    } else {
+      kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
+      kb = kf;
+      for (int r = 0; r < nre; ++r)
+        for (int qq = 0; qq < m.rnu[i][r]; ++qq) kb *= eG[m.rsp[i][r]];
+      for (int r = 0; r < npr; ++r)
+        for (int qq = 0; qq < m.pnu[i][r]; ++qq) kb *= reG[m.psp[i][r]];
+      for (int qq = 0; qq < dn; ++qq) kb *= rcref;
+      for (int qq = 0; qq < -dn; ++qq) kb *= cref;
+    }
+    double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
+    monomial(X, [&](int s_) { return m.rsp[i][s_]; }, [&](int s_) { return m.rnu[i][s_]; }, nre, zero, F, gF, DF, hF);
+    monomial(X, [&](int s_) { return m.psp[i][s_]; }, [&](int s_) { return m.pnu[i][s_]; }, npr, zero, B, gB, DB, hB);
+    double Mi = 1.0;
+    if (m.tb[i]) {
+      Mi = Ctot;
+      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
+    }
+    const double net = fma(kf, F, -kb * B);
+    gT = fma(mi * Mi, fma(kf * dlkf, F, -kb * dlkb * B), gT);
+    for (int r = 0; r < nre; ++r) gX[m.rsp[i][r]] = fma(mi * Mi * kf, gF[r], gX[m.rsp[i][r]]);
+    for (int r = 0; r < npr; ++r) gX[m.psp[i][r]] = fma(-mi * Mi * kb, gB[r], gX[m.psp[i][r]]);
+    if (m.tb[i])
+      for (int j = 0; j < NS; ++j) gX[j] = fma(1.0 + m.effm1[i][j], mi * net, gX[j]);
+  }
+  gT_out = gT;
+}
+
 // Lexicographic arg-max step: the larger speed (non-negative doubles as
 // bits), on equal speeds the lower linear index.
 __device__ __forceinline__ void argmax_merge(unsigned long long& m, int& i, unsigned long long m2, int i2) {
@@ -347,11 +492,14 @@ __device__ __forceinline__ void argmax_merge(unsigned long long& m, int& i, unsi
 // cotangents it leaves, per block, the block sums of the alpha cotangents
 // (atomically added) and the arg-max of |u|+c and |v|+c over its cells in
 // part_mx / part_id [2 * block + direction].
-template <int NS>
+// SRC (the explicit source-term form): the cell also adds the VJP of the
+// source S(U) at this stage state, (dS/dU)^T mu (src_grad, with the rate
+// constants from src_keep when the forward kept them).
+template <int NS, bool SRC>
 __global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, double* __restrict__ GFx,
                             double* __restrict__ GFy, VjpIO io, double* adj_alpha, GridDev g,
                             const MechDev* __restrict__ mech, unsigned long long* __restrict__ part_mx,
-                            int* __restrict__ part_id) {
+                            int* __restrict__ part_id, const double* __restrict__ src_keep) {
   constexpr int NV = NS + 3;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -380,6 +528,23 @@ __global__ void k_adj_cells(StateView S, const double* __restrict__ alpha2, doub
     aU[0] += -(vx * a_u + vy * a_v) * rrho;
     aU[1] += a_u * rrho;
     aU[2] += a_v * rrho;
+    if constexpr (SRC) {
+      constexpr int NSP = NS - 1;
+      const MechDev& m = *mech;
+      double w[NSP];
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) w[k] = m.M[k] * (io.mu_scale * io.lam[(long long)(4 + k) * n + idx]);
+      double gT, gX[NS];
+      src_grad<NS>(u, T, m, w, src_keep, n, idx, gT, gX);
+      const double gN = gX[NSP] * m.invM[NSP];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double d = gT * dT[k];
+        if (k == 0) d += gN;
+        if (k >= 4) d += fma(gX[k - 4], m.invM[k - 4], -gN);
+        aU[k] += d;
+      }
+    }
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       const long long kq = (long long)k * n + idx;
@@ -546,61 +711,6 @@ __global__ void k_adj_alpha(StateView S, GridDev g, const MechDev* __restrict__ 
 // monomials; its gradient in (T, X) is written out per reaction below and
 // chained to U* through X(U*) and the implicit dT/dU* of the Newton recovery.
 // ---------------------------------------------------------------------------
-
-// A mass-action monomial prod_s X_{sp(s)}^{a(s)} over n <= MAX_SIDE distinct
-// species (sp, a: accessors of the reaction side): the value, the gradient
-// g_s, the derivative along e (D), and the gradient of D
-// (h_s = sum_t e_t d2/dX_t dX_s).
-template <class SP, class A>
-__device__ __forceinline__ void monomial(const double* X, SP sp, A a, int n, const double* e, double& val, double* g,
-                                         double& D, double* h) {
-  double P[MAX_SIDE], P1[MAX_SIDE], P2[MAX_SIDE];
-#pragma unroll
-  for (int s = 0; s < n; ++s) {
-    const double x = X[sp(s)];
-    double pw = 1.0;
-#pragma unroll
-    for (int q = 0; q < a(s) - 2; ++q) pw *= x;  // x^(a-2)
-    P2[s] = a(s) >= 2 ? a(s) * (a(s) - 1) * pw : 0.0;
-    const double pw1 = a(s) >= 2 ? pw * x : 1.0;  // x^(a-1)
-    P1[s] = a(s) * pw1;
-    P[s] = pw1 * x;
-  }
-  val = 1.0;
-#pragma unroll
-  for (int s = 0; s < n; ++s) val *= P[s];
-  D = 0.0;
-#pragma unroll
-  for (int s = 0; s < n; ++s) {
-    double ex = P1[s];
-#pragma unroll
-    for (int t = 0; t < n; ++t)
-      if (t != s) ex *= P[t];
-    g[s] = ex;
-    D = fma(e[sp(s)], ex, D);
-  }
-#pragma unroll
-  for (int s = 0; s < n; ++s) {
-    double hs = 0.0;
-#pragma unroll
-    for (int t = 0; t < n; ++t) {
-      double v;
-      if (t == s) {
-        v = P2[s];
-#pragma unroll
-        for (int w = 0; w < n; ++w)
-          if (w != s) v *= P[w];
-      } else {
-        v = P1[s] * P1[t];
-#pragma unroll
-        for (int w = 0; w < n; ++w)
-          if (w != s && w != t) v *= P[w];
-      }
-      hs = fma(e[sp(t)], v, hs);
-    }
-    h[s] = hs;
-  }
-}
 
 // The forward pass keeps k_f, k_b and their log-T derivatives of every
 // reaction for the reverse pass: in local arrays for the run-time table, in
@@ -1094,116 +1204,6 @@ __global__ void __launch_bounds__(128) k_adj_chem_rev(StateView Sstar, GridDev g
   for (int k = 0; k < NV; ++k) out[(long long)k * n + q] = o[k];
 }
 
-// Explicit source S(U): rho Y_k rows receive M_k wdot_k(T(U), X(U)). The VJP
-// nu += (dS/dU)^T mu is the gradient of g = sum_i m_i q_i with
-// m_i = sum_k nu_ki M_k mu_{4+k}, in (T, X) per reaction, chained through
-// X(U) and the implicit dT/dU.
-template <int NS>
-__global__ void __launch_bounds__(128) k_src_vjp(StateView S, GridDev g, const MechDev* __restrict__ mech,
-                                                 const double* __restrict__ lam, double mu_scale,
-                                                 double* __restrict__ nu, const double* __restrict__ keep) {
-  constexpr int NSP = NS - 1;
-  constexpr int NV = NS + 3;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= g.n) return;
-  const long long n = g.n;
-  const MechDev& m = *mech;
-  double u[NV], w[NSP];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) u[k] = S.plane(k, n)[q];
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) w[k] = m.M[k] * (mu_scale * lam[(long long)(4 + k) * n + q]);
-  const double T = S.plane(NV, n)[q];
-  double X[NS];
-  double rest = u[0];
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) {
-    X[k] = u[4 + k] * m.invM[k];
-    rest -= u[4 + k];
-  }
-  X[NSP] = rest * m.invM[NSP];
-  double Ctot = X[0];
-#pragma unroll
-  for (int k = 1; k < NS; ++k) Ctot += X[k];
-  const double rT = rcp(T);
-  const double rT2 = rT * rT;
-  // with `keep` the forward's k_f and k_b are read back and exp(G_k) is not needed
-  const double lnT = keep ? 0.0 : log(T);
-  double eG[NS], reG[NS], dG[NS];
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    const double* c = m.gc[k];
-    if (!keep) {
-      eG[k] = exp_t(fma(c[0], lnT, fma(c[5], rT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[6]))));
-      reG[k] = rcp(eG[k]);
-    }
-    dG[k] = fma(c[0], rT, fma(-c[5], rT2, fma(T, fma(T, fma(T, 4.0 * c[4], 3.0 * c[3]), 2.0 * c[2]), c[1])));
-  }
-  const double cref = (P_REF / RU) * rT;
-  const double rcref = (RU / P_REF) * T;
-  double zero[NS];
-#pragma unroll
-  for (int k = 0; k < NS; ++k) zero[k] = 0.0;
-  double gT = 0.0, gX[NS];
-#pragma unroll
-  for (int k = 0; k < NS; ++k) gX[k] = 0.0;
-  for (int i = 0; i < m.nr; ++i) {
-    const int nre = m.nre[i], npr = m.npr[i];
-    double mi = 0.0;
-    for (int r = 0; r < nre; ++r)
-      if (m.rsp[i][r] < NSP) mi = fma(-m.rnud[i][r], w[m.rsp[i][r]], mi);
-    for (int r = 0; r < npr; ++r)
-      if (m.psp[i][r] < NSP) mi = fma(m.pnud[i][r], w[m.psp[i][r]], mi);
-    const double dlkf = fma(m.b[i], rT, m.EaR[i] * rT2);
-    double kf, kb, dlkb = dlkf;
-    for (int r = 0; r < nre; ++r)
-      for (int qq = 0; qq < m.rnu[i][r]; ++qq) dlkb += dG[m.rsp[i][r]];
-    for (int r = 0; r < npr; ++r)
-      for (int qq = 0; qq < m.pnu[i][r]; ++qq) dlkb -= dG[m.psp[i][r]];
-    const int dn = m.dnu[i];
-    dlkb = fma((double)dn, rT, dlkb);
-    if (keep) {
-      kf = __ldg(keep + (2LL * i) * n + q);
-      kb = __ldg(keep + (2LL * i + 1) * n + q);
-    } else {
-      kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
-      kb = kf;
-      for (int r = 0; r < nre; ++r)
-        for (int qq = 0; qq < m.rnu[i][r]; ++qq) kb *= eG[m.rsp[i][r]];
-      for (int r = 0; r < npr; ++r)
-        for (int qq = 0; qq < m.pnu[i][r]; ++qq) kb *= reG[m.psp[i][r]];
-      for (int qq = 0; qq < dn; ++qq) kb *= rcref;
-      for (int qq = 0; qq < -dn; ++qq) kb *= cref;
-    }
-    double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
-    monomial(X, [&](int s_) { return m.rsp[i][s_]; }, [&](int s_) { return m.rnu[i][s_]; }, nre, zero, F, gF, DF, hF);
-    monomial(X, [&](int s_) { return m.psp[i][s_]; }, [&](int s_) { return m.pnu[i][s_]; }, npr, zero, B, gB, DB, hB);
-    double Mi = 1.0;
-    if (m.tb[i]) {
-      Mi = Ctot;
-      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
-    }
-    const double net = fma(kf, F, -kb * B);
-    gT = fma(mi * Mi, fma(kf * dlkf, F, -kb * dlkb * B), gT);
-    for (int r = 0; r < nre; ++r) gX[m.rsp[i][r]] = fma(mi * Mi * kf, gF[r], gX[m.rsp[i][r]]);
-    for (int r = 0; r < npr; ++r) gX[m.psp[i][r]] = fma(-mi * Mi * kb, gB[r], gX[m.psp[i][r]]);
-    if (m.tb[i])
-      for (int j = 0; j < NS; ++j) gX[j] = fma(1.0 + m.effm1[i][j], mi * net, gX[j]);
-  }
-  CellThermo<NS> ct;
-  cell_thermo<NS>(u, T, m, ct);
-  double dT[NV], dp[NV];
-  dT_dp_dU<NS>(u, T, m, ct, dT, dp);
-  const double gN = gX[NSP] * m.invM[NSP];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double d = gT * dT[k];
-    if (k == 0) d += gN;
-    if (k >= 4) d += fma(gX[k - 4], m.invM[k - 4], -gN);
-    nu[(long long)k * n + q] += d;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Small kernels: linear combinations, loss terms, primitive T derivative.
 // ---------------------------------------------------------------------------
@@ -1318,7 +1318,7 @@ size_t rhs_vjp_scratch_bytes(const GridDev& g) {
 template <int NS>
 static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const VjpIO& io, double* CFx, double* CFy,
                              double* scratch, const GridDev& g, const MechDev* mech, const double* lin, bool fresh,
-                             cudaStream_t st) {
+                             bool src, const double* src_keep, cudaStream_t st) {
   constexpr int NV = NS + 3;
   const int nb = adj_cell_blocks(g);
   double* adj_alpha = scratch;
@@ -1353,18 +1353,28 @@ static cudaError_t rhs_vjp_t(const StateView& S, const double* alpha2_dev, const
     else k_adj_faces<NV, 8><<<total, VLINES * NV, 0, st>>>(S, alpha2_dev, mu, ms, CFx, CFy, g, nbx, ntx_x, ntx_y);
   }
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-  k_adj_cells<NS><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, io, adj_alpha, g, mech, part_mx, part_id);
+  bool done = false;
+  if constexpr (NS > 1) {
+    if (src) {
+      k_adj_cells<NS, true><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, io, adj_alpha, g, mech, part_mx, part_id,
+                                                  src_keep);
+      done = true;
+    }
+  }
+  if (!done)
+    k_adj_cells<NS, false><<<grd, blk, 0, st>>>(S, alpha2_dev, CFx, CFy, io, adj_alpha, g, mech, part_mx, part_id,
+                                                 nullptr);
   k_adj_alpha<NS><<<1, 256, 0, st>>>(S, g, mech, part_mx, part_id, nb, adj_alpha, io.a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const VjpIO& io, double* CFx,
                            double* CFy, double* scratch, const GridDev& g, const MechDev* mech, const double* lin,
-                           bool fresh, cudaStream_t st) {
+                           bool fresh, bool src, const double* src_keep, cudaStream_t st) {
   switch (ns) {
-    case 1: return rhs_vjp_t<1>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, st);
-    case 3: return rhs_vjp_t<3>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, st);
-    case 9: return rhs_vjp_t<9>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, st);
+    case 1: return rhs_vjp_t<1>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, src, src_keep, st);
+    case 3: return rhs_vjp_t<3>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, src, src_keep, st);
+    case 9: return rhs_vjp_t<9>(S, alpha2_dev, io, CFx, CFy, scratch, g, mech, lin, fresh, src, src_keep, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1401,15 +1411,6 @@ cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const VjpIO& io,
-                              const double* keep, cudaStream_t st) {
-  switch (ns) {
-    case 3: k_src_vjp<3><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, io.lam, io.mu_scale, io.a, keep); break;
-    case 9: k_src_vjp<9><<<nblk(g.n, 128), 128, 0, st>>>(S, g, mech, io.lam, io.mu_scale, io.a, keep); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
 
 cudaError_t launch_lincomb(long long count, double* out, double a, const double* x, double b, const double* y,
                            bool accumulate, cudaStream_t st) {

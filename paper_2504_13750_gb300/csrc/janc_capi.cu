@@ -733,7 +733,7 @@ int janc_rhs_vjp(janc_grid_t g, const double* mu, double* nu, void* workspace, s
   if (e == cudaSuccess)
     e = launch_rhs_vjp(g->ns, sv(g, 0), (const double*)g->alpha,
                        VjpIO{dmu, 1.0, dnu, nullptr, 0.0, 0, nullptr, nullptr, 0.0, 0}, cfx, cfy, scratch, g->gd,
-                       g->mech, nullptr, true, g->stream);
+                       g->mech, nullptr, true, false, nullptr, g->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(nu, dnu, sizeof(double) * nvn,
                         where == JANC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream);
@@ -1044,29 +1044,23 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
         else e = cudaMemcpyAsync(lamS, lamN, sizeof(double) * nvn, cudaMemcpyDeviceToDevice, st);
       }
       // Each stage's RHS VJP takes mu = c dt lam directly and writes the
-      // stage's combinations itself (VjpIO); the explicit-source VJP adds
-      // to the same output.
+      // stage's combinations itself (VjpIO); in the explicit source-term form
+      // its cell pass also adds the source's VJP at the stage state.
       // stage 3: U* = U^n/3 + 2/3 (U2 + dt L(U2)): lam2 = 2/3 lamS + L^T mu, lam0 = lamS / 3
       const VjpIO io3{lamS, 2.0 / 3.0 * dt, lam2, lamS, 2.0 / 3.0, 0, lam0, lamS, 1.0 / 3.0, 0};
       if (e == cudaSuccess)
         e = launch_rhs_vjp(g->ns, segS(m, 2), (const double*)(a + 4), io3, cfx, cfy, small + 32, g->gd, g->mech,
-                           seg_lin(sq, L, m, 2), false, st);
-      if (e == cudaSuccess && src)
-        e = launch_source_vjp(g->ns, segS(m, 2), g->gd, g->mech, io3, seg_src(sq, L, m, 2), st);
+                           seg_lin(sq, L, m, 2), false, src, src ? seg_src(sq, L, m, 2) : nullptr, st);
       // stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1)): lam1 = lam2 / 4 + L^T mu, lam0 += 3/4 lam2
       const VjpIO io2{lam2, 0.25 * dt, lam1, lam2, 0.25, 0, lam0, lam2, 0.75, 1};
       if (e == cudaSuccess)
         e = launch_rhs_vjp(g->ns, segS(m, 1), (const double*)(a + 2), io2, cfx, cfy, small + 32, g->gd, g->mech,
-                           seg_lin(sq, L, m, 1), false, st);
-      if (e == cudaSuccess && src)
-        e = launch_source_vjp(g->ns, segS(m, 1), g->gd, g->mech, io2, seg_src(sq, L, m, 1), st);
+                           seg_lin(sq, L, m, 1), false, src, src ? seg_src(sq, L, m, 1) : nullptr, st);
       // stage 1: U1 = U^n + dt L(U^n): lam0 += lam1 + L^T mu
       const VjpIO io1{lam1, dt, lam0, lam1, 1.0, 1, nullptr, nullptr, 0.0, 0};
       if (e == cudaSuccess)
         e = launch_rhs_vjp(g->ns, segS0(m), (const double*)a, io1, cfx, cfy, small + 32, g->gd, g->mech,
-                           seg_lin(sq, L, m, 0), false, st);
-      if (e == cudaSuccess && src)
-        e = launch_source_vjp(g->ns, segS0(m), g->gd, g->mech, io1, seg_src(sq, L, m, 0), st);
+                           seg_lin(sq, L, m, 0), false, src, src ? seg_src(sq, L, m, 0) : nullptr, st);
       std::swap(lamN, lam0);
     }
     // segment c's store is free once its reverse is done: refill it with c - 2

@@ -50,15 +50,6 @@ cudaError_t launch_rk_update(int ns, int stage, const StateView& Sin, const Stat
                              const StepCtl& ctl, const unsigned long long* alpha_step, unsigned long long* alpha_out,
                              int* status, double* clock2, cudaStream_t st, double* src_keep = nullptr);
 
-// io.a += (dS/dU)^T mu, mu = io.mu_scale io.lam, for the explicit source S(U)
-// (production rates of the carried species at the stored T) at state S
-// (janc_adjoint.cu).
-// keep: the stage's rate constants kept by launch_rk_update, or null to form
-// them again.
-struct VjpIO;
-cudaError_t launch_source_vjp(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const VjpIO& io,
-                              const double* keep, cudaStream_t st);
-
 // Point-implicit chemistry in place on S (janc_chem.cu).
 cudaError_t launch_chem(int ns, const StateView& S, const GridDev& g, const MechDev* mech, const StepCtl& ctl,
                         const unsigned long long* alpha_step, unsigned long long* alpha_out, int* status,
@@ -121,10 +112,12 @@ struct VjpIO {
 // lin: the state's face-derivative store (launch_face_flux_lin), or null to
 // recompute the reconstructions. fresh: zero the per-position sums and the
 // alpha cotangents first; otherwise they must be zero on entry (every call
-// leaves them zero).
+// leaves them zero). src (explicit source-term form): add the VJP of the
+// source S(U) at the state, (dS/dU)^T mu, to io.a; src_keep: the stage's rate
+// constants kept by launch_rk_update, or null to form them again.
 cudaError_t launch_rhs_vjp(int ns, const StateView& S, const double* alpha2_dev, const VjpIO& io, double* CFx,
                            double* CFy, double* scratch, const GridDev& g, const MechDev* mech, const double* lin,
-                           bool fresh, cudaStream_t st);
+                           bool fresh, bool src, const double* src_keep, cudaStream_t st);
 // clin: the factors the segment recompute kept (launch_chem_lin), or null to
 // form them again.
 cudaError_t launch_chem_vjp(int ns, const StateView& Sstar, const GridDev& g, const MechDev* mech, double dt,
