@@ -453,3 +453,29 @@ def test_store_mode_workspace_matches_the_documented_size(J):
     faces = al(8 * 3 * 7 * 8 * nv * ((nx + 1) * ny + (ny + 1) * nx))
     assert store - base == 2 * (faces + al(8 * 7 * 6 * nr * nx * ny))
     g.close()
+
+
+def test_pending_forward_keeps_its_mode(J):
+    """A forward started in the store mode is reversed from its stores even
+    when the grid's mode is changed before janc_adjoint_reverse (the mode is
+    read by the forward); the result equals an uninterrupted store-mode run bit
+    for bit, and the other mode's within rounding."""
+    st, U = _state(24, 8, 51, vel=40.0)
+    n, dt, ck = 9, 1e-8, 4
+    g = J.Grid.from_grid_dict(H2AIR, st["grid"])
+    seed = np.ascontiguousarray(np.random.default_rng(52).normal(size=U.shape)
+                                / np.maximum(np.abs(U).reshape(U.shape[0], -1).max(axis=1), 1e-12)[:, None, None])
+    grads = {}
+    for name, fwd_mode, rev_mode in (("store", True, True), ("switched", True, False), ("recompute", False, False)):
+        g.set_state(U, st["T"])
+        _mode(J, g, fwd_mode)
+        J.janc_adjoint_forward(g.handle, n, dt, ck, J.LOSS_SEEDED)
+        _mode(J, g, rev_mode)
+        out = np.zeros_like(U)
+        J.janc_adjoint_reverse(g.handle, seed, out)
+        grads[name] = out
+    assert np.array_equal(grads["store"], grads["switched"])
+    for k in range(U.shape[0]):
+        s = max(np.max(np.abs(grads["recompute"][k])), 1e-300)
+        assert np.max(np.abs(grads["store"][k] - grads["recompute"][k])) <= 1e-11 * s, k
+    g.close()
