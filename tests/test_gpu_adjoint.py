@@ -458,8 +458,9 @@ def test_store_mode_workspace_matches_the_documented_size(J):
 def test_pending_forward_keeps_its_mode(J):
     """A forward started in the store mode is reversed from its stores even
     when the grid's mode is changed before janc_adjoint_reverse (the mode is
-    read by the forward); the result equals an uninterrupted store-mode run bit
-    for bit, and the other mode's within rounding."""
+    read by the forward); the result equals an uninterrupted store-mode run up
+    to the rounding of the atomic block sums of the alpha cotangents, and the
+    other mode's within rounding."""
     st, U = _state(24, 8, 51, vel=40.0)
     n, dt, ck = 9, 1e-8, 4
     g = J.Grid.from_grid_dict(H2AIR, st["grid"])
@@ -474,8 +475,8 @@ def test_pending_forward_keeps_its_mode(J):
         out = np.zeros_like(U)
         J.janc_adjoint_reverse(g.handle, seed, out)
         grads[name] = out
-    assert np.array_equal(grads["store"], grads["switched"])
     for k in range(U.shape[0]):
-        s = max(np.max(np.abs(grads["recompute"][k])), 1e-300)
+        s = max(np.max(np.abs(grads["store"][k])), 1e-300)
+        assert np.max(np.abs(grads["store"][k] - grads["switched"][k])) <= 1e-12 * s, k
         assert np.max(np.abs(grads["store"][k] - grads["recompute"][k])) <= 1e-11 * s, k
     g.close()
