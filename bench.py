@@ -407,7 +407,7 @@ def run_adjoint(janc, stream, nsteps=500, ckpt=50):
             "store_all": res[best, nsteps],
             "modes": {names[m]: {"ckpt": res[m, ckpt], "store_all": res[m, nsteps]} for m in names},
             "note": "forward_s is janc_step over the trajectory; adjoint_s covers the forward with checkpoints, the "
-                    "recompute of every segment but the last and the reverse sweep; store_all keeps the whole "
+                    "recompute of every segment but the last two and the reverse sweep; store_all keeps the whole "
                     "trajectory in HBM (one segment, nothing recomputed). Modes: recompute rebuilds the WENO5 "
                     "derivatives in the reverse face pass; store_faces keeps them from the forward / recompute "
                     "(JANC_ADJ_STORE_FACES); the headline is the faster mode at the stated interval",

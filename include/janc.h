@@ -230,7 +230,7 @@ int janc_selfcheck_exp(const double* x, int n, long long* max_ulp);
  * reconstructions (Eq. 4.10) from the stage state, and the chemistry VJP
  * forms the rates, J'' and the LU factors of Eq. 4.13 again.
  * JANC_ADJ_STORE_FACES: the steps that fill a segment store (the forward's
- * last segment, every recomputed segment) run a face-flux kernel that also
+ * last two segments, every recomputed segment) run a face-flux kernel that also
  * stores, per face, variable and split sign, the four partials of the
  * reconstruction with respect to its window's differences, and (with
  * JANC_CHEM_LIE) a chemistry kernel that also keeps, per cell, the rate
@@ -257,8 +257,8 @@ int janc_set_adjoint_mode(janc_grid_t g, int mode);
 /* Device bytes janc_step_adjoint needs as workspace: checkpoints every
  * ckpt_every steps, the stage states of one segment of ckpt_every steps (two
  * such stores when n_steps > ckpt_every), cotangent and face buffers. The
- * forward writes the last segment's stages directly, so the reverse
- * recomputes every segment but the last; with ckpt_every >= n_steps the
+ * forward writes the last two segments' stages directly (one per store), so
+ * the reverse recomputes every segment but those; with ckpt_every >= n_steps the
  * whole trajectory is kept and nothing is recomputed (about
  * (4 n_steps + 2) (nv + 4) nx ny doubles, plus the face derivatives and
  * chemistry factors of n_steps steps in mode JANC_ADJ_STORE_FACES). */

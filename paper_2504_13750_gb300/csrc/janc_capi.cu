@@ -898,13 +898,14 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
   auto ckpt_state = [&](int c) { return StateView{(double*)(q.ckpt + (size_t)c * (L.state + 256))}; };
   auto ckpt_alpha = [&](int c) { return (unsigned long long*)(q.ckpt + (size_t)c * (L.state + 256) + L.state); };
   const double w_loss = dt / g->gd.ny;
-  // The steps of the last segment run straight into the segment store, so
-  // that the reverse sweep starts without recomputing them; with
-  // ckpt_every >= n_steps nothing is recomputed at all.
-  const int m_last = (L.ncp - 1) * ckpt_every;
+  // The steps of the last nstore segments (one per segment store) run
+  // straight into the stores, so that the reverse sweep starts on them
+  // without recomputing anything; with ckpt_every >= n_steps nothing is
+  // recomputed at all.
+  const int m_first = (L.ncp - L.nstore) * ckpt_every;
   int rc = JANC_OK;
   cudaError_t e = cudaMemsetAsync(q.small, 0, 256, st);
-  for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
+  for (int s = 0; s < n_steps && e == cudaSuccess;) {
     if (s % ckpt_every == 0) {
       const int c = s / ckpt_every;
       e = cudaMemcpyAsync(ckpt_state(c).base, g->S[0], L.state, cudaMemcpyDeviceToDevice, st);
@@ -912,9 +913,9 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
         e = cudaMemcpyAsync(ckpt_alpha(c), g->alpha, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
     }
     if (e != cudaSuccess) break;
-    if (s == m_last) {
-      const int len = n_steps - m_last;
-      const SegStore& sq = q.store[(L.ncp - 1) % L.nstore];
+    if (s >= m_first) {  // s is the first step of segment s / ckpt_every
+      const int len = (n_steps - s) < ckpt_every ? (n_steps - s) : ckpt_every;
+      const SegStore& sq = q.store[(s / ckpt_every) % L.nstore];
       e = cudaMemcpyAsync(seg_S0(sq, L, 0).base, g->S[0], L.state, cudaMemcpyDeviceToDevice, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(sq.alog, 0, L.alog, st);
       if (e == cudaSuccess)
@@ -928,11 +929,13 @@ int janc_adjoint_forward(janc_grid_t g, int n_steps, double dt, int ckpt_every, 
         e = cudaMemcpyAsync(g->alpha, sq.alog + 10 * (len - 1) + 8, 2 * sizeof(unsigned long long),
                             cudaMemcpyDeviceToDevice, st);
       g->steps_done += len;
-      break;
+      s += len;
+      continue;
     }
     rc = janc_step(g, 1, dt, 0.0, nullptr, nullptr);
     if (rc) break;
     if (loss_kind == JANC_LOSS_ENDWALL_P) e = launch_loss_endwall(g->ns, sv(g, 0), g->gd, w_loss, q.small, st);
+    ++s;
   }
   if (!rc && e == cudaSuccess && loss_out) e = cudaMemcpyAsync(loss_out, q.small, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -987,11 +990,11 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
   if (e == cudaSuccess) e = cudaMemsetAsync(cfx, 0, L.cfx, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(cfy, 0, L.cfy, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(small + 32, 0, 2 * sizeof(double), st);
-  // Segments other than the last are recomputed from their checkpoints on a
-  // second stream into the other segment store, one segment ahead of the
-  // reverse sweep: segment c - 1 is recomputed while segment c is reversed.
-  // On a grid too small to fill the GPU the two overlap. Store c % 2 is
-  // refilled (segment c - 2) only after segment c's reverse has finished.
+  // The forward left its last nstore segments in the stores. The others are
+  // recomputed from their checkpoints on a second stream, one segment ahead
+  // of the reverse sweep: segment c - 2 goes into store c % 2 once segment
+  // c's reverse has finished with it, and is recomputed while segment c - 1
+  // is reversed.
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_rev = nullptr;
   auto seg_len = [&](int c) {
@@ -1009,10 +1012,10 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
     return r;
   };
   // With recomputation the sweep runs on an internal stream of the highest
-  // priority and the recompute on one of the lowest: the sweep is the
-  // critical path, the recompute has a whole segment of slack.
+  // priority and the recompute on one of the lowest.
+  const int n_fwd = L.nstore;  // trailing segments the forward left in the stores
   cudaStream_t s1 = nullptr;
-  if (e == cudaSuccess && L.ncp > 1 && n_steps > 0) {
+  if (e == cudaSuccess && L.ncp > n_fwd && n_steps > 0) {
     int least = 0, greatest = 0;
     e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s1, cudaStreamNonBlocking, greatest);
@@ -1024,7 +1027,6 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_rev, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, ev_rev, 0);
     if (e == cudaSuccess) st = s1;
-    if (e == cudaSuccess) e = recompute(L.ncp - 2);
   }
   for (int c = L.ncp - 1; c >= 0 && e == cudaSuccess && n_steps > 0; --c) {
     const int len = seg_len(c);
@@ -1032,8 +1034,8 @@ int janc_adjoint_reverse(janc_grid_t g, const double* seed, double* dL_dU0, int 
     const unsigned long long* alog = sq.alog;
     auto segS0 = [&](int m) { return seg_S0(sq, L, m); };
     auto segS = [&](int m, int which) { return seg_S(sq, L, m, which); };
-    // the forward left the last segment in its store; the others come from s2
-    if (c < L.ncp - 1) e = cudaStreamWaitEvent(st, ev_rec[c % 2], 0);
+    // the forward left the last n_fwd segments in their stores; the others come from s2
+    if (c < L.ncp - n_fwd) e = cudaStreamWaitEvent(st, ev_rec[c % 2], 0);
     // reverse through the segment
     for (int m = len - 1; m >= 0 && e == cudaSuccess; --m) {
       const unsigned long long* a = alog + 10 * m;
