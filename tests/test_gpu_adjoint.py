@@ -514,3 +514,36 @@ def test_stiff_chemistry_dot_product(J, store):
         a, b = float(np.sum(seed * dUN[l])), float(np.sum(gU0 * V[l]))
         assert abs(a - b) <= 1e-8 * np.sum(np.abs(seed * dUN[l])), (l, a, b)
     g.close()
+
+
+@MODES
+def test_ideal_gas_trajectory_dot_product(J, store):
+    """The one-species ideal gas (4 conserved variables, no chemistry):
+    <seed, dU^N> from the oracle's trajectory tangent equals
+    <dL/dU^0, dU^0> from the GPU reverse sweep, in both adjoint modes (the
+    4-variable face-derivative store included), on a dx != dy grid."""
+    gas = inputs.load_mechanism("ideal_gamma14")
+    nx, ny = 20, 12
+    rng = np.random.default_rng(71)
+    T = 300.0 + rng.normal(0.0, 15.0, (ny, nx))
+    p = inputs.ATM * (1.0 + 0.2 * rng.random((ny, nx)))
+    u = rng.normal(0.0, 40.0, (ny, nx))
+    v = rng.normal(0.0, 40.0, (ny, nx))
+    Y = np.ones((1, ny, nx))
+    grid = inputs.grid_dict(nx, ny, 1e-3, 1.7e-3, [0, 1, 2, 2])
+    U = orc.prim_to_cons(gas, T, p, u, v, Y)
+    n, dt = 8, 5e-7
+    g = J.Grid.from_grid_dict(gas, grid, chemistry=False)
+    _mode(J, g, store)
+    g.set_state(U, T)
+    scale = np.maximum(np.abs(U).reshape(U.shape[0], -1).max(axis=1), 1e-12)
+    seed = np.ascontiguousarray(rng.normal(size=U.shape) / scale[:, None, None])
+    gU0 = np.zeros_like(U)
+    J.janc_step_adjoint(g.handle, n, dt, 3, J.LOSS_SEEDED, seed, gU0)
+    V = _dirs(U, 4, 72)
+    dUN, _, _, s = orc.trajectory_tangent(gas, grid, U, T, V, n, dt, chem=False)
+    assert s == 0
+    for l in range(4):
+        a, b = float(np.sum(seed * dUN[l])), float(np.sum(gU0 * V[l]))
+        assert abs(a - b) <= 1e-8 * np.sum(np.abs(seed * dUN[l])), (l, a, b)
+    g.close()
