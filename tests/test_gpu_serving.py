@@ -5,6 +5,7 @@ served request matches the oracle."""
 import numpy as np
 import pytest
 
+import mech_variants
 import oracle as orc
 from paper_2504_13750_gb300 import inputs
 
@@ -50,8 +51,8 @@ def _alone(J, st, steps):
     return U, T
 
 
-def _serve(J, reqs, pool_bytes=2 << 30, max_active=64, stagger=0, watch=None, budget=None):
-    mech = J.Mechanism(H2AIR)
+def _serve(J, reqs, pool_bytes=2 << 30, max_active=64, stagger=0, watch=None, budget=None, mech_dict=None):
+    mech = J.Mechanism(H2AIR if mech_dict is None else mech_dict)
     s = J.janc_server_create(mech, chemistry=True, pool_bytes=pool_bytes, max_active=max_active)
     if budget is not None:
         J.janc_server_set_cell_budget(s, *budget)
@@ -212,3 +213,19 @@ def test_run_until_returns_each_request_once(J):
             assert np.array_equal(U, Ua) and np.array_equal(T, Ta)
     finally:
         J.janc_server_destroy(s)
+
+
+def test_served_request_with_run_time_table_chemistry(J):
+    """A server whose 9-species table has another reaction structure than the
+    compiled one (the shipped reactions in reverse order) runs the batched
+    run-time-table chemistry kernel: two requests served together, each
+    against the oracle on the same table."""
+    rev = mech_variants.reordered(H2AIR)
+    reqs = [_requests()[k] for k in (0, 2)]
+    served = _serve(J, reqs, mech_dict=rev)
+    for (req, st), (U, T) in zip(reqs, served):
+        U0 = orc.prim_to_cons(rev, st["T"], st["p"], st["u"], st["v"], st["Y"])
+        Uo, To, s, _, _ = orc.step(rev, st["grid"], U0, st["T"], req["steps"], cfl=0.5)
+        assert s == 0
+        for k in range(U.shape[0]):
+            assert np.max(np.abs(U[k] - Uo[k])) <= 1e-10 * np.max(np.abs(Uo[k])) + 1e-300
