@@ -399,11 +399,10 @@ __device__ __forceinline__ void monomial(const double* X, SP sp, A a, int n, con
 // the stage input kept by the forward (entries 2i, 2i+1 of cell q), or null
 // to form them again.
 template <int NS>
-__device__ __forceinline__ void src_grad(const double* u, double T, const MechDev& m, const double (&w)[NS - 1],
+__device__ __forceinline__ void src_grad(const double* u, double T, const MechDev& m, const double* w,
                                          const double* __restrict__ keep, long long n, long long q, double& gT_out,
-                                         double (&gX)[NS]) {
+                                         double* gX) {
   constexpr int NSP = NS - 1;
-  // species arrays are read and written through pick / put (run-time indices)
   double X[NS];
   double rest = u[0];
 #pragma unroll
@@ -431,32 +430,25 @@ __device__ __forceinline__ void src_grad(const double* u, double T, const MechDe
   }
   const double cref = (P_REF / RU) * rT;
   const double rcref = (RU / P_REF) * T;
+  double zero[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) zero[k] = 0.0;
   double gT = 0.0;
 #pragma unroll
   for (int k = 0; k < NS; ++k) gX[k] = 0.0;
   for (int i = 0; i < m.nr; ++i) {
     const int nre = m.nre[i], npr = m.npr[i];
     double mi = 0.0;
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < nre && m.rsp[i][r] < NSP) mi = fma(-m.rnud[i][r], pick(w, m.rsp[i][r]), mi);
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < npr && m.psp[i][r] < NSP) mi = fma(m.pnud[i][r], pick(w, m.psp[i][r]), mi);
+    for (int r = 0; r < nre; ++r)
+      if (m.rsp[i][r] < NSP) mi = fma(-m.rnud[i][r], w[m.rsp[i][r]], mi);
+    for (int r = 0; r < npr; ++r)
+      if (m.psp[i][r] < NSP) mi = fma(m.pnud[i][r], w[m.psp[i][r]], mi);
     const double dlkf = fma(m.b[i], rT, m.EaR[i] * rT2);
     double kf, kb, dlkb = dlkf;
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < nre) {
-        const double d = pick(dG, m.rsp[i][r]);
-        for (int qq = 0; qq < m.rnu[i][r]; ++qq) dlkb += d;
-      }
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < npr) {
-        const double d = pick(dG, m.psp[i][r]);
-        for (int qq = 0; qq < m.pnu[i][r]; ++qq) dlkb -= d;
-      }
+    for (int r = 0; r < nre; ++r)
+      for (int qq = 0; qq < m.rnu[i][r]; ++qq) dlkb += dG[m.rsp[i][r]];
+    for (int r = 0; r < npr; ++r)
+      for (int qq = 0; qq < m.pnu[i][r]; ++qq) dlkb -= dG[m.psp[i][r]];
     const int dn = m.dnu[i];
     dlkb = fma((double)dn, rT, dlkb);
     if (keep) {
@@ -465,79 +457,26 @@ __device__ __forceinline__ void src_grad(const double* u, double T, const MechDe
     } else {
       kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
       kb = kf;
-#pragma unroll
-      for (int r = 0; r < MAX_SIDE; ++r)
-        if (r < nre) {
-          const double e = pick(eG, m.rsp[i][r]);
-          for (int qq = 0; qq < m.rnu[i][r]; ++qq) kb *= e;
-        }
-#pragma unroll
-      for (int r = 0; r < MAX_SIDE; ++r)
-        if (r < npr) {
-          const double e = pick(reG, m.psp[i][r]);
-          for (int qq = 0; qq < m.pnu[i][r]; ++qq) kb *= e;
-        }
+      for (int r = 0; r < nre; ++r)
+        for (int qq = 0; qq < m.rnu[i][r]; ++qq) kb *= eG[m.rsp[i][r]];
+      for (int r = 0; r < npr; ++r)
+        for (int qq = 0; qq < m.pnu[i][r]; ++qq) kb *= reG[m.psp[i][r]];
       for (int qq = 0; qq < dn; ++qq) kb *= rcref;
       for (int qq = 0; qq < -dn; ++qq) kb *= cref;
     }
-    // mass-action monomials of both sides and their gradients: P = x^a,
-    // P1 = a x^(a-1), F = prod P, gF_s = P1_s prod_{t != s} P_t
-    double PF[MAX_SIDE], P1F[MAX_SIDE], PB[MAX_SIDE], P1B[MAX_SIDE];
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r) {
-      PF[r] = 1.0; P1F[r] = 0.0; PB[r] = 1.0; P1B[r] = 0.0;
-      if (r < nre) {
-        const double x = pick(X, m.rsp[i][r]);
-        const int a = m.rnu[i][r];
-        double pw1 = 1.0;  // x^(a-1)
-        for (int qq = 0; qq < a - 1; ++qq) pw1 *= x;
-        P1F[r] = a * pw1;
-        PF[r] = pw1 * x;
-      }
-      if (r < npr) {
-        const double x = pick(X, m.psp[i][r]);
-        const int a = m.pnu[i][r];
-        double pw1 = 1.0;
-        for (int qq = 0; qq < a - 1; ++qq) pw1 *= x;
-        P1B[r] = a * pw1;
-        PB[r] = pw1 * x;
-      }
-    }
-    double F = 1.0, B = 1.0;
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r) {
-      if (r < nre) F *= PF[r];
-      if (r < npr) B *= PB[r];
-    }
+    double F, gF[MAX_SIDE], DF, hF[MAX_SIDE], B, gB[MAX_SIDE], DB, hB[MAX_SIDE];
+    monomial(X, [&](int s_) { return m.rsp[i][s_]; }, [&](int s_) { return m.rnu[i][s_]; }, nre, zero, F, gF, DF, hF);
+    monomial(X, [&](int s_) { return m.psp[i][s_]; }, [&](int s_) { return m.pnu[i][s_]; }, npr, zero, B, gB, DB, hB);
     double Mi = 1.0;
     if (m.tb[i]) {
       Mi = Ctot;
-      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], pick(X, m.effsp[i][e]), Mi);
+      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
     }
     const double net = fma(kf, F, -kb * B);
     gT = fma(mi * Mi, fma(kf * dlkf, F, -kb * dlkb * B), gT);
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < nre) {
-        double ex = P1F[r];
-#pragma unroll
-        for (int t = 0; t < MAX_SIDE; ++t)
-          if (t != r && t < nre) ex *= PF[t];
-        const int sp = m.rsp[i][r];
-        put(gX, sp, fma(mi * Mi * kf, ex, pick(gX, sp)));
-      }
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < npr) {
-        double ex = P1B[r];
-#pragma unroll
-        for (int t = 0; t < MAX_SIDE; ++t)
-          if (t != r && t < npr) ex *= PB[t];
-        const int sp = m.psp[i][r];
-        put(gX, sp, fma(-mi * Mi * kb, ex, pick(gX, sp)));
-      }
+    for (int r = 0; r < nre; ++r) gX[m.rsp[i][r]] = fma(mi * Mi * kf, gF[r], gX[m.rsp[i][r]]);
+    for (int r = 0; r < npr; ++r) gX[m.psp[i][r]] = fma(-mi * Mi * kb, gB[r], gX[m.psp[i][r]]);
     if (m.tb[i])
-#pragma unroll
       for (int j = 0; j < NS; ++j) gX[j] = fma(1.0 + m.effm1[i][j], mi * net, gX[j]);
   }
   gT_out = gT;

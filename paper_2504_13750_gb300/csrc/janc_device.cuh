@@ -231,42 +231,22 @@ __device__ __forceinline__ double sound_speed(const double* u, double t, const M
   return sqrt(Cp * p * rrho * rcp(Cv));
 }
 
-// a[i] and a[i] = v for a run-time index i, as selects over the constant
-// indices: the array stays in registers (an index into it from a run-time
-// table would put it in local memory).
-template <int N>
-__device__ __forceinline__ double pick(const double (&a)[N], int i) {
-  double v = a[0];
-#pragma unroll
-  for (int k = 1; k < N; ++k) v = (i == k) ? a[k] : v;
-  return v;
-}
-template <int N>
-__device__ __forceinline__ void put(double (&a)[N], int i, double v) {
-#pragma unroll
-  for (int k = 0; k < N; ++k) a[k] = (i == k) ? v : a[k];
-}
-
 // Molar production rates (Eq. 4.7-4.9) of the carried species k < ns - 1 at
 // (T, X(u)), for the explicit source-term form of the step.
+template <int NS>
 // keep (the discrete adjoint's store): k_f and k_b of reaction i go to
 // keep[2i n + idx] and keep[(2i+1) n + idx].
-template <int NS>
 __device__ __forceinline__ void carried_rates(const double* u, double T, const MechDev& m, double* wd,
                                               double* __restrict__ keep = nullptr, long long n = 0,
                                               long long idx = 0) {
   constexpr int NSP = NS - 1;
-  constexpr int NW = NSP > 0 ? NSP : 1;
-  // species arrays are read and written through pick / put: the reaction
-  // table's indices are run-time values
-  double X[NS], w[NW];
+  double X[NS];
   double rest = u[0];
-#pragma unroll
-  for (int k = 0; k < NW; ++k) w[k] = 0.0;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     X[k] = u[4 + k] * m.invM[k];
     rest -= u[4 + k];
+    wd[k] = 0.0;
   }
   X[NSP] = rest * m.invM[NSP];
   double Ctot = X[0];
@@ -287,18 +267,10 @@ __device__ __forceinline__ void carried_rates(const double* u, double T, const M
     const int nre = m.nre[i], npr = m.npr[i];
     const double kf = exp_t(fma(m.b[i], lnT, fma(-m.EaR[i], rT, m.lnA[i])));
     double kb = kf;
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < nre) {
-        const double e = pick(eG, m.rsp[i][r]);
-        for (int q = 0; q < m.rnu[i][r]; ++q) kb *= e;
-      }
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < npr) {
-        const double e = pick(reG, m.psp[i][r]);
-        for (int q = 0; q < m.pnu[i][r]; ++q) kb *= e;
-      }
+    for (int r = 0; r < nre; ++r)
+      for (int q = 0; q < m.rnu[i][r]; ++q) kb *= eG[m.rsp[i][r]];
+    for (int r = 0; r < npr; ++r)
+      for (int q = 0; q < m.pnu[i][r]; ++q) kb *= reG[m.psp[i][r]];
     for (int q = 0; q < m.dnu[i]; ++q) kb *= rcref;
     for (int q = 0; q < -m.dnu[i]; ++q) kb *= cref;
     if (keep) {
@@ -306,33 +278,21 @@ __device__ __forceinline__ void carried_rates(const double* u, double T, const M
       keep[(2LL * i + 1) * n + idx] = kb;
     }
     double fwd = kf, bwd = kb;
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < nre) {
-        const double x = pick(X, m.rsp[i][r]);
-        for (int q = 0; q < m.rnu[i][r]; ++q) fwd *= x;
-      }
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < npr) {
-        const double x = pick(X, m.psp[i][r]);
-        for (int q = 0; q < m.pnu[i][r]; ++q) bwd *= x;
-      }
+    for (int r = 0; r < nre; ++r)
+      for (int q = 0; q < m.rnu[i][r]; ++q) fwd *= X[m.rsp[i][r]];
+    for (int r = 0; r < npr; ++r)
+      for (int q = 0; q < m.pnu[i][r]; ++q) bwd *= X[m.psp[i][r]];
     double Mi = 1.0;
     if (m.tb[i]) {
       Mi = Ctot;
-      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], pick(X, m.effsp[i][e]), Mi);
+      for (int e = 0; e < m.neff[i]; ++e) Mi = fma(m.effv[i][e], X[m.effsp[i][e]], Mi);
     }
     const double q = Mi * (fwd - bwd);
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < nre && m.rsp[i][r] < NSP) put(w, m.rsp[i][r], fma(-m.rnud[i][r], q, pick(w, m.rsp[i][r])));
-#pragma unroll
-    for (int r = 0; r < MAX_SIDE; ++r)
-      if (r < npr && m.psp[i][r] < NSP) put(w, m.psp[i][r], fma(m.pnud[i][r], q, pick(w, m.psp[i][r])));
+    for (int r = 0; r < nre; ++r)
+      if (m.rsp[i][r] < NSP) wd[m.rsp[i][r]] = fma(-m.rnud[i][r], q, wd[m.rsp[i][r]]);
+    for (int r = 0; r < npr; ++r)
+      if (m.psp[i][r] < NSP) wd[m.psp[i][r]] = fma(m.pnud[i][r], q, wd[m.psp[i][r]]);
   }
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) wd[k] = w[k];
 }
 
 // Ghost-cell source index along one axis (3 layers, text after Eq. 4.11).
